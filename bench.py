@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the FHT2DT forward transform on GB300.
+
+Workload (default): one 4095 x 4095 float32 image, pixels i.i.d. N(0, 1)
+(seed 2), all four slope quadrants, EXTENDED boundary (output 4 x 4095 x 8189
+float32).  A step is one complete forward transform of that image.
+
+Prints one JSON line on rank 0.  `value` is input Mpix/s over all ranks with
+the image resident in HBM; `e2e` is the same metric through the public API
+with host buffers (pinned host -> device copy of the image and device -> host
+copy of the whole Hough output inside every step).  `roofline` reports the
+dominant kernel's model bytes per launch over its event-timed duration.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fht|reference]
+
+`--impl reference` times the CPU oracle (the plain single-threaded C
+recursion) on the host cores on a bounded sample of the same workload.
+Multi-GPU runs are independent replicas (weak scaling, no data exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "c2-extended": dict(h=4095, w=4095, quads=15, boundary="extended",
+                        desc="4095x4095 float32 N(0,1) seed 2, 4 quadrants, extended boundary"),
+    "c2-cyclic": dict(h=4095, w=4095, quads=15, boundary="cyclic",
+                      desc="4095x4095 float32 N(0,1) seed 2, 4 quadrants, cyclic boundary"),
+}
+METRIC = "FHT Mpix/s (4 quadrants)"
+UNIT = "Mpix/s"
+FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# --------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def clocks_start(gpu: int):
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    try:
+        p = subprocess.Popen(["nvidia-smi", "-i", str(gpu), f"--query-gpu={CLOCK_FIELDS}",
+                              "--format=csv,noheader,nounits", "-lms", "100"], stdout=f, stderr=subprocess.DEVNULL)
+    except OSError:
+        p = None
+    return p, f.name
+
+
+def clocks_stop(handle) -> dict:
+    p, path = handle
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    sm, smax, reasons, power = [], [], set(), []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    with open(path) as f:
+        for line in f:
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+    os.unlink(path)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+            "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2411_07351_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("source_hash") != _source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (reported baseline and the reference arm)
+# --------------------------------------------------------------------------
+def oracle_sample_seconds(img, wl, rows: int):
+    import oracle
+
+    sub = np.ascontiguousarray(img[:rows])
+    t = time.perf_counter()
+    oracle.fht(sub, 1, oracle.EXTENDED if wl["boundary"] == "extended" else oracle.CYCLIC)
+    return time.perf_counter() - t
+
+
+def _band_rows(per_step_budget_s: float, w: int, h: int) -> int:
+    # cost model of one quadrant of a band of r rows: r (w + r) log2 r, 3 s at r = 4095 (measured)
+    def est(r):
+        return 3.0 * (r * (w + r) * max(1.0, math.log2(r))) / (4095 * 8190 * 12)
+
+    r = h
+    while r > 64 and est(r) > per_step_budget_s:
+        r //= 2
+    return r
+
+
+def run_reference(args, wl):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2411_07351_gb300 import inputs
+
+    oracle.build()
+    img = inputs.c2_image(h=wl["h"], w=wl["w"])
+    rows = _band_rows(150.0 / max(1, args.steps + args.warmup), wl["w"], wl["h"])
+    for _ in range(args.warmup):
+        oracle_sample_seconds(img, wl, rows)
+    times = [oracle_sample_seconds(img, wl, rows) for _ in range(args.steps)]
+    sec = statistics.mean(times)
+    # one quadrant of `rows` image rows per step: a quarter of the 4-quadrant work per pixel
+    value = rows * wl["w"] / 4.0 / sec / 1e6
+    sample = f"quadrant Q0 of the first {rows} rows of the image (one quarter of the 4-quadrant work)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu": _cpu_model(), "nproc": os.cpu_count()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_fht(args, wl):
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2411_07351_gb300 as F
+    from paper_2411_07351_gb300 import _capi, inputs
+
+    h, w = wl["h"], wl["w"]
+    img = inputs.c2_image(h=h, w=w)
+    x = torch.from_numpy(img).cuda()
+    plan = F.Plan(h, w, torch.float32, wl["quads"], wl["boundary"], "T", device=local)
+    out = plan.new_output()
+    ws = plan.new_workspace()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    lib = _capi.load()
+    nl = ctypes.c_int32()
+    _capi.check(lib.fht_plan_launches(plan._h, ctypes.byref(nl)), "fht_plan_launches")
+    launches = nl.value
+    kinds, lbytes = [], []
+    for k in range(launches):
+        kd, by = ctypes.c_int32(), ctypes.c_int64()
+        _capi.check(lib.fht_plan_launch_info(plan._h, k, ctypes.byref(kd), ctypes.byref(by)), "launch_info")
+        kinds.append(kd.value)
+        lbytes.append(by.value)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    clk = clocks_start(local)
+    for _ in range(max(3, args.warmup)):
+        plan.forward(x, out, ws)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed between steps outside the step events ----
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush.zero_()
+        ev[i][0].record(stream)
+        plan.forward(x, out, ws)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = max_over_ranks(statistics.mean(step_ms))
+    value = world * h * w / (ms * 1e-3) / 1e6
+
+    # ---- per-kernel timing (events around every launch) ----
+    KP = min(K, 50)
+    kev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * launches)]
+    for e in kev:
+        e.record(stream)  # materialise the handles
+    handles = (ctypes.c_void_p * (2 * launches))(*[e.cuda_event for e in kev])
+    per_launch = np.zeros(launches)
+    torch.cuda.synchronize()
+    for _ in range(KP):
+        flush.zero_()
+        _capi.check(lib.fht_forward_timed(plan._h, x.data_ptr(), x.stride(0), out.data_ptr(), ws.data_ptr(),
+                                          ws.numel(), stream.cuda_stream, handles, 2 * launches), "fht_forward_timed")
+        torch.cuda.synchronize()
+        for k in range(launches):
+            per_launch[k] += kev[2 * k].elapsed_time(kev[2 * k + 1])
+    per_launch /= KP
+    kind_names = {0: "fused_kernel", 1: "upper_kernel"}
+    kernels = {}
+    for k in range(launches):
+        nm = kind_names[kinds[k]]
+        d = kernels.setdefault(nm, {"launches": 0, "ms": 0.0, "model_bytes": 0})
+        d["launches"] += 1
+        d["ms"] += per_launch[k]
+        d["model_bytes"] += lbytes[k]
+    dom = max(kernels, key=lambda n: kernels[n]["ms"])
+    peak, peak_kind = _peaks()
+    dk = kernels[dom]
+    achieved = dk["model_bytes"] / (dk["ms"] * 1e-3) / 1e9
+    for nm, d in kernels.items():
+        d["gbs"] = d["model_bytes"] / (d["ms"] * 1e-3) / 1e9
+        d["share"] = d["ms"] / float(per_launch.sum())
+
+    # ---- end to end through the public API with host buffers ----
+    host_in = torch.from_numpy(img).pin_memory()
+    host_out = torch.empty(plan.out_elems, dtype=torch.float32).pin_memory()
+    xin = torch.empty_like(x)
+    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(K):
+        eev[i][0].record(stream)
+        xin.copy_(host_in, non_blocking=True)
+        plan.forward(xin, out, ws)
+        host_out.copy_(out, non_blocking=True)
+        eev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in eev))
+    clocks = clocks_stop(clk)
+    e2e_value = world * h * w / (e2e_ms * 1e-3) / 1e6
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = h
+        sec = oracle_sample_seconds(img, wl, rows)
+        cpu = {"value": rows * w / 4.0 / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"quadrant Q0 of the full {h}x{w} image, one run ({sec:.1f} s); "
+                         "value scaled to 4 quadrants", "cpu": _cpu_model(), "nproc": os.cpu_count()}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "h": h, "w": w, "quadrants": 4, "boundary": wl["boundary"],
+                       "split": "T", "fused_rows": int(plan.info.fused_rows), "tile_cols": int(plan.info.tile_cols),
+                       "l2": "256 MiB buffer written between timed steps, outside the step events",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": _traffic(dom, "c2-" + wl["boundary"]),
+                         "algorithmic_bytes_per_launch": dk["model_bytes"] / dk["launches"]},
+            "kernels": kernels,
+            "model_bytes_per_step": int(plan.info.model_bytes), "ideal_bytes_per_step": int(plan.info.ideal_bytes),
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": int(host_in.numel() * host_in.element_size()),
+                    "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size())},
+            "gpu_launches": launches * K,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["fht", "reference"], default="fht")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2-extended")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_fht(args, wl)
+
+
+if __name__ == "__main__":
+    main()

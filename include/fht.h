@@ -1,0 +1,156 @@
+/*
+ * fht.h -- C ABI of libfht.so, a GB300 (sm_103a) implementation of the
+ * generalised Brady-Yong fast Hough transform FHT2DT (and the FHT2DS variant)
+ * of "Generalization of Brady-Yong Algorithm for Fast Hough Transform to
+ * Arbitrary Image Size" (arXiv 2411.07351).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Images are row-major I[y][x]: h rows, w columns, a row pitch given in
+ *    elements.  The transform splits the ROW range (Algorithm 1 of Section 3
+ *    applied to the transposed image), so each Hough row is contiguous.
+ *  - Quadrant Q0 sums the patterns pat(h, t) of Algorithm 2 running to the
+ *    right:  H0[t][x] = sum_y I[y][(x + pat(h,t)[y]) mod W], t in [0, h).
+ *    Q1 runs to the left (x - pat), Q2 / Q3 are Q0 / Q1 of the transposed
+ *    image (t in [0, w)).  Quadrants are not in the paper; the paper's
+ *    transform is one quadrant.
+ *  - Boundary: FHT_CYCLIC is the paper's Rotate (Algorithm 1, W = row length).
+ *    FHT_EXTENDED is the cyclic transform of the image zero-padded on the right
+ *    to W = length + n - 1, so that every line meeting the image is counted
+ *    exactly once; lines entering from the left land in columns [length, W).
+ *  - The output holds the requested quadrants packed in the order Q0..Q3,
+ *    each a dense row-major block of rows[q] x cols[q] elements starting at
+ *    element out_offset[q] (see fht_plan_info).
+ *  - Rounding of the child slopes [t (n_P - 1)/(n - 1)] is half to even, in
+ *    exact integer arithmetic.
+ *  - Device pointers are plain CUDA device addresses; `stream` is a
+ *    cudaStream_t passed as void* (NULL = the legacy default stream).
+ *  - Every call returns an fht_status and never aborts.  On failure a
+ *    message is available from fht_last_error() (per thread).
+ *  - Calls that take a stream only enqueue work: they never synchronise and
+ *    never allocate device memory.  The caller owns every buffer it passes.
+ */
+#ifndef FHT_H
+#define FHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fht_plan_s* fht_plan_t;
+typedef struct fht_queue_s* fht_queue_t;
+
+typedef enum {
+  FHT_OK = 0,
+  FHT_ERR_INVALID = 1,     /* bad argument, shape, dtype or size */
+  FHT_ERR_NOMEM = 2,       /* host or device allocation failed (plan creation) */
+  FHT_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+  FHT_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  FHT_ERR_BUSY = 5,        /* queue full; retry after polling */
+  FHT_ERR_UNSUPPORTED = 6, /* valid request this build does not implement */
+  FHT_ERR_DEVICE = 7       /* a device-side check failed (status word) */
+} fht_status;
+
+/* Input type -> accumulation / output type. */
+typedef enum {
+  FHT_U8_I32 = 0,  /* uint8 in, int32 out: exact (255 * 65535 < 2^31) */
+  FHT_I32_I32 = 1, /* int32 in, int32 out: exact while sums fit in int32 */
+  FHT_F32_F32 = 2, /* float in, float out, FP32 accumulation */
+  FHT_F64_F64 = 3  /* double in, double out */
+} fht_dtype;
+
+enum { FHT_Q0 = 1, FHT_Q1 = 2, FHT_Q2 = 4, FHT_Q3 = 8, FHT_QALL = 15 };
+
+typedef enum { FHT_CYCLIC = 0, FHT_EXTENDED = 1 } fht_boundary;
+
+/* Section 3: Split_T cuts off the largest power of two (FHT2DT, the paper's
+ * method); Split_S bisects (FHT2DS, Anikeev et al.). */
+typedef enum { FHT_SPLIT_T = 0, FHT_SPLIT_S = 1 } fht_split;
+
+/* Tuning knobs; zero fields take the built-in defaults. */
+typedef struct {
+  int32_t fused_rows;  /* F: largest subtree merged in shared memory (2..64, power of two) */
+  int32_t tile_cols;   /* column tile of the fused pass (multiple of 32) */
+  int32_t threads;     /* threads per CTA of the fused pass (multiple of 32) */
+  int32_t reserved[5];
+} fht_tuning_t;
+
+typedef struct {
+  int32_t h, w;
+  int32_t rows[4];       /* per quadrant: number of slopes (h for Q0/Q1, w for Q2/Q3); 0 if absent */
+  int32_t cols[4];       /* per quadrant: output row length W */
+  int64_t out_offset[4]; /* per quadrant: element offset of its block in the output; -1 if absent */
+  int64_t out_elems;     /* total output elements */
+  size_t workspace_bytes;/* minimum size of d_ws for fht_forward / fht_adjoint */
+  int64_t adds;          /* additions of the transform (Theorem 1's count, all quadrants) */
+  int64_t model_bytes;   /* HBM bytes the forward schedule must move (reads + writes) */
+  int64_t ideal_bytes;   /* input read once + output written once */
+  int32_t fused_rows, tile_cols, upper_passes, reserved;
+} fht_plan_info_t;
+
+/* Build a plan: the split tree of Section 3 (Split_T or Split_S applied
+ * recursively), the exact merge tables t -> (t1, t2, s) of Algorithm 1, the
+ * fused-subtree programs and the pass schedule; upload them to `device`.
+ * h, w in [1, 65535]; quadrants a non-zero subset of FHT_QALL.
+ * Synchronous; allocates the plan's own device tables (owned by the plan).
+ * device < 0 builds a host-only plan (tables, sizes and the byte model for
+ * inspection; no CUDA call is made and it cannot be executed).
+ * `tuning` may be NULL. */
+fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint32_t quadrants,
+                    fht_boundary boundary, fht_split split, int device, const fht_tuning_t* tuning);
+
+/* Shapes, offsets, workspace size and the byte / addition model of a plan. */
+fht_status fht_plan_info(fht_plan_t plan, fht_plan_info_t* info);
+
+/* Forward transform (Algorithm 1, all requested quadrants).
+ * d_in: h x w input elements of the plan's input type, row pitch in_pitch
+ * (elements, >= w).  d_out: out_elems elements of the output type (packed
+ * quadrants).  d_ws: workspace of at least workspace_bytes, 256-byte aligned;
+ * its contents on entry are ignored.  Enqueued on `stream`. */
+fht_status fht_forward(fht_plan_t plan, const void* d_in, int64_t in_pitch, void* d_out, void* d_ws,
+                       size_t ws_bytes, void* stream);
+
+/* Kernel launches one fht_forward of this plan enqueues. */
+fht_status fht_plan_launches(fht_plan_t plan, int32_t* count);
+
+/* Kind of the k-th launch of fht_forward (0: fused shared-memory pass,
+ * 1: upper per-height pass) and the HBM bytes its schedule must move
+ * (compulsory reads + writes of that launch). */
+fht_status fht_plan_launch_info(fht_plan_t plan, int32_t k, int32_t* kind, int64_t* model_bytes);
+
+/* fht_forward that also records events[2k] and events[2k + 1] (cudaEvent_t
+ * handles created by the caller) on `stream` just before and just after its
+ * k-th kernel launch, for per-kernel timing.  nevents >= 2 * launches. */
+fht_status fht_forward_timed(fht_plan_t plan, const void* d_in, int64_t in_pitch, void* d_out, void* d_ws,
+                             size_t ws_bytes, void* stream, void** events, int32_t nevents);
+
+/* Adjoint (back-projection): the exact transpose of fht_forward, i.e.
+ * d_gin = sum over quadrants of Q^T(d_gout_q), the transpose of Algorithm 1's
+ * merge applied level by level in reverse.  Float and double plans only.
+ * d_gout: out_elems elements; d_gin: h x w, row pitch gin_pitch (overwritten). */
+fht_status fht_adjoint(fht_plan_t plan, const void* d_gout, void* d_gin, int64_t gin_pitch, void* d_ws,
+                       size_t ws_bytes, void* stream);
+
+/* Host-side verification of a plan: walks every table entry and checks that
+ * each input, workspace, output and shared-memory index the kernels derive
+ * from it lies inside its buffer.  No device access; works on host-only plans.
+ * FHT_OK, or FHT_ERR_INVALID with the first violation in fht_last_error(). */
+fht_status fht_plan_check(fht_plan_t plan);
+
+/* Release a plan and its device tables.  NULL is accepted. */
+fht_status fht_plan_destroy(fht_plan_t plan);
+
+/* Device status word kept at the start of a workspace: FHT_OK or the first
+ * device-side error recorded by a kernel that used it.  Synchronises `stream`. */
+fht_status fht_ws_status(const void* d_ws, void* stream);
+
+const char* fht_status_string(fht_status status);
+const char* fht_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FHT_H */

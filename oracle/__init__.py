@@ -71,6 +71,7 @@ def _load():
             for name in ("orc_fht_i64", "orc_fht_f64", "orc_brute_i64", "orc_brute_f64",
                          "orc_adjoint_f64", "orc_adjoint_brute_f64"):
                 getattr(lib, name).argtypes = [i32, i32, vp, u32, i32, i32, vp]
+            lib.orc_brute_at_f64.argtypes = [i32, i32, vp, i32, i32, i64, vp, vp, vp, vp, vp]
             lib.orc_brady_yong_i64.argtypes = [i32, i32, vp, vp]
             lib.orc_brady_yong_i64.restype = ctypes.c_int
             _lib = lib
@@ -184,6 +185,20 @@ def adjoint(gout, h: int, w: int, quads: int = 1, boundary: int = CYCLIC, rule: 
     fn = lib.orc_adjoint_brute_f64 if brute_force else lib.orc_adjoint_f64
     fn(h, w, _ptr(g), quads, boundary, rule, _ptr(out))
     return out
+
+
+def brute_at(img, qs, ts, xs, boundary: int = CYCLIC, rule: int = SPLIT_T):
+    """Definition evaluated at sampled outputs (q, t, x): returns (values, L1 masses), float64."""
+    src = np.ascontiguousarray(np.asarray(img), dtype=np.float64)
+    h, w = src.shape
+    qs = np.ascontiguousarray(qs, dtype=np.int32)
+    ts = np.ascontiguousarray(ts, dtype=np.int32)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    val = np.zeros(len(qs), np.float64)
+    mass = np.zeros(len(qs), np.float64)
+    _load().orc_brute_at_f64(h, w, _ptr(src), boundary, rule, len(qs), _ptr(qs), _ptr(ts), _ptr(xs),
+                             _ptr(val), _ptr(mass))
+    return val, mass
 
 
 def brady_yong(img) -> np.ndarray:

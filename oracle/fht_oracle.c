@@ -432,3 +432,32 @@ int orc_brady_yong_i64(int32_t n, int32_t W, const int64_t* img, int64_t* out) {
   free(b);
   return 0;
 }
+
+/* Sampled brute force: the definition evaluated at chosen outputs only.
+ * For sample k (quadrant q[k], slope t[k], output column x[k]):
+ *   val[k]  = sum_y V[y][(x + sign pat(n,t)[y]) mod W]       (the Hough value)
+ *   mass[k] = sum_y |V[y][(x + sign pat(n,t)[y]) mod W]|     (the pattern's L1 mass)
+ * V is the quadrant's view of the image (transposed for q >= 2), zero outside
+ * the real columns.  Used for full-size images where O1 would be too slow. */
+void orc_brute_at_f64(int32_t h, int32_t w, const double* img, int32_t boundary, int32_t split, int64_t nsamp,
+                      const int32_t* qs, const int32_t* ts, const int32_t* xs, double* val, double* mass) {
+  int32_t* pat = (int32_t*)malloc(sizeof(int32_t) * (size_t)(h > w ? h : w));
+  for (int64_t k = 0; k < nsamp; k++) {
+    int q = qs[k];
+    int32_t n, L, W;
+    view_dims(h, w, q, boundary, &n, &L, &W);
+    int sign = (q & 1) ? -1 : 1;
+    orc_pattern(n, ts[k], split, pat);
+    double acc = 0, m = 0;
+    for (int32_t y = 0; y < n; y++) {
+      int32_t c = imod((int64_t)xs[k] + sign * pat[y], W);
+      if (c >= L) continue;
+      double v = (q < 2) ? img[(size_t)y * w + c] : img[(size_t)c * w + y];
+      acc += v;
+      m += v < 0 ? -v : v;
+    }
+    val[k] = acc;
+    mass[k] = m;
+  }
+  free(pat);
+}

@@ -1,0 +1,271 @@
+// extern "C" entry points of libfht.so (declared in include/fht.h).
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "../../include/fht.h"
+#include "fht_launch.hpp"
+#include "plan.hpp"
+
+struct fht_plan_s {
+  fht::HostPlan host;
+  fht::DevicePlan dev;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+fht_status fail(fht_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+fht_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(FHT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  *dst = nullptr;
+  if (src.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * src.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+void free_dev(fht::DevicePlan& d) {
+  if (d.fused) cudaFree(d.fused);
+  if (d.ops) cudaFree(d.ops);
+  if (d.rows) cudaFree(d.rows);
+  d.fused = nullptr;
+  d.ops = nullptr;
+  d.rows = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint32_t quadrants,
+                    fht_boundary boundary, fht_split split, int device, const fht_tuning_t* tuning) {
+  if (!out) return fail(FHT_ERR_INVALID, "fht_plan: out is NULL");
+  *out = nullptr;
+  if ((int)split != 0 && (int)split != 1) return fail(FHT_ERR_INVALID, "fht_plan: unknown split rule");
+  fht::PlanConfig cfg;
+  cfg.h = h;
+  cfg.w = w;
+  cfg.dtype = (int32_t)dtype;
+  cfg.quads = quadrants;
+  cfg.ext = (int32_t)boundary;
+  cfg.split = split == FHT_SPLIT_S ? fht::Split::S : fht::Split::T;
+  cfg.F = 64;
+  cfg.TW = dtype == FHT_F64_F64 ? 64 : 128;
+  cfg.threads = 256;
+  if (tuning) {
+    if (tuning->fused_rows) cfg.F = tuning->fused_rows;
+    if (tuning->tile_cols) cfg.TW = tuning->tile_cols;
+    if (tuning->threads) cfg.threads = tuning->threads;
+    if (cfg.threads > 256) return fail(FHT_ERR_INVALID, "fht_plan: threads must be <= 256");
+  }
+  fht_plan_s* p = new (std::nothrow) fht_plan_s();
+  if (!p) return fail(FHT_ERR_NOMEM, "fht_plan: host allocation failed");
+  std::string err;
+  try {
+    err = fht::build_plan(cfg, p->host);
+  } catch (const std::bad_alloc&) {
+    delete p;
+    return fail(FHT_ERR_NOMEM, "fht_plan: host allocation failed while building tables");
+  }
+  if (!err.empty()) {
+    delete p;
+    return fail(FHT_ERR_INVALID, "fht_plan: " + err);
+  }
+  p->dev.host = &p->host;
+  p->dev.device = device;
+  fht::fused_geometry(p->host, p->dev.fused_rp, p->dev.fused_smem);
+  if (device < 0) {  // host-only plan: tables and sizes for inspection, no device copy
+    *out = p;
+    return FHT_OK;
+  }
+  int max_smem = 0;
+  {
+    DeviceGuard g(device);
+    if (!g.ok) {
+      delete p;
+      return fail(FHT_ERR_CUDA, "fht_plan: cannot select device " + std::to_string(device));
+    }
+    cudaError_t e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, "fht_plan: cudaDeviceGetAttribute");
+    }
+    if ((size_t)max_smem < p->dev.fused_smem) {
+      const std::string need = std::to_string(p->dev.fused_smem);
+      delete p;
+      return fail(FHT_ERR_INVALID,
+                  "fht_plan: fused tile needs " + need + " bytes of shared memory; lower tile_cols or fused_rows");
+    }
+    if ((e = upload(&p->dev.fused, p->host.fused)) != cudaSuccess ||
+        (e = upload(&p->dev.ops, p->host.ops)) != cudaSuccess ||
+        (e = upload(&p->dev.rows, p->host.rows)) != cudaSuccess) {
+      free_dev(p->dev);
+      delete p;
+      if (e == cudaErrorMemoryAllocation) return fail(FHT_ERR_NOMEM, "fht_plan: device allocation failed");
+      return cuda_fail(e, "fht_plan: upload");
+    }
+  }
+  *out = p;
+  return FHT_OK;
+}
+
+fht_status fht_plan_info(fht_plan_t plan, fht_plan_info_t* info) {
+  if (!plan || !info) return fail(FHT_ERR_INVALID, "fht_plan_info: NULL argument");
+  const fht::HostPlan& P = plan->host;
+  memset(info, 0, sizeof(*info));
+  info->h = P.cfg.h;
+  info->w = P.cfg.w;
+  for (int q = 0; q < 4; q++) {
+    if (P.cfg.quads & (1u << q)) {
+      info->rows[q] = P.quad[q].n;
+      info->cols[q] = P.quad[q].W;
+      info->out_offset[q] = P.quad[q].out_off;
+    } else {
+      info->out_offset[q] = -1;
+    }
+  }
+  info->out_elems = P.out_elems;
+  info->workspace_bytes = P.ws_bytes;
+  info->adds = P.adds;
+  info->model_bytes = P.model_bytes;
+  info->ideal_bytes = P.ideal_bytes;
+  info->fused_rows = P.cfg.F;
+  info->tile_cols = P.cfg.TW;
+  info->upper_passes = (int32_t)P.pass_begin.size() - 1;
+  return FHT_OK;
+}
+
+static fht_status forward_impl(fht_plan_t plan, const void* d_in, int64_t in_pitch, void* d_out, void* d_ws,
+                               size_t ws_bytes, void* stream, void** events, int32_t nevents) {
+  if (!plan) return fail(FHT_ERR_INVALID, "fht_forward: plan is NULL");
+  if (events && nevents < 2 * fht::forward_launches(plan->host))
+    return fail(FHT_ERR_INVALID, "fht_forward_timed: need two events per kernel launch");
+  const fht::HostPlan& P = plan->host;
+  if (!d_in || !d_out || !d_ws) return fail(FHT_ERR_INVALID, "fht_forward: NULL buffer");
+  if (in_pitch < P.cfg.w) return fail(FHT_ERR_INVALID, "fht_forward: in_pitch < w");
+  if (ws_bytes < P.ws_bytes)
+    return fail(FHT_ERR_INVALID, "fht_forward: workspace too small (need " + std::to_string(P.ws_bytes) + " bytes)");
+  if (((uintptr_t)d_ws) % 256) return fail(FHT_ERR_INVALID, "fht_forward: workspace must be 256-byte aligned");
+  if (((uintptr_t)d_out) % P.acc_size) return fail(FHT_ERR_INVALID, "fht_forward: misaligned output");
+  if (((uintptr_t)d_in) % P.in_size) return fail(FHT_ERR_INVALID, "fht_forward: misaligned input");
+  if (plan->dev.device < 0) return fail(FHT_ERR_INVALID, "fht_forward: host-only plan (device < 0)");
+  DeviceGuard g(plan->dev.device);
+  if (!g.ok) return fail(FHT_ERR_CUDA, "fht_forward: cannot select the plan's device");
+  cudaError_t e = fht::launch_forward(plan->dev, d_in, in_pitch, d_out, d_ws, (cudaStream_t)stream,
+                                      reinterpret_cast<cudaEvent_t*>(events));
+  if (e != cudaSuccess) return cuda_fail(e, "fht_forward");
+  return FHT_OK;
+}
+
+fht_status fht_forward(fht_plan_t plan, const void* d_in, int64_t in_pitch, void* d_out, void* d_ws,
+                       size_t ws_bytes, void* stream) {
+  return forward_impl(plan, d_in, in_pitch, d_out, d_ws, ws_bytes, stream, nullptr, 0);
+}
+
+fht_status fht_forward_timed(fht_plan_t plan, const void* d_in, int64_t in_pitch, void* d_out, void* d_ws,
+                             size_t ws_bytes, void* stream, void** events, int32_t nevents) {
+  if (!events) return fail(FHT_ERR_INVALID, "fht_forward_timed: events is NULL");
+  return forward_impl(plan, d_in, in_pitch, d_out, d_ws, ws_bytes, stream, events, nevents);
+}
+
+fht_status fht_plan_launches(fht_plan_t plan, int32_t* count) {
+  if (!plan || !count) return fail(FHT_ERR_INVALID, "fht_plan_launches: NULL argument");
+  *count = fht::forward_launches(plan->host);
+  return FHT_OK;
+}
+
+fht_status fht_plan_launch_info(fht_plan_t plan, int32_t k, int32_t* kind, int64_t* model_bytes) {
+  if (!plan || !kind || !model_bytes) return fail(FHT_ERR_INVALID, "fht_plan_launch_info: NULL argument");
+  if (k < 0 || k >= fht::forward_launches(plan->host)) return fail(FHT_ERR_INVALID, "fht_plan_launch_info: k");
+  fht::forward_launch_info(plan->host, k, *kind, *model_bytes);
+  return FHT_OK;
+}
+
+fht_status fht_adjoint(fht_plan_t plan, const void* d_gout, void* d_gin, int64_t gin_pitch, void* d_ws,
+                       size_t ws_bytes, void* stream) {
+  (void)d_gout;
+  (void)d_gin;
+  (void)gin_pitch;
+  (void)d_ws;
+  (void)ws_bytes;
+  (void)stream;
+  if (!plan) return fail(FHT_ERR_INVALID, "fht_adjoint: plan is NULL");
+  return fail(FHT_ERR_UNSUPPORTED, "fht_adjoint: not built yet");
+}
+
+fht_status fht_plan_check(fht_plan_t plan) {
+  if (!plan) return fail(FHT_ERR_INVALID, "fht_plan_check: plan is NULL");
+  std::string err = fht::check_plan(plan->host, plan->dev.fused_rp);
+  if (!err.empty()) return fail(FHT_ERR_INVALID, "fht_plan_check: " + err);
+  return FHT_OK;
+}
+
+fht_status fht_plan_destroy(fht_plan_t plan) {
+  if (!plan) return FHT_OK;
+  if (plan->dev.device < 0) {
+    delete plan;
+    return FHT_OK;
+  }
+  {
+    DeviceGuard g(plan->dev.device);
+    free_dev(plan->dev);
+  }
+  delete plan;
+  return FHT_OK;
+}
+
+fht_status fht_ws_status(const void* d_ws, void* stream) {
+  if (!d_ws) return fail(FHT_ERR_INVALID, "fht_ws_status: NULL workspace");
+  int32_t word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, d_ws, sizeof(word), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fht_ws_status");
+  if (word == 0) return FHT_OK;
+  return fail(word > 0 && word <= FHT_ERR_DEVICE ? (fht_status)word : FHT_ERR_DEVICE,
+              "fht_ws_status: device-side status " + std::to_string(word));
+}
+
+const char* fht_status_string(fht_status s) {
+  switch (s) {
+    case FHT_OK: return "FHT_OK";
+    case FHT_ERR_INVALID: return "FHT_ERR_INVALID";
+    case FHT_ERR_NOMEM: return "FHT_ERR_NOMEM";
+    case FHT_ERR_CUDA: return "FHT_ERR_CUDA";
+    case FHT_ERR_TIMEOUT: return "FHT_ERR_TIMEOUT";
+    case FHT_ERR_BUSY: return "FHT_ERR_BUSY";
+    case FHT_ERR_UNSUPPORTED: return "FHT_ERR_UNSUPPORTED";
+    case FHT_ERR_DEVICE: return "FHT_ERR_DEVICE";
+  }
+  return "FHT_ERR_UNKNOWN";
+}
+
+const char* fht_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

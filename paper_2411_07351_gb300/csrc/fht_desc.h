@@ -1,0 +1,67 @@
+// Descriptors shared by the host plan builder and the CUDA kernels.
+// Plain structs, identical layout on host and device.
+#pragma once
+#include <stdint.h>
+
+namespace fht {
+
+// One slope quadrant of the plan.  The quadrant's "view" V is the image
+// (q = 0, 1) or its transpose (q = 2, 3), with the columns reversed for the
+// leftward quadrants (q = 1, 3).  Every kernel runs the rightward recursion on
+// V; only the final store maps a node column u to the output column
+//   X = (sigma * u + kappa) mod W.
+struct QuadDesc {
+  int32_t transpose;  // V[i][j] = I[j][i]
+  int32_t flip;       // V[i][j] = I'[i][L - 1 - j]
+  int32_t n;          // rows of V (split axis)
+  int32_t L;          // real row length of V
+  int32_t W;          // output row length (L, or L + n - 1 when extended)
+  int32_t ext;        // extended boundary: zero outside [0, L), no wrap
+  int32_t sigma;      // +1 or -1
+  int32_t kappa;      // see above
+  int64_t out_off;    // element offset of the quadrant in the output
+};
+
+// A subtree of at most F rows, merged entirely in shared memory.
+struct FusedItem {
+  int32_t q;          // quadrant
+  int32_t a;          // first row of the subtree in V
+  int32_t m;          // rows of the subtree
+  int32_t nlev;       // merge levels (the subtree's height)
+  int32_t prog;       // first MergeOp of its program: ops[prog + lev * m + r]
+  int32_t wn;         // output columns of the subtree (node width)
+  int32_t c;          // node column u = window column x + c
+  int32_t final_;     // 1: the subtree is the whole tree, store into the output
+  int64_t dst;        // element offset of its first row (workspace, or output if final_)
+  int32_t dst_pitch;  // elements between rows of dst
+  int32_t ntiles;     // column tiles of width tile_cols covering wn
+};
+
+// One row of one level of a fused program: dst row <- src[top] + src[bot] shifted by s.
+// bot < 0 means the row is carried unchanged to the next level.
+struct MergeOp {
+  int16_t top;
+  int16_t bot;
+  int16_t s;
+  int16_t pad;
+};
+
+// One output row of an upper (HBM-pass) merge:
+//   out[u] = top[u + dtop] + bot[u + dbot],  u in [0, wout)
+// cyclic: indices taken mod W (dtop = 0, 0 <= dbot < W, wout = wtop = wbot = W);
+// extended: terms outside [0, wtop) / [0, wbot) are zero.
+// The final merge stores out[u] at column (sigma * u + kappa) mod W of the output row.
+struct RowJob {
+  int64_t dst;  // element offset of the output row (workspace or output)
+  int64_t top;  // element offset of the top child's row t1 (workspace)
+  int64_t bot;  // element offset of the bottom child's row t2 (workspace)
+  int32_t wout, wtop, wbot;
+  int32_t dtop, dbot;
+  int32_t W;
+  int32_t flags;  // bit0: final (dst in output), bit1: extended, bit2: sigma = -1
+  int32_t kappa;
+};
+
+enum : int32_t { ROW_FINAL = 1, ROW_EXT = 2, ROW_NEG = 4 };
+
+}  // namespace fht

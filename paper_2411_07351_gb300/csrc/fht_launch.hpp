@@ -1,0 +1,34 @@
+// Device-side copy of a plan and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "plan.hpp"
+
+namespace fht {
+
+struct DevicePlan {
+  const HostPlan* host = nullptr;
+  int device = 0;
+  FusedItem* fused = nullptr;
+  MergeOp* ops = nullptr;
+  RowJob* rows = nullptr;
+  int32_t fused_rp = 0;    // shared row pitch of the fused kernel (elements)
+  size_t fused_smem = 0;   // dynamic shared memory of the fused kernel (bytes)
+};
+
+// Shared-memory geometry of the fused kernel for a plan.
+void fused_geometry(const HostPlan& P, int32_t& rp, size_t& smem);
+
+// Enqueues the forward transform.  When `events` is non-null, events[2k] and
+// events[2k + 1] are recorded just before and after the k-th kernel launch.
+cudaError_t launch_forward(const DevicePlan& D, const void* in, int64_t in_pitch, void* out, void* ws,
+                           cudaStream_t st, cudaEvent_t* events = nullptr);
+
+// Kernel launches of one forward transform, and the kind of launch k
+// (0: fused pass, 1: upper pass) with its model bytes.
+int32_t forward_launches(const HostPlan& P);
+void forward_launch_info(const HostPlan& P, int32_t k, int32_t& kind, int64_t& bytes);
+
+}  // namespace fht

@@ -1,0 +1,316 @@
+// Host plan builder (see plan.hpp).
+//
+// The transform of one quadrant is Algorithm 1 of Section 3 run on the
+// quadrant's view V (n rows split recursively, rows of length W).  The
+// calculation-order tree G(n) of Theorem 1's proof is built once; its nodes
+// are then scheduled in two kinds of passes:
+//   * fused pass: every maximal subtree of at most F rows is merged in shared
+//     memory from the input rows (one HBM read of the image, one write);
+//   * upper passes: one pass per tree height above the fused subtrees, each a
+//     gather-add over whole rows in HBM (Algorithm 1's merge, line by line).
+#include "plan.hpp"
+
+#include <algorithm>
+#include <map>
+
+namespace fht {
+
+static int32_t ceil_log2(int64_t n) {
+  int32_t k = 0;
+  while ((int64_t(1) << k) < n) k++;
+  return k;
+}
+
+void split_sizes(int32_t n, Split rule, int32_t& n0, int32_t& n1) {
+  if (rule == Split::T) {
+    n0 = (int32_t)(int64_t(1) << (ceil_log2(n) - 1));
+  } else {
+    n0 = n / 2;
+  }
+  n1 = n - n0;
+}
+
+int64_t round_half_even(int64_t a, int64_t d) {
+  int64_t q = a / d, r = a % d;
+  if (2 * r > d) return q + 1;
+  if (2 * r < d) return q;
+  return q + (q & 1);
+}
+
+void merge_entry(int32_t m, int32_t m0, int32_t m1, int32_t t, int32_t& t1, int32_t& t2, int32_t& s) {
+  t1 = (int32_t)round_half_even((int64_t)t * (m0 - 1), m - 1);
+  t2 = (int32_t)round_half_even((int64_t)t * (m1 - 1), m - 1);
+  s = t - t2;
+}
+
+static int32_t build_rec(Tree& tr, int32_t a, int32_t m, Split rule) {
+  TreeNode nd;
+  nd.a = a;
+  nd.m = m;
+  if (m > 1) {
+    int32_t m0, m1;
+    split_sizes(m, rule, m0, m1);
+    int32_t c0 = build_rec(tr, a, m0, rule);
+    int32_t c1 = build_rec(tr, a + m0, m1, rule);
+    nd.child[0] = c0;
+    nd.child[1] = c1;
+    nd.height = 1 + std::max(tr.nodes[c0].height, tr.nodes[c1].height);
+  }
+  tr.nodes.push_back(nd);
+  return (int32_t)tr.nodes.size() - 1;
+}
+
+Tree build_tree(int32_t n, Split rule) {
+  Tree tr;
+  tr.n = n;
+  tr.nodes.reserve(2 * (size_t)n);
+  build_rec(tr, 0, n, rule);
+  return tr;
+}
+
+// Program of a subtree of m rows rooted at node `r` of `tr`: for each level
+// (1..height) and each local row, the merge that produces it, or a carry.
+static void build_program(const Tree& tr, int32_t r, std::vector<MergeOp>& ops, int32_t& nlev) {
+  const TreeNode& root = tr.nodes[r];
+  nlev = root.height;
+  const int32_t m = root.m, base = root.a;
+  // collect the subtree's internal nodes by height
+  std::vector<std::vector<int32_t>> by_h(nlev + 1);
+  std::vector<int32_t> stack{r};
+  while (!stack.empty()) {
+    int32_t i = stack.back();
+    stack.pop_back();
+    const TreeNode& nd = tr.nodes[i];
+    if (nd.m > 1) {
+      by_h[nd.height].push_back(i);
+      stack.push_back(nd.child[0]);
+      stack.push_back(nd.child[1]);
+    }
+  }
+  for (int32_t lev = 1; lev <= nlev; lev++) {
+    size_t off = ops.size();
+    ops.resize(off + m);
+    for (int32_t j = 0; j < m; j++) ops[off + j] = MergeOp{(int16_t)j, (int16_t)-1, 0, 0};
+    for (int32_t i : by_h[lev]) {
+      const TreeNode& nd = tr.nodes[i];
+      const TreeNode& c0 = tr.nodes[nd.child[0]];
+      const TreeNode& c1 = tr.nodes[nd.child[1]];
+      for (int32_t t = 0; t < nd.m; t++) {
+        int32_t t1, t2, s;
+        merge_entry(nd.m, c0.m, c1.m, t, t1, t2, s);
+        MergeOp op;
+        op.top = (int16_t)(c0.a - base + t1);
+        op.bot = (int16_t)(c1.a - base + t2);
+        op.s = (int16_t)s;
+        op.pad = 0;
+        ops[off + (nd.a - base) + t] = op;
+      }
+    }
+  }
+}
+
+static int32_t dtype_in_size(int32_t dt) { return dt == 0 ? 1 : dt == 3 ? 8 : 4; }
+static int32_t dtype_acc_size(int32_t dt) { return dt == 3 ? 8 : 4; }
+
+std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
+  if (cfg.h < 1 || cfg.w < 1 || cfg.h > 65535 || cfg.w > 65535) return "h and w must be in [1, 65535]";
+  if (cfg.dtype < 0 || cfg.dtype > 3) return "unknown dtype";
+  if (cfg.quads == 0 || (cfg.quads & ~15u)) return "quadrants must be a non-empty subset of FHT_QALL";
+  if (cfg.ext != 0 && cfg.ext != 1) return "unknown boundary";
+  if (cfg.F < 1 || cfg.F > 64 || (cfg.F & (cfg.F - 1))) return "fused_rows must be a power of two in [1, 64]";
+  if (cfg.TW < 32 || cfg.TW % 32 || cfg.TW > 1024) return "tile_cols must be a multiple of 32 in [32, 1024]";
+  if (cfg.threads < 32 || cfg.threads % 32 || cfg.threads > 1024) return "threads must be a multiple of 32";
+  P = HostPlan();
+  P.cfg = cfg;
+  P.in_size = dtype_in_size(cfg.dtype);
+  P.acc_size = dtype_acc_size(cfg.dtype);
+  const int32_t acc = P.acc_size;
+
+  Tree trees[2];
+  bool have[2] = {false, false};
+  for (int q = 0; q < 4; q++) {
+    if (!(cfg.quads & (1u << q))) continue;
+    int ti = q < 2 ? 0 : 1;
+    if (!have[ti]) {
+      trees[ti] = build_tree(ti == 0 ? cfg.h : cfg.w, cfg.split);
+      have[ti] = true;
+    }
+  }
+
+  std::map<int32_t, std::pair<int32_t, int32_t>> prog_cache;  // fused root size -> (prog offset, nlev)
+  int64_t out_off = 0;
+  int64_t ws_off = 0;  // elements of the accumulator type after the header
+  std::vector<std::vector<RowJob>> passes;
+  std::vector<int64_t> bytes_by_height;
+
+  for (int q = 0; q < 4; q++) {
+    if (!(cfg.quads & (1u << q))) continue;
+    const int ti = q < 2 ? 0 : 1;
+    Tree tr = trees[ti];  // per-quadrant copy: buffer assignment is per quadrant
+    QuadDesc& Q = P.quad[q];
+    Q.transpose = q >= 2;
+    Q.flip = q & 1;
+    Q.n = tr.n;
+    Q.L = q < 2 ? cfg.w : cfg.h;
+    Q.W = cfg.ext ? Q.L + Q.n - 1 : Q.L;
+    Q.ext = cfg.ext;
+    // output column X of node column u:  Q0 cyclic X = u; Q0 extended X = u - (n-1) mod W;
+    // Q1 cyclic X = L-1-u; Q1 extended X = W-1-u (the view of Q1 is the column-reversed image).
+    if (!Q.flip) {
+      Q.sigma = 1;
+      Q.kappa = cfg.ext ? -(Q.n - 1) : 0;
+    } else {
+      Q.sigma = -1;
+      Q.kappa = cfg.ext ? Q.W - 1 : Q.L - 1;
+    }
+    Q.out_off = out_off;
+    P.quad_id[P.nquad++] = q;
+    const int64_t qsize = (int64_t)Q.n * Q.W;
+    out_off += qsize;
+
+    // workspace row pitch: widest non-root node, rounded to 128 bytes
+    const int32_t rootidx = tr.root();
+    int32_t widest = 1;
+    for (int32_t i = 0; i < (int32_t)tr.nodes.size(); i++) {
+      if (i == rootidx) continue;
+      int32_t wn = cfg.ext ? Q.L + tr.nodes[i].m - 1 : Q.W;
+      widest = std::max(widest, wn);
+    }
+    const int32_t align = 128 / acc;
+    const int32_t pitch = (widest + align - 1) / align * align;
+
+    // fused roots: maximal subtrees with m <= F
+    std::vector<char> is_upper(tr.nodes.size(), 0);
+    std::vector<int32_t> fused_roots;
+    for (int32_t i = 0; i < (int32_t)tr.nodes.size(); i++) is_upper[i] = tr.nodes[i].m > cfg.F;
+    for (int32_t i = 0; i < (int32_t)tr.nodes.size(); i++) {
+      const TreeNode& nd = tr.nodes[i];
+      if (nd.m > cfg.F) {
+        for (int c = 0; c < 2; c++)
+          if (!is_upper[nd.child[c]]) fused_roots.push_back(nd.child[c]);
+      }
+    }
+    if (!is_upper[rootidx]) fused_roots.push_back(rootidx);
+
+    // buffer assignment: fused roots -> 0; upper nodes -> smallest buffer not used by a child
+    int32_t nbuf = 1;
+    for (int32_t i : fused_roots) tr.nodes[i].buf = 0;
+    for (int32_t i = 0; i < (int32_t)tr.nodes.size(); i++) {
+      TreeNode& nd = tr.nodes[i];
+      if (!is_upper[i]) continue;
+      if (i == rootidx) {
+        nd.buf = -1;
+        continue;
+      }
+      int32_t b0 = tr.nodes[nd.child[0]].buf, b1 = tr.nodes[nd.child[1]].buf;
+      int32_t b = 0;
+      while (b == b0 || b == b1) b++;
+      nd.buf = b;
+      nbuf = std::max(nbuf, b + 1);
+    }
+    const bool root_fused = !is_upper[rootidx];
+    if (root_fused) nbuf = 0;  // the single fused subtree writes the output directly
+    P.ws_quad_off[q] = ws_off;
+    P.ws_pitch[q] = pitch;
+    P.nbuf[q] = nbuf;
+    const int64_t bufsize = (int64_t)tr.n * pitch;
+    ws_off += nbuf * bufsize;
+    auto buf_row = [&](int32_t b, int32_t row) -> int64_t {
+      return P.ws_quad_off[q] + (int64_t)b * bufsize + (int64_t)row * pitch;
+    };
+
+    // fused items
+    for (int32_t i : fused_roots) {
+      const TreeNode& nd = tr.nodes[i];
+      auto it = prog_cache.find(nd.m);
+      if (it == prog_cache.end()) {
+        int32_t off = (int32_t)P.ops.size(), nlev = 0;
+        build_program(tr, i, P.ops, nlev);
+        it = prog_cache.emplace(nd.m, std::make_pair(off, nlev)).first;
+      }
+      FusedItem fi;
+      fi.q = q;
+      fi.a = nd.a;
+      fi.m = nd.m;
+      fi.prog = it->second.first;
+      fi.nlev = it->second.second;
+      fi.wn = cfg.ext ? Q.L + nd.m - 1 : Q.W;
+      fi.c = cfg.ext ? nd.m - 1 : 0;
+      fi.final_ = (i == rootidx);
+      if (fi.final_) {
+        fi.dst = Q.out_off;
+        fi.dst_pitch = Q.W;
+      } else {
+        fi.dst = buf_row(nd.buf, nd.a);
+        fi.dst_pitch = pitch;
+      }
+      fi.ntiles = (fi.wn + cfg.TW - 1) / cfg.TW;
+      P.max_ntiles = std::max(P.max_ntiles, fi.ntiles);
+      P.max_fused_m = std::max(P.max_fused_m, nd.m);
+      P.fused.push_back(fi);
+      // model bytes: the subtree's input rows once, its Hough rows once
+      P.fused_bytes += (int64_t)nd.m * Q.L * P.in_size + (int64_t)nd.m * fi.wn * acc;
+    }
+
+    // upper passes: one per tree height, shared by all quadrants
+    for (int32_t i = 0; i < (int32_t)tr.nodes.size(); i++) {
+      const TreeNode& nd = tr.nodes[i];
+      if (!is_upper[i]) continue;
+      const TreeNode& c0 = tr.nodes[nd.child[0]];
+      const TreeNode& c1 = tr.nodes[nd.child[1]];
+      if ((int32_t)passes.size() <= nd.height) {
+        passes.resize(nd.height + 1);
+        bytes_by_height.resize(nd.height + 1, 0);
+      }
+      const bool fin = (i == rootidx);
+      const int32_t wout = cfg.ext ? Q.L + nd.m - 1 : Q.W;
+      const int32_t wtop = cfg.ext ? Q.L + c0.m - 1 : Q.W;
+      const int32_t wbot = cfg.ext ? Q.L + c1.m - 1 : Q.W;
+      for (int32_t t = 0; t < nd.m; t++) {
+        int32_t t1, t2, s;
+        merge_entry(nd.m, c0.m, c1.m, t, t1, t2, s);
+        RowJob rj;
+        rj.dst = fin ? Q.out_off + (int64_t)t * Q.W : buf_row(nd.buf, nd.a + t);
+        rj.top = buf_row(c0.buf, c0.a + t1);
+        rj.bot = buf_row(c1.buf, c1.a + t2);
+        rj.wout = wout;
+        rj.wtop = wtop;
+        rj.wbot = wbot;
+        if (cfg.ext) {
+          rj.dtop = -c1.m;
+          rj.dbot = s - c0.m;
+        } else {
+          rj.dtop = 0;
+          rj.dbot = (int32_t)(s % Q.W);
+        }
+        rj.W = Q.W;
+        rj.flags = (fin ? ROW_FINAL : 0) | (cfg.ext ? ROW_EXT : 0) | (Q.sigma < 0 ? ROW_NEG : 0);
+        rj.kappa = Q.kappa;
+        passes[nd.height].push_back(rj);
+      }
+      bytes_by_height[nd.height] += ((int64_t)c0.m * wtop + (int64_t)c1.m * wbot + (int64_t)nd.m * wout) * acc;
+    }
+    // additions (Theorem 1): every merged element of every internal node is one addition
+    for (const TreeNode& nd : tr.nodes)
+      if (nd.m > 1) P.adds += (int64_t)nd.m * (cfg.ext ? Q.L + nd.m - 1 : Q.W);
+    P.ideal_bytes += (int64_t)Q.n * Q.L * P.in_size + qsize * acc;
+  }
+  P.out_elems = out_off;
+  P.ws_bytes = kWsHeader + (size_t)ws_off * acc;
+  // flatten passes (skip empty heights)
+  P.pass_begin.push_back(0);
+  P.model_bytes = P.fused_bytes;
+  for (size_t k = 0; k < passes.size(); k++) {
+    if (passes[k].empty()) continue;
+    P.rows.insert(P.rows.end(), passes[k].begin(), passes[k].end());
+    P.pass_begin.push_back((int64_t)P.rows.size());
+    P.pass_bytes.push_back(bytes_by_height[k]);
+    P.model_bytes += bytes_by_height[k];
+  }
+  if (P.ops.empty()) P.ops.push_back(MergeOp{0, -1, 0, 0});
+  for (const MergeOp& op : P.ops)
+    if (op.bot >= 0) P.max_fused_shift = std::max<int32_t>(P.max_fused_shift, op.s);
+  return "";
+}
+
+}  // namespace fht

@@ -1,0 +1,87 @@
+// Host plan builder: split tree, exact merge tables, fused-subtree programs,
+// pass schedule and workspace layout for one (h, w, dtype, quadrants,
+// boundary, split) request.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fht_desc.h"
+
+namespace fht {
+
+enum class Split : int32_t { T = 0, S = 1 };
+
+// Section 3: Split_T(n) = <2^(ceil(log2 n) - 1), rest>; Split_S(n) = <floor(n/2), ceil(n/2)>.
+void split_sizes(int32_t n, Split rule, int32_t& n0, int32_t& n1);
+
+// [a / d] for a >= 0, d > 0, ties to even; exact integer arithmetic.
+int64_t round_half_even(int64_t a, int64_t d);
+
+struct TreeNode {
+  int32_t a = 0, m = 1;       // rows [a, a + m) of the view
+  int32_t child[2] = {-1, -1};
+  int32_t height = 0;         // 0 for a single row
+  int32_t buf = -1;           // workspace buffer holding the node's Hough rows (-1: output)
+};
+
+struct Tree {
+  int32_t n = 0;
+  std::vector<TreeNode> nodes;  // children precede parents; the root is last
+  int32_t root() const { return (int32_t)nodes.size() - 1; }
+};
+
+// Build G(n) of Theorem 1's proof: the binary tree of recursive splits.
+Tree build_tree(int32_t n, Split rule);
+
+// Merge table of a node of size m with children (m0, m1):
+// t -> (t1, t2, s) with t1 = [t(m0-1)/(m-1)], t2 = [t(m1-1)/(m-1)], s = t - t2.
+void merge_entry(int32_t m, int32_t m0, int32_t m1, int32_t t, int32_t& t1, int32_t& t2, int32_t& s);
+
+struct PlanConfig {
+  int32_t h = 0, w = 0;
+  int32_t dtype = 0;       // fht_dtype
+  uint32_t quads = 1;
+  int32_t ext = 0;         // boundary
+  Split split = Split::T;
+  int32_t F = 64;          // fused rows
+  int32_t TW = 128;        // fused column tile
+  int32_t threads = 256;   // fused CTA size
+};
+
+struct HostPlan {
+  PlanConfig cfg;
+  int32_t in_size = 1, acc_size = 4;
+  QuadDesc quad[4];
+  int32_t nquad = 0;                 // number of requested quadrants
+  int32_t quad_id[4];                // quadrant index of slot k
+  int64_t ws_quad_off[4];            // element offset of each quadrant's buffers in the workspace
+  int32_t ws_pitch[4];               // row pitch of each quadrant's buffers (elements)
+  int32_t nbuf[4];
+  int64_t out_elems = 0;
+  size_t ws_bytes = 0;               // includes the 256-byte status header
+  std::vector<FusedItem> fused;
+  std::vector<MergeOp> ops;
+  std::vector<RowJob> rows;          // all upper passes, pass after pass
+  std::vector<int64_t> pass_begin;   // rows[pass_begin[p] .. pass_begin[p+1])
+  std::vector<int64_t> pass_bytes;   // model bytes of each upper pass
+  int64_t fused_bytes = 0;           // model bytes of the fused pass
+  int32_t max_ntiles = 0;
+  int32_t max_fused_m = 1;
+  int32_t max_fused_shift = 0;        // largest shift s of any fused merge
+  int64_t adds = 0, model_bytes = 0, ideal_bytes = 0;
+};
+
+// Returns "" on success, else an error message.
+std::string build_plan(const PlanConfig& cfg, HostPlan& out);
+
+// Verifies, on the host, that every memory access the kernels derive from the
+// plan's tables stays inside its buffer (input, workspace, output, shared
+// window).  Returns "" or the first violation.
+std::string check_plan(const HostPlan& P, int32_t fused_rp);
+
+// Bytes of the status header at the start of every workspace.
+constexpr size_t kWsHeader = 256;
+
+}  // namespace fht

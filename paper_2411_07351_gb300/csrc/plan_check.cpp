@@ -1,0 +1,91 @@
+// Host-side bounds and race verification of a plan (see plan.hpp).
+// Every check below mirrors an index expression of the kernels in
+// fht_forward.cu; a plan that passes cannot make them touch memory outside
+// the input, the workspace, the output or the shared window.
+#include <algorithm>
+#include <set>
+#include <string>
+
+#include "plan.hpp"
+
+namespace fht {
+
+static std::string at(const char* what, int64_t i) { return std::string(what) + " #" + std::to_string(i) + ": "; }
+
+std::string check_plan(const HostPlan& P, int32_t fused_rp) {
+  const int64_t ws_elems = (int64_t)((P.ws_bytes - kWsHeader) / P.acc_size);
+  const int64_t out_elems = P.out_elems;
+  const int32_t TW = P.cfg.TW;
+  for (size_t k = 0; k < P.fused.size(); k++) {
+    const FusedItem& it = P.fused[k];
+    if (it.q < 0 || it.q > 3 || !(P.cfg.quads & (1u << it.q))) return at("fused", k) + "bad quadrant";
+    const QuadDesc& Q = P.quad[it.q];
+    const int32_t img_rows = Q.transpose ? P.cfg.w : P.cfg.h;  // view rows are image rows or columns
+    const int32_t img_len = Q.transpose ? P.cfg.h : P.cfg.w;
+    if (Q.n != img_rows || Q.L != img_len) return at("fused", k) + "view dims disagree with the image";
+    if (it.m < 1 || it.a < 0 || it.a + it.m > Q.n) return at("fused", k) + "rows outside the view";
+    if (it.m > P.max_fused_m) return at("fused", k) + "subtree taller than the shared buffers";
+    if (!Q.ext && it.c != 0) return at("fused", k) + "cyclic window must start at a column >= 0";
+    if (it.ntiles < 1 || (int64_t)(it.ntiles - 1) * TW >= it.wn || (int64_t)it.ntiles * TW < it.wn)
+      return at("fused", k) + "tile count does not cover the node width";
+    if (it.ntiles > P.max_ntiles) return at("fused", k) + "more tiles than the grid";
+    const int32_t TWin = TW + it.m - 1;
+    if (it.prog < 0 || (size_t)it.prog + (size_t)it.nlev * it.m > P.ops.size()) return at("fused", k) + "program";
+    for (int32_t l = 0; l < it.nlev; l++)
+      for (int32_t r = 0; r < it.m; r++) {
+        const MergeOp& op = P.ops[(size_t)it.prog + (size_t)l * it.m + r];
+        if (op.top < 0 || op.top >= it.m) return at("fused", k) + "merge reads a row outside the subtree";
+        if (op.bot >= it.m) return at("fused", k) + "merge reads a row outside the subtree";
+        if (op.bot >= 0 && (op.s < 0 || TWin - 1 + op.s >= fused_rp))
+          return at("fused", k) + "shifted read beyond the shared row";
+      }
+    if (TWin > fused_rp) return at("fused", k) + "window wider than the shared row";
+    if (!it.final_) {
+      if (it.wn > it.dst_pitch) return at("fused", k) + "node wider than the workspace pitch";
+      if (it.dst < 0 || it.dst + (int64_t)(it.m - 1) * it.dst_pitch + it.wn > ws_elems)
+        return at("fused", k) + "store outside the workspace";
+    } else {
+      if (it.dst_pitch != Q.W || it.wn != Q.W) return at("fused", k) + "final subtree must span the output row";
+      if (it.dst < 0 || it.dst + (int64_t)it.m * Q.W > out_elems) return at("fused", k) + "store outside the output";
+      for (int32_t u : {0, it.wn - 1}) {
+        const int64_t X = (int64_t)Q.sigma * u + Q.kappa;
+        if (X < -Q.W || X >= 2 * (int64_t)Q.W) return at("fused", k) + "column map needs more than one wrap";
+      }
+    }
+  }
+  for (size_t p = 0; p + 1 < P.pass_begin.size(); p++) {
+    std::set<int64_t> written;
+    for (int64_t k = P.pass_begin[p]; k < P.pass_begin[p + 1]; k++) {
+      const RowJob& J = P.rows[k];
+      if (!(J.flags & ROW_FINAL)) written.insert(J.dst);
+    }
+    for (int64_t k = P.pass_begin[p]; k < P.pass_begin[p + 1]; k++) {
+      const RowJob& J = P.rows[k];
+      const bool ext = J.flags & ROW_EXT, fin = J.flags & ROW_FINAL;
+      if (J.wout < 1 || J.wtop < 1 || J.wbot < 1 || J.W < 1) return at("row", k) + "empty row";
+      if (ext) {
+        if (J.top < 0 || J.top + J.wtop > ws_elems) return at("row", k) + "top row outside the workspace";
+        if (J.bot < 0 || J.bot + J.wbot > ws_elems) return at("row", k) + "bottom row outside the workspace";
+      } else {
+        if (J.wtop < J.wout || J.wbot != J.W || J.wout != J.W) return at("row", k) + "cyclic widths disagree";
+        if (J.dbot < 0 || J.dbot >= J.W || J.dtop != 0) return at("row", k) + "cyclic shift not reduced";
+        if (J.top < 0 || J.top + J.wout > ws_elems) return at("row", k) + "top row outside the workspace";
+        if (J.bot < 0 || J.bot + J.W > ws_elems) return at("row", k) + "bottom row outside the workspace";
+      }
+      if (written.count(J.top) || written.count(J.bot)) return at("row", k) + "reads a row written in the same pass";
+      if (fin) {
+        if (J.wout != J.W) return at("row", k) + "final row must span the output row";
+        if (J.dst < 0 || J.dst + J.W > out_elems) return at("row", k) + "store outside the output";
+        for (int32_t u : {0, J.wout - 1}) {
+          const int64_t X = (J.flags & ROW_NEG) ? (int64_t)J.kappa - u : (int64_t)u + J.kappa;
+          if (X < -J.W || X >= 2 * (int64_t)J.W) return at("row", k) + "column map needs more than one wrap";
+        }
+      } else {
+        if (J.dst < 0 || J.dst + J.wout > ws_elems) return at("row", k) + "store outside the workspace";
+      }
+    }
+  }
+  return "";
+}
+
+}  // namespace fht

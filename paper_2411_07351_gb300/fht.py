@@ -1,0 +1,158 @@
+"""Python face of libfht.so.
+
+PyTorch supplies device memory and streams; every step of the transform runs
+in the library's CUDA kernels.  ``Plan`` owns one ``fht_plan_t``.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from collections import OrderedDict
+
+import torch
+
+from . import _capi as C
+
+DTYPES = {  # torch input dtype -> (fht_dtype, output dtype)
+    torch.uint8: (C.FHT_U8_I32, torch.int32),
+    torch.int32: (C.FHT_I32_I32, torch.int32),
+    torch.float32: (C.FHT_F32_F32, torch.float32),
+    torch.float64: (C.FHT_F64_F64, torch.float64),
+}
+BOUNDARY = {"cyclic": C.FHT_CYCLIC, "extended": C.FHT_EXTENDED}
+SPLIT = {"T": C.FHT_SPLIT_T, "S": C.FHT_SPLIT_S}
+
+
+def _stream_handle(device: torch.device, stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return int(s.cuda_stream)
+
+
+class Plan:
+    """A transform plan for one (h, w, dtype, quadrants, boundary, split).
+
+    ``device`` is a CUDA device index, or -1 for a host-only plan (sizes,
+    tables and the byte model; cannot run).
+    """
+
+    def __init__(self, h: int, w: int, dtype=torch.float32, quads: int = C.FHT_QALL,
+                 boundary: str = "cyclic", split: str = "T", device: int | None = None,
+                 fused_rows: int = 0, tile_cols: int = 0, threads: int = 0):
+        self._lib = C.load()
+        if dtype not in DTYPES:
+            raise ValueError(f"unsupported dtype {dtype}")
+        self.h, self.w = int(h), int(w)
+        self.in_dtype = dtype
+        self.fht_dtype, self.out_dtype = DTYPES[dtype]
+        self.quads = int(quads)
+        self.boundary = boundary
+        self.split = split
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device_index = int(device)
+        tun = C.fht_tuning_t(fused_rows, tile_cols, threads)
+        handle = ctypes.c_void_p()
+        C.check(self._lib.fht_plan(ctypes.byref(handle), self.h, self.w, self.fht_dtype, self.quads,
+                                   BOUNDARY[boundary], SPLIT[split], self.device_index, ctypes.byref(tun)),
+                "fht_plan")
+        self._h = handle
+        info = C.fht_plan_info_t()
+        C.check(self._lib.fht_plan_info(self._h, ctypes.byref(info)), "fht_plan_info")
+        self.info = info
+        self.out_elems = int(info.out_elems)
+        self.workspace_bytes = int(info.workspace_bytes)
+        self.shapes = [(int(info.rows[q]), int(info.cols[q])) for q in range(4) if self.quads & (1 << q)]
+        self.offsets = [int(info.out_offset[q]) for q in range(4) if self.quads & (1 << q)]
+
+    @property
+    def device(self) -> torch.device:
+        return torch.device("cuda", self.device_index)
+
+    def check(self):
+        C.check(self._lib.fht_plan_check(self._h), "fht_plan_check")
+
+    def new_workspace(self) -> torch.Tensor:
+        # 256-byte alignment: the caching allocator returns 512-byte aligned blocks
+        return torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
+
+    def new_output(self) -> torch.Tensor:
+        return torch.empty(self.out_elems, dtype=self.out_dtype, device=self.device)
+
+    def forward(self, x: torch.Tensor, out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+        if x.dtype != self.in_dtype or x.dim() != 2 or tuple(x.shape) != (self.h, self.w):
+            raise ValueError(f"expected a {self.h}x{self.w} {self.in_dtype} tensor, got {tuple(x.shape)} {x.dtype}")
+        if not x.is_cuda or x.device.index != self.device_index:
+            raise ValueError("input must live on the plan's CUDA device")
+        if x.stride(1) != 1:
+            x = x.contiguous()
+        if out is None:
+            out = self.new_output()
+        if ws is None:
+            ws = self.new_workspace()
+        if out.numel() < self.out_elems or out.dtype != self.out_dtype or not out.is_contiguous():
+            raise ValueError("output buffer has the wrong size, dtype or layout")
+        C.check(self._lib.fht_forward(self._h, x.data_ptr(), x.stride(0), out.data_ptr(), ws.data_ptr(),
+                                      ws.numel() * ws.element_size(), _stream_handle(x.device, stream)),
+                "fht_forward")
+        return out
+
+    def adjoint(self, gout: torch.Tensor, gin: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+        if gout.dtype != self.out_dtype or gout.numel() != self.out_elems or not gout.is_contiguous():
+            raise ValueError("gout must be a contiguous tensor of out_elems elements of the output dtype")
+        if gin is None:
+            gin = torch.empty((self.h, self.w), dtype=self.out_dtype, device=self.device)
+        if ws is None:
+            ws = self.new_workspace()
+        C.check(self._lib.fht_adjoint(self._h, gout.data_ptr(), gin.data_ptr(), gin.stride(0), ws.data_ptr(),
+                                      ws.numel() * ws.element_size(), _stream_handle(gout.device, stream)),
+                "fht_adjoint")
+        return gin
+
+    def unpack(self, out: torch.Tensor) -> list[torch.Tensor]:
+        return [out[o:o + n * c].view(n, c) for (n, c), o in zip(self.shapes, self.offsets)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fht_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PlanCache:
+    """Least-recently-used cache of plans keyed by their full configuration."""
+
+    def __init__(self, capacity: int = 64):
+        self.capacity = capacity
+        self._d: OrderedDict = OrderedDict()
+        self._lock = threading.Lock()
+
+    def get(self, h, w, dtype, quads, boundary, split, device) -> Plan:
+        key = (h, w, dtype, quads, boundary, split, device)
+        with self._lock:
+            p = self._d.get(key)
+            if p is not None:
+                self._d.move_to_end(key)
+                return p
+        p = Plan(h, w, dtype, quads, boundary, split, device)
+        with self._lock:
+            self._d[key] = p
+            while len(self._d) > self.capacity:
+                _, old = self._d.popitem(last=False)
+                old.close()
+        return p
+
+
+_cache = PlanCache()
+
+
+def forward(x: torch.Tensor, quads: int = C.FHT_QALL, boundary: str = "cyclic", split: str = "T") -> torch.Tensor:
+    """FHT of one 2-D image tensor on its CUDA device; returns the packed quadrants."""
+    plan = _cache.get(x.shape[0], x.shape[1], x.dtype, quads, boundary, split, x.device.index)
+    return plan.forward(x)

@@ -1,0 +1,174 @@
+"""GPU parity of the forward transform against the CPU oracle.
+
+Integer inputs (uint8 -> int32, int32 -> int32) must be bit-exact.  Float32
+must satisfy |H_gpu - H_fp64| <= 1e-5 * M element by element, where M is the
+same transform of |I| in float64 (the L1 mass of the pattern); float64 must
+satisfy the same bound at 1e-12.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2411_07351_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5
+TOL_F64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_07351_gb300 import build as B
+
+    B.build()
+    import paper_2411_07351_gb300 as F
+
+    return F
+
+
+def _run(F, img_np, quads, boundary, split="T", **tun):
+    x = torch.from_numpy(np.ascontiguousarray(img_np)).cuda()
+    p = F.Plan(img_np.shape[0], img_np.shape[1], x.dtype, quads, boundary, split, **tun)
+    p.check()
+    out = p.forward(x)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _ob(orc, b):
+    return orc.EXTENDED if b == "extended" else orc.CYCLIC
+
+
+def _rule(orc, s):
+    return orc.SPLIT_S if s == "S" else orc.SPLIT_T
+
+
+def check_exact(F, orc, img, quads, boundary, split="T", **tun):
+    got = _run(F, img, quads, boundary, split, **tun)
+    ref = orc.fht(img.astype(np.int64), quads, _ob(orc, boundary), _rule(orc, split))
+    assert got.shape == ref.shape
+    bad = np.nonzero(got.astype(np.int64) != ref)[0]
+    assert bad.size == 0, f"{bad.size} mismatches, first at {bad[:5]}: got {got[bad[:5]]} want {ref[bad[:5]]}"
+
+
+def check_float(F, orc, img, quads, boundary, split="T", tol=TOL_F32, **tun):
+    got = _run(F, img, quads, boundary, split, **tun).astype(np.float64)
+    ref = orc.fht(img.astype(np.float64), quads, _ob(orc, boundary), _rule(orc, split))
+    mass = orc.fht(np.abs(img.astype(np.float64)), quads, _ob(orc, boundary), _rule(orc, split))
+    err = np.abs(got - ref)
+    bound = tol * mass + 1e-30
+    worst = int(np.argmax(err / bound))
+    assert (err <= bound).all(), f"worst {err[worst]} vs bound {bound[worst]} at {worst}"
+
+
+AWKWARD_H = [1, 2, 3, 5, 17, 63, 64, 65, 127, 129, 255, 257]
+AWKWARD_W = [1, 2, 3, 4, 31, 33, 130]
+
+
+@pytest.mark.parametrize("boundary", ["cyclic", "extended"])
+def test_c1_257_exact(F, orc, boundary):
+    img = inputs.c1_image()
+    check_exact(F, orc, img, 1, boundary)
+    check_exact(F, orc, img, 15, boundary)
+
+
+def test_c1_matches_brute_force(F, orc):
+    img = inputs.c1_image()
+    got = _run(F, img, 1, "cyclic")
+    ref = orc.brute(img.astype(np.int64), 1, orc.CYCLIC)
+    assert np.array_equal(got.astype(np.int64), ref)
+
+
+@pytest.mark.parametrize("boundary", ["cyclic", "extended"])
+def test_awkward_sizes_u8(F, orc, boundary):
+    for h in AWKWARD_H:
+        for w in AWKWARD_W:
+            img = inputs.uniform_u8(100 + h * 7 + w, h, w)
+            check_exact(F, orc, img, 15, boundary)
+
+
+@pytest.mark.parametrize("h,w", [(511, 300), (4095, 33), (4097, 17), (33, 4097), (1000, 1000)])
+def test_larger_u8(F, orc, h, w):
+    img = inputs.uniform_u8(h + w, h, w)
+    check_exact(F, orc, img, 15, "cyclic")
+    check_exact(F, orc, img, 15, "extended")
+
+
+@pytest.mark.parametrize("boundary", ["cyclic", "extended"])
+def test_split_s_u8(F, orc, boundary):
+    for h, w in [(3, 5), (23, 45), (100, 64), (363, 90)]:
+        img = inputs.uniform_u8(h * w, h, w)
+        check_exact(F, orc, img, 15, boundary, "S")
+
+
+@pytest.mark.parametrize("boundary", ["cyclic", "extended"])
+def test_float32(F, orc, boundary):
+    for h, w in [(1, 9), (13, 11), (64, 64), (65, 200), (300, 257), (700, 500)]:
+        img = inputs.normal_f32(h + 3 * w, h, w)
+        check_float(F, orc, img, 15, boundary)
+
+
+def test_float64_and_int32(F, orc):
+    rng = np.random.default_rng(0)
+    for h, w in [(7, 3), (129, 77), (257, 100)]:
+        img = rng.standard_normal((h, w))
+        check_float(F, orc, img, 15, "extended", tol=TOL_F64)
+        imi = rng.integers(-1000, 1000, (h, w)).astype(np.int32)
+        check_exact(F, orc, imi, 15, "cyclic")
+
+
+@pytest.mark.parametrize("fused_rows,tile_cols", [(1, 32), (2, 64), (8, 96), (32, 256), (64, 32)])
+def test_tuning_knobs_same_result(F, orc, fused_rows, tile_cols):
+    img = inputs.uniform_u8(7, 200, 150)
+    check_exact(F, orc, img, 15, "extended", fused_rows=fused_rows, tile_cols=tile_cols)
+    check_exact(F, orc, img, 15, "cyclic", fused_rows=fused_rows, tile_cols=tile_cols)
+
+
+def test_pitched_input(F, orc):
+    img = inputs.uniform_u8(9, 100, 70)
+    big = torch.zeros((100, 96), dtype=torch.uint8)
+    big[:, :70] = torch.from_numpy(img)
+    x = big.cuda()[:, :70]
+    assert x.stride(0) == 96
+    p = F.Plan(100, 70, torch.uint8, 15, "extended")
+    got = p.forward(x).cpu().numpy().astype(np.int64)
+    assert np.array_equal(got, orc.fht(img.astype(np.int64), 15, orc.EXTENDED))
+
+
+def test_c2_full_size_sampled(F, orc):
+    """4095 x 4095 float32, four quadrants, extended: sampled outputs against the
+    definition (FP64), plus the mass invariant on every row of every quadrant."""
+    img = inputs.c2_image()
+    x = torch.from_numpy(img).cuda()
+    p = F.Plan(4095, 4095, torch.float32, 15, "extended")
+    out = p.forward(x)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(42)
+    k = 3000
+    qs = rng.integers(0, 4, k)
+    ts = rng.integers(0, 4095, k)
+    xs = rng.integers(0, 8189, k)
+    # include the edges of every quadrant
+    qs = np.concatenate([qs, np.repeat(np.arange(4), 4)])
+    ts = np.concatenate([ts, np.tile([0, 4094, 0, 4094], 4)])
+    xs = np.concatenate([xs, np.tile([0, 8188, 8188, 0], 4)])
+    val, mass = orc.brute_at(img, qs, ts, xs, orc.EXTENDED)
+    blocks = p.unpack(out)
+    got = np.array([blocks[q][t, xx].item() for q, t, xx in zip(qs, ts, xs)], dtype=np.float64)
+    err = np.abs(got - val)
+    assert (err <= TOL_F32 * mass).all(), float((err / (mass + 1e-30)).max())
+    total = float(img.astype(np.float64).sum())
+    l1 = float(np.abs(img.astype(np.float64)).sum())
+    for b in blocks:
+        rs = b.double().sum(1).cpu().numpy()
+        assert np.abs(rs - total).max() <= TOL_F32 * l1
+
+
+def test_repeat_deterministic(F):
+    img = inputs.uniform_u8(3, 300, 300)
+    a = _run(F, img, 15, "extended")
+    b = _run(F, img, 15, "extended")
+    assert np.array_equal(a, b)
