@@ -1,0 +1,38 @@
+"""Run the forward transform a few times on a seeded image, for profilers.
+
+    python -m paper_2411_07351_gb300.profile_forward --h 2048 --w 2048 --reps 3
+
+Each rep launches the plan's kernels once (fused pass, then one pass per upper
+tree height).  Nothing is timed here; use it under ncu.
+"""
+import argparse
+
+import torch
+
+import paper_2411_07351_gb300 as F
+from paper_2411_07351_gb300 import inputs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--h", type=int, default=2048)
+    ap.add_argument("--w", type=int, default=2048)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--dtype", choices=["f32", "u8"], default="f32")
+    ap.add_argument("--boundary", choices=["cyclic", "extended"], default="extended")
+    a = ap.parse_args()
+    if a.dtype == "f32":
+        x = torch.from_numpy(inputs.normal_f32(2, a.h, a.w)).cuda()
+    else:
+        x = torch.from_numpy(inputs.uniform_u8(2, a.h, a.w)).cuda()
+    p = F.Plan(a.h, a.w, x.dtype, F.FHT_QALL, a.boundary)
+    out, ws = p.new_output(), p.new_workspace()
+    for _ in range(a.reps):
+        p.forward(x, out, ws)
+    torch.cuda.synchronize()
+    print(f"ok {a.h}x{a.w} {a.dtype} {a.boundary}: launches per forward = {1 + p.info.upper_passes}, "
+          f"model bytes = {p.info.model_bytes}")
+
+
+if __name__ == "__main__":
+    main()
