@@ -127,6 +127,27 @@ fht_status fht_plan_launch_info(fht_plan_t plan, int32_t k, int32_t* kind, int64
 fht_status fht_forward_timed(fht_plan_t plan, const void* d_in, int64_t in_pitch, void* d_out, void* d_ws,
                              size_t ws_bytes, void* stream, void** events, int32_t nevents);
 
+/* Size of the fixed scratch array used by fht_forward_noalloc (32 MiB). */
+#define FHT_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/* fht_forward without a caller-provided workspace, for callers that cannot
+ * allocate device memory when they run the transform (a real-time loop that
+ * must not block on cudaMalloc, a plugin whose host owns all allocations, a
+ * process whose free device memory already belongs to its own pool).  The
+ * paper has no counterpart: this is an interface choice of this library.
+ *  - The workspace is a fixed array of FHT_NOALLOC_SCRATCH_BYTES inside the
+ *    library, held on every GPU that loads it until the process exits.  Plans
+ *    whose workspace_bytes exceed it are rejected with FHT_ERR_INVALID.
+ *  - The call allocates nothing (no cudaMalloc, no cudaFree).  The plan is
+ *    created beforehand with fht_plan, which does allocate its tables.
+ *  - The first call on a device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - All calls share the one array, which keeps the last call's contents:
+ *    calls whose kernels overlap on the GPU (different streams without
+ *    ordering between them) race on it.  Order them on one stream.
+ *  - Arguments, output and errors as for fht_forward. */
+fht_status fht_forward_noalloc(fht_plan_t plan, const void* d_in, int64_t in_pitch, void* d_out, void* stream);
+
 /* Adjoint (back-projection): the exact transpose of fht_forward, i.e.
  * d_gin = sum over quadrants of Q^T(d_gout_q), the transpose of Algorithm 1's
  * merge applied level by level in reverse.  Float and double plans only.

@@ -47,6 +47,7 @@ SIGNATURES = {
     "fht_plan_launches": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "fht_plan_launch_info": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "fht_forward_timed": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp), _i32]),
+    "fht_forward_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "fht_plan_destroy": (ctypes.c_int, [_vp]),
     "fht_ws_status": (ctypes.c_int, [_vp, _vp]),
     "fht_status_string": (ctypes.c_char_p, [ctypes.c_int]),

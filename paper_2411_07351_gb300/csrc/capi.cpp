@@ -62,6 +62,10 @@ void free_dev(fht::DevicePlan& d) {
 
 }  // namespace
 
+// Shared with noalloc.cu.
+fht_status fht_capi_fail(fht_status st, const std::string& msg) { return fail(st, msg); }
+const fht::DevicePlan* fht_capi_device_plan(fht_plan_t plan) { return plan ? &plan->dev : nullptr; }
+
 extern "C" {
 
 fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint32_t quadrants,
