@@ -74,7 +74,7 @@ typedef enum { FHT_SPLIT_T = 0, FHT_SPLIT_S = 1 } fht_split;
 typedef struct {
   int32_t fused_rows;  /* F: largest subtree merged in shared memory (2..64, power of two) */
   int32_t tile_cols;   /* column tile of the fused pass (multiple of 32) */
-  int32_t threads;     /* threads per CTA of the fused pass (multiple of 32) */
+  int32_t threads;     /* threads per CTA of the fused pass (multiple of 32, <= 512) */
   int32_t reserved[5];
 } fht_tuning_t;
 
@@ -84,7 +84,8 @@ typedef struct {
   int32_t cols[4];       /* per quadrant: output row length W */
   int64_t out_offset[4]; /* per quadrant: element offset of its block in the output; -1 if absent */
   int64_t out_elems;     /* total output elements */
-  size_t workspace_bytes;/* minimum size of d_ws for fht_forward / fht_adjoint */
+  size_t workspace_bytes;/* minimum size of d_ws for fht_forward */
+  size_t adjoint_workspace_bytes; /* minimum size of d_ws for fht_adjoint */
   int64_t adds;          /* additions of the transform (Theorem 1's count, all quadrants) */
   int64_t model_bytes;   /* HBM bytes the forward schedule must move (reads + writes) */
   int64_t ideal_bytes;   /* input read once + output written once */
@@ -150,8 +151,10 @@ fht_status fht_forward_noalloc(fht_plan_t plan, const void* d_in, int64_t in_pit
 
 /* Adjoint (back-projection): the exact transpose of fht_forward, i.e.
  * d_gin = sum over quadrants of Q^T(d_gout_q), the transpose of Algorithm 1's
- * merge applied level by level in reverse.  Float and double plans only.
- * d_gout: out_elems elements; d_gin: h x w, row pitch gin_pitch (overwritten). */
+ * merge applied level by level in reverse, as gathers (deterministic).
+ * d_gout: out_elems elements of the output type; d_gin: h x w elements of the
+ * output type (int32 for integer plans), row pitch gin_pitch, overwritten.
+ * d_ws: at least adjoint_workspace_bytes, 256-byte aligned. */
 fht_status fht_adjoint(fht_plan_t plan, const void* d_gout, void* d_gin, int64_t gin_pitch, void* d_ws,
                        size_t ws_bytes, void* stream);
 

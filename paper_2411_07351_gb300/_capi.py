@@ -29,7 +29,8 @@ class fht_plan_info_t(ctypes.Structure):
     _fields_ = [("h", ctypes.c_int32), ("w", ctypes.c_int32),
                 ("rows", ctypes.c_int32 * 4), ("cols", ctypes.c_int32 * 4),
                 ("out_offset", ctypes.c_int64 * 4), ("out_elems", ctypes.c_int64),
-                ("workspace_bytes", ctypes.c_size_t), ("adds", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_size_t), ("adjoint_workspace_bytes", ctypes.c_size_t),
+                ("adds", ctypes.c_int64),
                 ("model_bytes", ctypes.c_int64), ("ideal_bytes", ctypes.c_int64),
                 ("fused_rows", ctypes.c_int32), ("tile_cols", ctypes.c_int32),
                 ("upper_passes", ctypes.c_int32), ("reserved", ctypes.c_int32)]

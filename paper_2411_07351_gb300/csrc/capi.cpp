@@ -3,6 +3,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 
@@ -52,12 +53,16 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 }
 
 void free_dev(fht::DevicePlan& d) {
-  if (d.fused) cudaFree(d.fused);
-  if (d.ops) cudaFree(d.ops);
-  if (d.rows) cudaFree(d.rows);
+  void* ptrs[] = {d.fused, d.ops, d.rows, d.arows, d.aterms, d.aptr, d.aops};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
   d.fused = nullptr;
   d.ops = nullptr;
   d.rows = nullptr;
+  d.arows = nullptr;
+  d.aterms = nullptr;
+  d.aptr = nullptr;
+  d.aops = nullptr;
 }
 
 }  // namespace
@@ -81,13 +86,13 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
   cfg.ext = (int32_t)boundary;
   cfg.split = split == FHT_SPLIT_S ? fht::Split::S : fht::Split::T;
   cfg.F = 64;
-  cfg.TW = dtype == FHT_F64_F64 ? 64 : 128;
-  cfg.threads = 256;
+  cfg.TW = dtype == FHT_F64_F64 ? 64 : 256;
+  cfg.threads = 512;
   if (tuning) {
     if (tuning->fused_rows) cfg.F = tuning->fused_rows;
     if (tuning->tile_cols) cfg.TW = tuning->tile_cols;
     if (tuning->threads) cfg.threads = tuning->threads;
-    if (cfg.threads > 256) return fail(FHT_ERR_INVALID, "fht_plan: threads must be <= 256");
+    if (cfg.threads > 512) return fail(FHT_ERR_INVALID, "fht_plan: threads must be <= 512");
   }
   fht_plan_s* p = new (std::nothrow) fht_plan_s();
   if (!p) return fail(FHT_ERR_NOMEM, "fht_plan: host allocation failed");
@@ -121,7 +126,10 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
       delete p;
       return cuda_fail(e, "fht_plan: cudaDeviceGetAttribute");
     }
-    if ((size_t)max_smem < p->dev.fused_smem) {
+    int32_t arp = 0, apad = 0;
+    size_t asmem = 0;
+    fht::adjoint_geometry(p->host, arp, apad, asmem);
+    if ((size_t)max_smem < std::max(p->dev.fused_smem, asmem)) {
       const std::string need = std::to_string(p->dev.fused_smem);
       delete p;
       return fail(FHT_ERR_INVALID,
@@ -129,7 +137,11 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
     }
     if ((e = upload(&p->dev.fused, p->host.fused)) != cudaSuccess ||
         (e = upload(&p->dev.ops, p->host.ops)) != cudaSuccess ||
-        (e = upload(&p->dev.rows, p->host.rows)) != cudaSuccess) {
+        (e = upload(&p->dev.rows, p->host.rows)) != cudaSuccess ||
+        (e = upload(&p->dev.arows, p->host.arows)) != cudaSuccess ||
+        (e = upload(&p->dev.aterms, p->host.aterms)) != cudaSuccess ||
+        (e = upload(&p->dev.aptr, p->host.aptr)) != cudaSuccess ||
+        (e = upload(&p->dev.aops, p->host.aops)) != cudaSuccess) {
       free_dev(p->dev);
       delete p;
       if (e == cudaErrorMemoryAllocation) return fail(FHT_ERR_NOMEM, "fht_plan: device allocation failed");
@@ -157,6 +169,7 @@ fht_status fht_plan_info(fht_plan_t plan, fht_plan_info_t* info) {
   }
   info->out_elems = P.out_elems;
   info->workspace_bytes = P.ws_bytes;
+  info->adjoint_workspace_bytes = P.adj_ws_bytes;
   info->adds = P.adds;
   info->model_bytes = P.model_bytes;
   info->ideal_bytes = P.ideal_bytes;
@@ -214,19 +227,30 @@ fht_status fht_plan_launch_info(fht_plan_t plan, int32_t k, int32_t* kind, int64
 
 fht_status fht_adjoint(fht_plan_t plan, const void* d_gout, void* d_gin, int64_t gin_pitch, void* d_ws,
                        size_t ws_bytes, void* stream) {
-  (void)d_gout;
-  (void)d_gin;
-  (void)gin_pitch;
-  (void)d_ws;
-  (void)ws_bytes;
-  (void)stream;
   if (!plan) return fail(FHT_ERR_INVALID, "fht_adjoint: plan is NULL");
-  return fail(FHT_ERR_UNSUPPORTED, "fht_adjoint: not built yet");
+  const fht::HostPlan& P = plan->host;
+  if (plan->dev.device < 0) return fail(FHT_ERR_INVALID, "fht_adjoint: host-only plan (device < 0)");
+  if (!d_gout || !d_gin || !d_ws) return fail(FHT_ERR_INVALID, "fht_adjoint: NULL buffer");
+  if (gin_pitch < P.cfg.w) return fail(FHT_ERR_INVALID, "fht_adjoint: gin_pitch < w");
+  if (ws_bytes < P.adj_ws_bytes)
+    return fail(FHT_ERR_INVALID,
+                "fht_adjoint: workspace too small (need " + std::to_string(P.adj_ws_bytes) + " bytes)");
+  if (((uintptr_t)d_ws) % 256) return fail(FHT_ERR_INVALID, "fht_adjoint: workspace must be 256-byte aligned");
+  if (((uintptr_t)d_gout) % P.acc_size || ((uintptr_t)d_gin) % P.acc_size)
+    return fail(FHT_ERR_INVALID, "fht_adjoint: misaligned buffer");
+  DeviceGuard g(plan->dev.device);
+  if (!g.ok) return fail(FHT_ERR_CUDA, "fht_adjoint: cannot select the plan's device");
+  cudaError_t e = fht::launch_adjoint(plan->dev, d_gout, d_gin, gin_pitch, d_ws, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fht_adjoint");
+  return FHT_OK;
 }
 
 fht_status fht_plan_check(fht_plan_t plan) {
   if (!plan) return fail(FHT_ERR_INVALID, "fht_plan_check: plan is NULL");
-  std::string err = fht::check_plan(plan->host, plan->dev.fused_rp);
+  int32_t arp = 0, apad = 0;
+  size_t asmem = 0;
+  fht::adjoint_geometry(plan->host, arp, apad, asmem);
+  std::string err = fht::check_plan(plan->host, plan->dev.fused_rp, arp, apad);
   if (!err.empty()) return fail(FHT_ERR_INVALID, "fht_plan_check: " + err);
   return FHT_OK;
 }

@@ -1,0 +1,259 @@
+// Adjoint (back-projection) kernels: the exact transpose of the forward
+// schedule of fht_forward.cu, run in reverse.
+//
+// Forward merge (Algorithm 1):  J(t)[u] = R0(t1)[u + dtop] + R1(t2)[u + dbot(t)].
+// Its transpose sends the gradient of J(t) back to R0(t1) and, shifted the
+// other way, to R1(t2).  Written as gathers (no atomics, fixed summation
+// order, so results are deterministic):
+//   * adj_upper_kernel: one pass per upper tree height, highest first; each
+//     child row sums the parent rows that read it (a contiguous range of t).
+//   * adj_fused_kernel: each fused subtree's levels in reverse in shared
+//     memory, over a window of tile + m - 1 columns with the halo on the
+//     left (a pixel is read by outputs at columns up to m - 1 to its left).
+//   * adj_sum_kernel: the per-quadrant image gradients are summed.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fht_desc.h"
+#include "fht_launch.hpp"
+
+namespace fht {
+
+struct AdjFusedParams {
+  const void* gout;  // AccT output gradient
+  void* ws;          // AccT workspace base (after the header)
+  const FusedItem* items;
+  const int32_t* aptr;
+  const MergeOp* aops;
+  QuadDesc quad[4];
+  int32_t h, w;
+  int32_t TW;
+  int32_t RP;    // shared row pitch
+  int32_t PADL;  // left pad of every shared row (largest shift)
+  int32_t Fm;
+};
+
+__device__ __forceinline__ int32_t wrap_mod(int32_t x, int32_t W) {
+  int32_t r = x % W;
+  return r < 0 ? r + W : r;
+}
+
+template <typename AccT>
+__global__ void __launch_bounds__(512, 1) adj_fused_kernel(AdjFusedParams p) {
+  const FusedItem it = p.items[blockIdx.x];
+  const int32_t tile = blockIdx.y;
+  if (tile >= it.antiles) return;
+  const QuadDesc& Q = p.quad[it.q];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AccT* bufA = reinterpret_cast<AccT*>(smem_raw);
+  AccT* bufB = bufA + (size_t)p.Fm * p.RP;
+  const AccT* __restrict__ gout = static_cast<const AccT*>(p.gout);
+  AccT* __restrict__ ws = static_cast<AccT*>(p.ws);
+
+  const int32_t m = it.m;
+  const int32_t TZin = p.TW + m - 1;
+  const int32_t z0 = tile * p.TW;
+  const int32_t xs = z0 - (m - 1);  // window start in node x coordinates
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+
+  // ---- stage the gradient of the subtree's Hough rows ----
+  constexpr int U = 8;
+  for (int32_t r = warp; r < m; r += nwarps) {
+    AccT* dst = bufA + (size_t)r * p.RP + p.PADL;
+    for (int32_t j0 = 0; j0 < TZin; j0 += 32 * U) {
+      AccT v[U];
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const int32_t j = j0 + q * 32 + lane;
+        v[q] = AccT(0);
+        if (j < TZin) {
+          int32_t u = xs + j + it.c;
+          bool ok = true;
+          if (Q.ext) {
+            ok = u >= 0 && u < it.wn;
+          } else {
+            u = wrap_mod(u, Q.W);
+          }
+          if (ok) {
+            if (it.final_) {
+              int32_t X = Q.sigma * u + Q.kappa;
+              if (X < 0) X += Q.W;
+              if (X >= Q.W) X -= Q.W;
+              v[q] = gout[it.dst + (int64_t)r * Q.W + X];
+            } else {
+              v[q] = ws[it.dst + (int64_t)r * it.dst_pitch + u];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const int32_t j = j0 + q * 32 + lane;
+        if (j < TZin) dst[j] = v[q];
+      }
+    }
+  }
+
+  // ---- the subtree's merges in reverse ----
+  AccT* src = bufA;
+  AccT* dst = bufB;
+  for (int32_t lev = it.nlev - 1; lev >= 0; lev--) {
+    __syncthreads();
+    const int32_t* ptr = p.aptr + it.aprog + (size_t)lev * (m + 1);
+    for (int32_t k = warp; k < m; k += nwarps) {
+      const int32_t b = ptr[k], e = ptr[k + 1];
+      AccT* d = dst + (size_t)k * p.RP + p.PADL;
+      for (int32_t j = lane; j < TZin; j += 32) {
+        AccT acc = AccT(0);
+        for (int32_t t = b; t < e; t++) {
+          const MergeOp op = p.aops[t];
+          acc += src[(size_t)op.top * p.RP + p.PADL + j - op.s];
+        }
+        d[j] = acc;
+      }
+    }
+    AccT* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  __syncthreads();
+
+  // ---- leaf gradients: window columns [m - 1, TZin) are view columns [z0, z0 + TW) ----
+  AccT* __restrict__ gq = ws + Q.grad_off;
+  if (!Q.transpose) {
+    for (int32_t r = warp; r < m; r += nwarps) {
+      const AccT* s = src + (size_t)r * p.RP + p.PADL + (m - 1);
+      AccT* o = gq + (int64_t)(it.a + r) * p.w;
+      for (int32_t jj = lane; jj < p.TW; jj += 32) {
+        const int32_t z = z0 + jj;
+        if (z < Q.L) o[Q.flip ? Q.L - 1 - z : z] = s[jj];
+      }
+    }
+  } else {
+    for (int32_t jj = warp; jj < p.TW; jj += nwarps) {
+      const int32_t z = z0 + jj;
+      if (z >= Q.L) continue;
+      AccT* o = gq + (int64_t)(Q.flip ? Q.L - 1 - z : z) * p.w + it.a;
+      for (int32_t r = lane; r < m; r += 32) o[r] = src[(size_t)r * p.RP + p.PADL + (m - 1) + jj];
+    }
+  }
+}
+
+template <typename AccT>
+__global__ void __launch_bounds__(256) adj_upper_kernel(const AdjRow* __restrict__ rows, int64_t nrows,
+                                                       const AdjTerm* __restrict__ terms, const AccT* ws_in,
+                                                       AccT* ws_out, const AccT* __restrict__ gout) {
+  for (int64_t k = blockIdx.x; k < nrows; k += gridDim.x) {
+    const AdjRow R = rows[k];
+    const bool fin = R.flags & ROW_FINAL;
+    const bool ext = R.flags & ROW_EXT;
+    const bool neg = R.flags & ROW_NEG;
+    const AccT* src = (fin ? gout : ws_in) + R.src;
+    AccT* dst = ws_out + R.dst;
+    for (int32_t i = threadIdx.x; i < R.wdst; i += blockDim.x) {
+      AccT acc = AccT(0);
+      for (int32_t c = 0; c < R.term_count; c++) {
+        const AdjTerm T = terms[R.term_begin + c];
+        int32_t u = i + T.e;
+        if (ext) {
+          if (u < 0 || u >= R.wsrc) continue;
+        } else if (u >= R.W) {
+          u -= R.W;
+        }
+        if (fin) {
+          int32_t X = neg ? R.kappa - u : u + R.kappa;
+          if (X < 0) X += R.W;
+          if (X >= R.W) X -= R.W;
+          u = X;
+        }
+        acc += src[(int64_t)T.t * R.src_pitch + u];
+      }
+      dst[i] = acc;
+    }
+  }
+}
+
+template <typename AccT>
+__global__ void adj_sum_kernel(const AccT* __restrict__ ws, int64_t g0, int64_t g1, int64_t g2, int64_t g3,
+                               int32_t nq, int32_t h, int32_t w, AccT* __restrict__ gin, int64_t pitch) {
+  const int64_t total = (int64_t)h * w;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    AccT v = ws[g0 + i];
+    if (nq > 1) v += ws[g1 + i];
+    if (nq > 2) v += ws[g2 + i];
+    if (nq > 3) v += ws[g3 + i];
+    const int64_t y = i / w, x = i - y * w;
+    gin[y * pitch + x] = v;
+  }
+}
+
+void adjoint_geometry(const HostPlan& P, int32_t& rp, int32_t& padl, size_t& smem) {
+  const int32_t Fm = P.max_fused_m;
+  padl = P.max_fused_shift;
+  rp = padl + P.cfg.TW + Fm - 1;
+  if (rp % 2 == 0) rp++;
+  smem = (size_t)2 * Fm * rp * P.acc_size;
+}
+
+template <typename AccT>
+static cudaError_t launch_adjoint_t(const DevicePlan& D, const void* gout, void* gin, int64_t gin_pitch, void* ws,
+                                    cudaStream_t st) {
+  const HostPlan& P = *D.host;
+  AccT* wsa = reinterpret_cast<AccT*>(static_cast<unsigned char*>(ws) + kWsHeader);
+  cudaError_t e;
+  for (size_t p = 0; p + 1 < P.apass_begin.size(); p++) {
+    const int64_t b = P.apass_begin[p], n = P.apass_begin[p + 1] - b;
+    if (n <= 0) continue;
+    const unsigned blocks = (unsigned)std::min<int64_t>(n, 1 << 30);
+    adj_upper_kernel<AccT><<<blocks, 256, 0, st>>>(D.arows + b, n, D.aterms, wsa, wsa,
+                                                   static_cast<const AccT*>(gout));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  AdjFusedParams fp;
+  fp.gout = gout;
+  fp.ws = wsa;
+  fp.items = D.fused;
+  fp.aptr = D.aptr;
+  fp.aops = D.aops;
+  for (int q = 0; q < 4; q++) fp.quad[q] = P.quad[q];
+  fp.h = P.cfg.h;
+  fp.w = P.cfg.w;
+  fp.TW = P.cfg.TW;
+  int32_t rp, padl;
+  size_t smem;
+  adjoint_geometry(P, rp, padl, smem);
+  fp.RP = rp;
+  fp.PADL = padl;
+  fp.Fm = P.max_fused_m;
+  auto kfn = adj_fused_kernel<AccT>;
+  if ((e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  dim3 grid((unsigned)P.fused.size(), P.max_antiles);
+  kfn<<<grid, P.cfg.threads, smem, st>>>(fp);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int64_t g[4] = {0, 0, 0, 0};
+  int32_t nq = 0;
+  for (int q = 0; q < 4; q++)
+    if (P.cfg.quads & (1u << q)) g[nq++] = P.quad[q].grad_off;
+  const int64_t total = (int64_t)P.cfg.h * P.cfg.w;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  adj_sum_kernel<AccT><<<blocks, 256, 0, st>>>(wsa, g[0], g[1], g[2], g[3], nq, P.cfg.h, P.cfg.w,
+                                               static_cast<AccT*>(gin), gin_pitch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const DevicePlan& D, const void* gout, void* gin, int64_t gin_pitch, void* ws,
+                           cudaStream_t st) {
+  switch (D.host->cfg.dtype) {
+    case 0:
+    case 1:
+      return launch_adjoint_t<int32_t>(D, gout, gin, gin_pitch, ws, st);
+    case 2:
+      return launch_adjoint_t<float>(D, gout, gin, gin_pitch, ws, st);
+    default:
+      return launch_adjoint_t<double>(D, gout, gin, gin_pitch, ws, st);
+  }
+}
+
+}  // namespace fht

@@ -20,6 +20,7 @@ struct QuadDesc {
   int32_t sigma;      // +1 or -1
   int32_t kappa;      // see above
   int64_t out_off;    // element offset of the quadrant in the output
+  int64_t grad_off;   // adjoint: workspace offset of this quadrant's h x w image gradient
 };
 
 // A subtree of at most F rows, merged entirely in shared memory.
@@ -35,6 +36,8 @@ struct FusedItem {
   int64_t dst;        // element offset of its first row (workspace, or output if final_)
   int32_t dst_pitch;  // elements between rows of dst
   int32_t ntiles;     // column tiles of width tile_cols covering wn
+  int32_t aprog;      // adjoint program: first row pointer (nlev * (m + 1) entries)
+  int32_t antiles;    // adjoint column tiles of width tile_cols covering the view length L
 };
 
 // One row of one level of a fused program: dst row <- src[top] + src[bot] shifted by s.
@@ -63,5 +66,27 @@ struct RowJob {
 };
 
 enum : int32_t { ROW_FINAL = 1, ROW_EXT = 2, ROW_NEG = 4 };
+
+// Adjoint of the upper merges: one child row, gathered from the parent rows
+// that read it in the forward merge (a contiguous range of slopes t, because
+// t -> t1 and t -> t2 are monotone):
+//   dst[i] = sum_k src[t_k][i + e_k],  i in [0, wdst)
+// cyclic: index taken mod W; extended: terms with i + e_k outside [0, wsrc)
+// are zero.  With ROW_FINAL the parent is the root, read from the output
+// gradient through the quadrant's column map  X = (sigma * u + kappa) mod W.
+struct AdjRow {
+  int64_t dst;        // workspace offset of the child row
+  int64_t src;        // offset of the parent's row 0 (workspace, or output gradient if final)
+  int32_t src_pitch;  // elements between parent rows
+  int32_t wdst, wsrc, W;
+  int32_t flags;      // ROW_FINAL: src is the output gradient; ROW_EXT; ROW_NEG
+  int32_t kappa;
+  int32_t term_begin, term_count;
+};
+
+struct AdjTerm {
+  int32_t t;  // parent row
+  int32_t e;  // column offset (reduced to [0, W) in the cyclic case)
+};
 
 }  // namespace fht

@@ -41,7 +41,7 @@ __device__ __forceinline__ AccT view_load(const InT* __restrict__ in, int64_t pi
 }
 
 template <typename InT, typename AccT>
-__global__ void __launch_bounds__(256) fused_kernel(FusedParams p) {
+__global__ void __launch_bounds__(512, 1) fused_kernel(FusedParams p) {
   const FusedItem it = p.items[blockIdx.x];
   const int32_t tile = blockIdx.y;
   if (tile >= it.ntiles) return;
@@ -59,21 +59,31 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedParams p) {
   const int32_t nwarps = blockDim.x >> 5;
 
   // ---- stage the subtree's input rows ----
+  // Loads are issued in batches of U per thread before their shared stores so
+  // that several global loads are in flight per thread.
+  constexpr int U = 8;
   if (!Q.transpose) {
     for (int32_t r = warp; r < m; r += nwarps) {
       AccT* dst = bufA + (size_t)r * p.RP;
       const int32_t row = it.a + r;
-      if (Q.ext) {
-        for (int32_t j = lane; j < TWin; j += 32) {
-          const int32_t z = x0 + j;
-          dst[j] = (z >= 0 && z < Q.L) ? view_load<InT, AccT>(in, p.in_pitch, Q, row, z) : AccT(0);
+      for (int32_t j0 = 0; j0 < TWin; j0 += 32 * U) {
+        AccT v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int32_t j = j0 + u * 32 + lane;
+          int32_t z = x0 + j;
+          bool ok = j < TWin;
+          if (Q.ext) {
+            ok = ok && z >= 0 && z < Q.L;
+          } else if (z >= Q.L) {
+            z = z < 2 * Q.L ? z - Q.L : z % Q.L;  // x0 >= 0 in the cyclic case
+          }
+          v[u] = ok ? view_load<InT, AccT>(in, p.in_pitch, Q, row, z) : AccT(0);
         }
-      } else {
-        int32_t z = (x0 + lane) % Q.L;  // x0 >= 0 in the cyclic case
-        for (int32_t j = lane; j < TWin; j += 32) {
-          dst[j] = view_load<InT, AccT>(in, p.in_pitch, Q, row, z);
-          z += 32;
-          while (z >= Q.L) z -= Q.L;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int32_t j = j0 + u * 32 + lane;
+          if (j < TWin) dst[j] = v[u];
         }
       }
     }
@@ -106,8 +116,10 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedParams p) {
       const AccT* a = src + (size_t)op.top * p.RP;
       if (op.bot >= 0) {
         const AccT* b = src + (size_t)op.bot * p.RP + op.s;
+#pragma unroll 4
         for (int32_t j = lane; j < TWin; j += 32) d[j] = a[j] + b[j];
       } else {
+#pragma unroll 4
         for (int32_t j = lane; j < TWin; j += 32) d[j] = a[j];
       }
     }
@@ -142,42 +154,54 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedParams p) {
 }
 
 template <typename AccT>
+__device__ __forceinline__ void store_row(AccT* dst, const RowJob& J, bool fin, int32_t u, AccT v) {
+  if (fin) {
+    int32_t X = (J.flags & ROW_NEG) ? J.kappa - u : u + J.kappa;
+    if (X < 0) X += J.W;
+    if (X >= J.W) X -= J.W;
+    dst[X] = v;
+  } else {
+    dst[u] = v;
+  }
+}
+
+// One CTA per output row; every thread keeps U independent element pairs in
+// flight (all loads issued before the adds and stores).
+template <typename AccT>
 __global__ void __launch_bounds__(256) upper_kernel(const RowJob* __restrict__ rows, int64_t nrows,
                                                    const AccT* __restrict__ ws_in, AccT* ws_out, AccT* out) {
+  constexpr int U = 8;
   for (int64_t k = blockIdx.x; k < nrows; k += gridDim.x) {
     const RowJob J = rows[k];
     const AccT* __restrict__ top = ws_in + J.top;
     const AccT* __restrict__ bot = ws_in + J.bot;
     const bool fin = J.flags & ROW_FINAL;
+    const bool ext = J.flags & ROW_EXT;
     AccT* dst = (fin ? out : ws_out) + J.dst;
-    if (J.flags & ROW_EXT) {
-      for (int32_t u = threadIdx.x; u < J.wout; u += blockDim.x) {
-        const int32_t i = u + J.dtop, k2 = u + J.dbot;
-        const AccT a = (i >= 0 && i < J.wtop) ? top[i] : AccT(0);
-        const AccT b = (k2 >= 0 && k2 < J.wbot) ? bot[k2] : AccT(0);
-        const AccT v = a + b;
-        if (fin) {
-          int32_t X = (J.flags & ROW_NEG) ? J.kappa - u : u + J.kappa;
-          if (X < 0) X += J.W;
-          if (X >= J.W) X -= J.W;
-          dst[X] = v;
-        } else {
-          dst[u] = v;
+    for (int32_t u0 = 0; u0 < J.wout; u0 += (int32_t)blockDim.x * U) {
+      AccT a[U], b[U];
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const int32_t u = u0 + q * (int32_t)blockDim.x + (int32_t)threadIdx.x;
+        a[q] = AccT(0);
+        b[q] = AccT(0);
+        if (u < J.wout) {
+          if (ext) {
+            const int32_t i = u + J.dtop, i2 = u + J.dbot;
+            if (i >= 0 && i < J.wtop) a[q] = top[i];
+            if (i2 >= 0 && i2 < J.wbot) b[q] = bot[i2];
+          } else {
+            int32_t i2 = u + J.dbot;
+            if (i2 >= J.W) i2 -= J.W;
+            a[q] = top[u];
+            b[q] = bot[i2];
+          }
         }
       }
-    } else {
-      for (int32_t u = threadIdx.x; u < J.wout; u += blockDim.x) {
-        int32_t k2 = u + J.dbot;
-        if (k2 >= J.W) k2 -= J.W;
-        const AccT v = top[u] + bot[k2];
-        if (fin) {
-          int32_t X = (J.flags & ROW_NEG) ? J.kappa - u : u + J.kappa;
-          if (X < 0) X += J.W;
-          if (X >= J.W) X -= J.W;
-          dst[X] = v;
-        } else {
-          dst[u] = v;
-        }
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const int32_t u = u0 + q * (int32_t)blockDim.x + (int32_t)threadIdx.x;
+        if (u < J.wout) store_row(dst, J, fin, u, a[q] + b[q]);
       }
     }
   }

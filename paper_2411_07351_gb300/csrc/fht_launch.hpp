@@ -14,6 +14,10 @@ struct DevicePlan {
   FusedItem* fused = nullptr;
   MergeOp* ops = nullptr;
   RowJob* rows = nullptr;
+  AdjRow* arows = nullptr;
+  AdjTerm* aterms = nullptr;
+  int32_t* aptr = nullptr;
+  MergeOp* aops = nullptr;
   int32_t fused_rp = 0;    // shared row pitch of the fused kernel (elements)
   size_t fused_smem = 0;   // dynamic shared memory of the fused kernel (bytes)
 };
@@ -25,6 +29,13 @@ void fused_geometry(const HostPlan& P, int32_t& rp, size_t& smem);
 // events[2k + 1] are recorded just before and after the k-th kernel launch.
 cudaError_t launch_forward(const DevicePlan& D, const void* in, int64_t in_pitch, void* out, void* ws,
                            cudaStream_t st, cudaEvent_t* events = nullptr);
+
+// Shared-memory geometry of the fused adjoint kernel.
+void adjoint_geometry(const HostPlan& P, int32_t& rp, int32_t& padl, size_t& smem);
+
+// Enqueues the adjoint: gin (h x w, pitch gin_pitch) = transpose of the forward applied to gout.
+cudaError_t launch_adjoint(const DevicePlan& D, const void* gout, void* gin, int64_t gin_pitch, void* ws,
+                           cudaStream_t st);
 
 // Kernel launches of one forward transform, and the kind of launch k
 // (0: fused pass, 1: upper pass) with its model bytes.

@@ -109,6 +109,27 @@ static void build_program(const Tree& tr, int32_t r, std::vector<MergeOp>& ops, 
   }
 }
 
+// Adjoint of a fused program: for each level and each source row k, the
+// forward outputs that read it, as a CSR list of (forward dst row r, shift s):
+// the gradient of k at column j gathers the gradient of r at column j - s.
+static void build_adjoint_program(const std::vector<MergeOp>& ops, int32_t prog, int32_t nlev, int32_t m,
+                                  std::vector<int32_t>& aptr, std::vector<MergeOp>& aops, int32_t& aoff) {
+  aoff = (int32_t)aptr.size();
+  for (int32_t lev = 0; lev < nlev; lev++) {
+    std::vector<std::vector<MergeOp>> by_src(m);
+    for (int32_t r = 0; r < m; r++) {
+      const MergeOp& op = ops[(size_t)prog + (size_t)lev * m + r];
+      by_src[op.top].push_back(MergeOp{(int16_t)r, 0, 0, 0});
+      if (op.bot >= 0) by_src[op.bot].push_back(MergeOp{(int16_t)r, 0, op.s, 0});
+    }
+    for (int32_t k = 0; k < m; k++) {
+      aptr.push_back((int32_t)aops.size());
+      for (const MergeOp& t : by_src[k]) aops.push_back(t);
+    }
+    aptr.push_back((int32_t)aops.size());  // end of this level's last row
+  }
+}
+
 static int32_t dtype_in_size(int32_t dt) { return dt == 0 ? 1 : dt == 3 ? 8 : 4; }
 static int32_t dtype_acc_size(int32_t dt) { return dt == 3 ? 8 : 4; }
 
@@ -138,6 +159,9 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
   }
 
   std::map<int32_t, std::pair<int32_t, int32_t>> prog_cache;  // fused root size -> (prog offset, nlev)
+  std::map<int32_t, int32_t> aprog_cache;                       // fused root size -> adjoint ptr offset
+  std::vector<std::vector<AdjRow>> apasses;                     // by height
+  std::vector<std::vector<AdjTerm>> aterms_by_h;
   int64_t out_off = 0;
   int64_t ws_off = 0;  // elements of the accumulator type after the header
   std::vector<std::vector<RowJob>> passes;
@@ -228,7 +252,16 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
         build_program(tr, i, P.ops, nlev);
         it = prog_cache.emplace(nd.m, std::make_pair(off, nlev)).first;
       }
+      auto ait = aprog_cache.find(nd.m);
+      if (ait == aprog_cache.end()) {
+        int32_t aoff = 0;
+        build_adjoint_program(P.ops, it->second.first, it->second.second, nd.m, P.aptr, P.aops, aoff);
+        ait = aprog_cache.emplace(nd.m, aoff).first;
+      }
       FusedItem fi;
+      fi.aprog = ait->second;
+      fi.antiles = (Q.L + cfg.TW - 1) / cfg.TW;
+      P.max_antiles = std::max(P.max_antiles, fi.antiles);
       fi.q = q;
       fi.a = nd.a;
       fi.m = nd.m;
@@ -289,6 +322,41 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
         passes[nd.height].push_back(rj);
       }
       bytes_by_height[nd.height] += ((int64_t)c0.m * wtop + (int64_t)c1.m * wbot + (int64_t)nd.m * wout) * acc;
+      // adjoint: each child row gathers the parent rows that read it
+      if ((int32_t)apasses.size() <= nd.height) {
+        apasses.resize(nd.height + 1);
+        aterms_by_h.resize(nd.height + 1);
+      }
+      for (int c = 0; c < 2; c++) {
+        const TreeNode& ch = c == 0 ? c0 : c1;
+        std::vector<std::vector<AdjTerm>> lists(ch.m);
+        for (int32_t t = 0; t < nd.m; t++) {
+          int32_t t1, t2, s;
+          merge_entry(nd.m, c0.m, c1.m, t, t1, t2, s);
+          int32_t e;
+          if (c == 0) {
+            e = cfg.ext ? c1.m : 0;  // -dtop
+          } else {
+            e = cfg.ext ? c0.m - s : (int32_t)(((int64_t)Q.W - s % Q.W) % Q.W);  // -dbot
+          }
+          lists[c == 0 ? t1 : t2].push_back(AdjTerm{t, e});
+        }
+        for (int32_t r = 0; r < ch.m; r++) {
+          AdjRow ar;
+          ar.dst = buf_row(ch.buf, ch.a + r);
+          ar.src = fin ? Q.out_off : buf_row(nd.buf, nd.a);
+          ar.src_pitch = fin ? Q.W : pitch;
+          ar.wdst = c == 0 ? wtop : wbot;
+          ar.wsrc = wout;
+          ar.W = Q.W;
+          ar.flags = (fin ? ROW_FINAL : 0) | (cfg.ext ? ROW_EXT : 0) | (Q.sigma < 0 ? ROW_NEG : 0);
+          ar.kappa = Q.kappa;
+          ar.term_begin = (int32_t)aterms_by_h[nd.height].size();  // rebased when passes are flattened
+          ar.term_count = (int32_t)lists[r].size();
+          for (const AdjTerm& at : lists[r]) aterms_by_h[nd.height].push_back(at);
+          apasses[nd.height].push_back(ar);
+        }
+      }
     }
     // additions (Theorem 1): every merged element of every internal node is one addition
     for (const TreeNode& nd : tr.nodes)
@@ -297,6 +365,29 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
   }
   P.out_elems = out_off;
   P.ws_bytes = kWsHeader + (size_t)ws_off * acc;
+  // adjoint: one h x w gradient image per quadrant after the forward buffers
+  int64_t goff = ws_off;
+  for (int q = 0; q < 4; q++) {
+    if (!(cfg.quads & (1u << q))) continue;
+    P.quad[q].grad_off = goff;
+    goff += (int64_t)cfg.h * cfg.w;
+  }
+  P.adj_ws_bytes = kWsHeader + (size_t)goff * acc;
+  // adjoint passes: highest tree height first
+  P.apass_begin.push_back(0);
+  for (size_t k = apasses.size(); k-- > 0;) {
+    if (apasses[k].empty()) continue;
+    const int32_t base = (int32_t)P.aterms.size();
+    for (AdjRow ar : apasses[k]) {
+      ar.term_begin += base;
+      P.arows.push_back(ar);
+    }
+    P.aterms.insert(P.aterms.end(), aterms_by_h[k].begin(), aterms_by_h[k].end());
+    P.apass_begin.push_back((int64_t)P.arows.size());
+  }
+  if (P.aterms.empty()) P.aterms.push_back(AdjTerm{0, 0});
+  if (P.aops.empty()) P.aops.push_back(MergeOp{0, 0, 0, 0});
+  if (P.aptr.empty()) P.aptr.push_back(0);
   // flatten passes (skip empty heights)
   P.pass_begin.push_back(0);
   P.model_bytes = P.fused_bytes;

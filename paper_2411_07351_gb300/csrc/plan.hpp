@@ -67,6 +67,14 @@ struct HostPlan {
   std::vector<int64_t> pass_begin;   // rows[pass_begin[p] .. pass_begin[p+1])
   std::vector<int64_t> pass_bytes;   // model bytes of each upper pass
   int64_t fused_bytes = 0;           // model bytes of the fused pass
+  // adjoint
+  std::vector<AdjRow> arows;         // all adjoint upper passes, highest first
+  std::vector<AdjTerm> aterms;
+  std::vector<int64_t> apass_begin;  // arows[apass_begin[p] .. apass_begin[p+1])
+  std::vector<int32_t> aptr;         // fused adjoint programs: CSR row pointers into aops
+  std::vector<MergeOp> aops;         // (top = forward dst row r, s = shift): g[k][j] += g'[r][j - s]
+  size_t adj_ws_bytes = 0;
+  int32_t max_antiles = 0;
   int32_t max_ntiles = 0;
   int32_t max_fused_m = 1;
   int32_t max_fused_shift = 0;        // largest shift s of any fused merge
@@ -79,7 +87,7 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& out);
 // Verifies, on the host, that every memory access the kernels derive from the
 // plan's tables stays inside its buffer (input, workspace, output, shared
 // window).  Returns "" or the first violation.
-std::string check_plan(const HostPlan& P, int32_t fused_rp);
+std::string check_plan(const HostPlan& P, int32_t fused_rp, int32_t adj_rp, int32_t adj_padl);
 
 // Bytes of the status header at the start of every workspace.
 constexpr size_t kWsHeader = 256;

@@ -12,7 +12,7 @@ namespace fht {
 
 static std::string at(const char* what, int64_t i) { return std::string(what) + " #" + std::to_string(i) + ": "; }
 
-std::string check_plan(const HostPlan& P, int32_t fused_rp) {
+std::string check_plan(const HostPlan& P, int32_t fused_rp, int32_t adj_rp, int32_t adj_padl) {
   const int64_t ws_elems = (int64_t)((P.ws_bytes - kWsHeader) / P.acc_size);
   const int64_t out_elems = P.out_elems;
   const int32_t TW = P.cfg.TW;
@@ -82,6 +82,62 @@ std::string check_plan(const HostPlan& P, int32_t fused_rp) {
         }
       } else {
         if (J.dst < 0 || J.dst + J.wout > ws_elems) return at("row", k) + "store outside the workspace";
+      }
+    }
+  }
+  // ---- adjoint ----
+  const int64_t adj_elems = (int64_t)((P.adj_ws_bytes - kWsHeader) / P.acc_size);
+  const int64_t img = (int64_t)P.cfg.h * P.cfg.w;
+  for (int q = 0; q < 4; q++) {
+    if (!(P.cfg.quads & (1u << q))) continue;
+    // gradient images sit after the forward buffers
+    if (P.quad[q].grad_off < ws_elems) return "adjoint gradient image overlaps the forward buffers";
+    if (P.quad[q].grad_off + img > adj_elems) return "adjoint gradient image outside the workspace";
+  }
+  for (size_t k = 0; k < P.fused.size(); k++) {
+    const FusedItem& it = P.fused[k];
+    const QuadDesc& Q = P.quad[it.q];
+    if (it.antiles < 1 || (int64_t)(it.antiles - 1) * TW >= Q.L || (int64_t)it.antiles * TW < Q.L)
+      return at("adjoint fused", k) + "tiles do not cover the view length";
+    if (it.antiles > P.max_antiles) return at("adjoint fused", k) + "more tiles than the grid";
+    const int32_t TZin = TW + it.m - 1;
+    if (adj_padl + TZin > adj_rp) return at("adjoint fused", k) + "window wider than the shared row";
+    if (it.aprog < 0 || (size_t)it.aprog + (size_t)it.nlev * (it.m + 1) > P.aptr.size())
+      return at("adjoint fused", k) + "program pointers";
+    for (int32_t l = 0; l < it.nlev; l++)
+      for (int32_t r = 0; r <= it.m; r++) {
+        const int32_t v = P.aptr[(size_t)it.aprog + (size_t)l * (it.m + 1) + r];
+        if (v < 0 || (size_t)v > P.aops.size()) return at("adjoint fused", k) + "program terms";
+        if (r < it.m) {
+          const int32_t e = P.aptr[(size_t)it.aprog + (size_t)l * (it.m + 1) + r + 1];
+          for (int32_t t = v; t < e; t++) {
+            const MergeOp& op = P.aops[t];
+            if (op.top < 0 || op.top >= it.m || op.s < 0 || op.s > adj_padl)
+              return at("adjoint fused", k) + "term outside the shared window";
+          }
+        }
+      }
+  }
+  for (size_t p = 0; p + 1 < P.apass_begin.size(); p++) {
+    std::set<int64_t> written;
+    for (int64_t k = P.apass_begin[p]; k < P.apass_begin[p + 1]; k++) written.insert(P.arows[k].dst);
+    for (int64_t k = P.apass_begin[p]; k < P.apass_begin[p + 1]; k++) {
+      const AdjRow& R = P.arows[k];
+      const bool fin = R.flags & ROW_FINAL, ext = R.flags & ROW_EXT;
+      if (R.dst < 0 || R.dst + R.wdst > ws_elems) return at("adjoint row", k) + "store outside the workspace";
+      if (R.term_begin < 0 || (size_t)R.term_begin + R.term_count > P.aterms.size())
+        return at("adjoint row", k) + "terms";
+      for (int32_t c = 0; c < R.term_count; c++) {
+        const AdjTerm& T = P.aterms[R.term_begin + c];
+        if (!ext && (T.e < 0 || T.e >= R.W || R.wdst != R.W || R.wsrc != R.W))
+          return at("adjoint row", k) + "cyclic offset not reduced";
+        const int64_t row = R.src + (int64_t)T.t * R.src_pitch;
+        if (fin) {
+          if (R.src_pitch != R.W || row < 0 || row + R.W > out_elems) return at("adjoint row", k) + "source outside the output";
+        } else {
+          if (row < 0 || row + R.wsrc > ws_elems) return at("adjoint row", k) + "source outside the workspace";
+          if (written.count(row)) return at("adjoint row", k) + "reads a row written in the same pass";
+        }
       }
     }
   }

@@ -61,6 +61,7 @@ class Plan:
         self.info = info
         self.out_elems = int(info.out_elems)
         self.workspace_bytes = int(info.workspace_bytes)
+        self.adjoint_workspace_bytes = int(info.adjoint_workspace_bytes)
         self.shapes = [(int(info.rows[q]), int(info.cols[q])) for q in range(4) if self.quads & (1 << q)]
         self.offsets = [int(info.out_offset[q]) for q in range(4) if self.quads & (1 << q)]
 
@@ -71,9 +72,10 @@ class Plan:
     def check(self):
         C.check(self._lib.fht_plan_check(self._h), "fht_plan_check")
 
-    def new_workspace(self) -> torch.Tensor:
+    def new_workspace(self, adjoint: bool = False) -> torch.Tensor:
         # 256-byte alignment: the caching allocator returns 512-byte aligned blocks
-        return torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
+        nbytes = self.adjoint_workspace_bytes if adjoint else self.workspace_bytes
+        return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
 
     def new_output(self) -> torch.Tensor:
         return torch.empty(self.out_elems, dtype=self.out_dtype, device=self.device)
@@ -104,7 +106,7 @@ class Plan:
         if gin is None:
             gin = torch.empty((self.h, self.w), dtype=self.out_dtype, device=self.device)
         if ws is None:
-            ws = self.new_workspace()
+            ws = self.new_workspace(adjoint=True)
         C.check(self._lib.fht_adjoint(self._h, gout.data_ptr(), gin.data_ptr(), gin.stride(0), ws.data_ptr(),
                                       ws.numel() * ws.element_size(), _stream_handle(gout.device, stream)),
                 "fht_adjoint")
