@@ -146,8 +146,8 @@ class PlanCache:
         with self._lock:
             self._d[key] = p
             while len(self._d) > self.capacity:
-                _, old = self._d.popitem(last=False)
-                old.close()
+                # dropped, not closed: autograd graphs may still hold the plan
+                self._d.popitem(last=False)
         return p
 
 
