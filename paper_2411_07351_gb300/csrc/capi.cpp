@@ -86,7 +86,7 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
   cfg.ext = (int32_t)boundary;
   cfg.split = split == FHT_SPLIT_S ? fht::Split::S : fht::Split::T;
   cfg.F = 64;
-  cfg.TW = dtype == FHT_F64_F64 ? 64 : 256;
+  cfg.TW = dtype == FHT_F64_F64 ? 64 : 128;
   cfg.threads = 512;
   if (tuning) {
     if (tuning->fused_rows) cfg.F = tuning->fused_rows;
@@ -109,7 +109,7 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
   }
   p->dev.host = &p->host;
   p->dev.device = device;
-  fht::fused_geometry(p->host, p->dev.fused_rp, p->dev.fused_smem);
+  fht::fused_geometry(p->host, p->dev.geo);
   if (device < 0) {  // host-only plan: tables and sizes for inspection, no device copy
     *out = p;
     return FHT_OK;
@@ -129,8 +129,8 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
     int32_t arp = 0, apad = 0;
     size_t asmem = 0;
     fht::adjoint_geometry(p->host, arp, apad, asmem);
-    if ((size_t)max_smem < std::max(p->dev.fused_smem, asmem)) {
-      const std::string need = std::to_string(p->dev.fused_smem);
+    if ((size_t)max_smem < std::max(p->dev.geo.smem, asmem)) {
+      const std::string need = std::to_string(std::max(p->dev.geo.smem, asmem));
       delete p;
       return fail(FHT_ERR_INVALID,
                   "fht_plan: fused tile needs " + need + " bytes of shared memory; lower tile_cols or fused_rows");
@@ -250,7 +250,7 @@ fht_status fht_plan_check(fht_plan_t plan) {
   int32_t arp = 0, apad = 0;
   size_t asmem = 0;
   fht::adjoint_geometry(plan->host, arp, apad, asmem);
-  std::string err = fht::check_plan(plan->host, plan->dev.fused_rp, arp, apad);
+  std::string err = fht::check_plan(plan->host, plan->dev.geo, arp, apad);
   if (!err.empty()) return fail(FHT_ERR_INVALID, "fht_plan_check: " + err);
   return FHT_OK;
 }

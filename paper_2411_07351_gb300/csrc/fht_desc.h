@@ -38,7 +38,11 @@ struct FusedItem {
   int32_t ntiles;     // column tiles of width tile_cols covering wn
   int32_t aprog;      // adjoint program: first row pointer (nlev * (m + 1) entries)
   int32_t antiles;    // adjoint column tiles of width tile_cols covering the view length L
+  int32_t kind;       // 0: generic program; 1: perfect 64-row Brady-Yong block (fast path)
+  int32_t tw;         // column tile of this item (forward)
 };
+
+enum : int32_t { FUSED_GENERIC = 0, FUSED_BY64 = 1 };
 
 // One row of one level of a fused program: dst row <- src[top] + src[bot] shifted by s.
 // bot < 0 means the row is carried unchanged to the next level.

@@ -26,9 +26,10 @@ struct FusedParams {
   const FusedItem* items;
   const MergeOp* ops;
   QuadDesc quad[4];
-  int32_t TW;
-  int32_t RP;  // shared row pitch (elements)
-  int32_t Fm;  // rows per shared buffer
+  int32_t RP;  // generic path: shared row pitch (elements)
+  int32_t Fm;  // generic path: rows per shared buffer
+  int32_t RS;  // fast path: pitch of the staged input / level-4 rows
+  int32_t RA;  // fast path: pitch of the level-2 rows
 };
 
 template <typename InT, typename AccT>
@@ -40,39 +41,28 @@ __device__ __forceinline__ AccT view_load(const InT* __restrict__ in, int64_t pi
   return (AccT)v;
 }
 
+// Stage m view rows [a, a + m) x window columns [x0, x0 + width) into
+// buf (row pitch rp): wrapped (cyclic) or zero-filled (extended).  Loads are
+// issued in batches of U per thread before their shared stores so that several
+// global loads are in flight per thread.
 template <typename InT, typename AccT>
-__global__ void __launch_bounds__(512, 1) fused_kernel(FusedParams p) {
-  const FusedItem it = p.items[blockIdx.x];
-  const int32_t tile = blockIdx.y;
-  if (tile >= it.ntiles) return;
-  const QuadDesc& Q = p.quad[it.q];
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  AccT* bufA = reinterpret_cast<AccT*>(smem_raw);
-  AccT* bufB = bufA + (size_t)p.Fm * p.RP;
+__device__ __forceinline__ void stage_rows(const FusedParams& p, const QuadDesc& Q, int32_t a, int32_t m, int32_t x0,
+                                           int32_t width, AccT* buf, int32_t rp) {
   const InT* __restrict__ in = static_cast<const InT*>(p.in);
-
-  const int32_t m = it.m;
-  const int32_t TWin = p.TW + m - 1;
-  const int32_t u0 = tile * p.TW;
-  const int32_t x0 = u0 - it.c;  // first window column in view coordinates
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t nwarps = blockDim.x >> 5;
-
-  // ---- stage the subtree's input rows ----
-  // Loads are issued in batches of U per thread before their shared stores so
-  // that several global loads are in flight per thread.
   constexpr int U = 8;
   if (!Q.transpose) {
     for (int32_t r = warp; r < m; r += nwarps) {
-      AccT* dst = bufA + (size_t)r * p.RP;
-      const int32_t row = it.a + r;
-      for (int32_t j0 = 0; j0 < TWin; j0 += 32 * U) {
+      AccT* dst = buf + (size_t)r * rp;
+      const int32_t row = a + r;
+      for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
         AccT v[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
           const int32_t j = j0 + u * 32 + lane;
           int32_t z = x0 + j;
-          bool ok = j < TWin;
+          bool ok = j < width;
           if (Q.ext) {
             ok = ok && z >= 0 && z < Q.L;
           } else if (z >= Q.L) {
@@ -83,14 +73,14 @@ __global__ void __launch_bounds__(512, 1) fused_kernel(FusedParams p) {
 #pragma unroll
         for (int u = 0; u < U; u++) {
           const int32_t j = j0 + u * 32 + lane;
-          if (j < TWin) dst[j] = v[u];
+          if (j < width) dst[j] = v[u];
         }
       }
     }
   } else {
     // transposed view: view row r is image column a + r; lanes run along r so
     // that a warp reads consecutive image columns of one image row.
-    for (int32_t j = warp; j < TWin; j += nwarps) {
+    for (int32_t j = warp; j < width; j += nwarps) {
       int32_t z = x0 + j;
       bool valid = true;
       if (Q.ext) {
@@ -99,11 +89,51 @@ __global__ void __launch_bounds__(512, 1) fused_kernel(FusedParams p) {
         z %= Q.L;
       }
       for (int32_t r = lane; r < m; r += 32)
-        bufA[(size_t)r * p.RP + j] = valid ? view_load<InT, AccT>(in, p.in_pitch, Q, it.a + r, z) : AccT(0);
+        buf[(size_t)r * rp + j] = valid ? view_load<InT, AccT>(in, p.in_pitch, Q, a + r, z) : AccT(0);
     }
   }
+}
 
-  // ---- merges, level by level (Algorithm 1's merge on the shared window) ----
+// Store rows [0, m) x columns [0, ncols) of a shared buffer as the node's
+// Hough rows starting at node column u0.
+template <typename AccT>
+__device__ __forceinline__ void store_rows(const FusedParams& p, const FusedItem& it, const QuadDesc& Q,
+                                           const AccT* buf, int32_t rp, int32_t u0, int32_t ncols) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  if (!it.final_) {
+    AccT* __restrict__ ws = static_cast<AccT*>(p.ws) + it.dst;
+    for (int32_t r = warp; r < it.m; r += nwarps) {
+      const AccT* s = buf + (size_t)r * rp;
+      AccT* o = ws + (int64_t)r * it.dst_pitch + u0;
+      for (int32_t j = lane; j < ncols; j += 32) o[j] = s[j];
+    }
+  } else {
+    AccT* __restrict__ out = static_cast<AccT*>(p.out) + it.dst;
+    for (int32_t r = warp; r < it.m; r += nwarps) {
+      const AccT* s = buf + (size_t)r * rp;
+      AccT* o = out + (int64_t)r * it.dst_pitch;
+      for (int32_t j = lane; j < ncols; j += 32) {
+        int32_t X = Q.sigma * (u0 + j) + Q.kappa;
+        if (X < 0) X += Q.W;
+        if (X >= Q.W) X -= Q.W;
+        o[X] = s[j];
+      }
+    }
+  }
+}
+
+// Generic path: any subtree of at most F rows, run level by level from its
+// program, ping-ponging between two shared buffers.
+template <typename InT, typename AccT>
+__device__ void fused_generic(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile,
+                              AccT* bufA, AccT* bufB) {
+  const int32_t m = it.m;
+  const int32_t TWin = it.tw + m - 1;
+  const int32_t u0 = tile * it.tw;
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  stage_rows<InT, AccT>(p, Q, it.a, m, u0 - it.c, TWin, bufA, p.RP);
   AccT* src = bufA;
   AccT* dst = bufB;
   const MergeOp* prog = p.ops + it.prog;
@@ -128,28 +158,109 @@ __global__ void __launch_bounds__(512, 1) fused_kernel(FusedParams p) {
     dst = tmp;
   }
   __syncthreads();
+  store_rows<AccT>(p, it, Q, src, p.RP, u0, min(it.tw, it.wn - u0));
+}
 
-  // ---- store the subtree's Hough rows (columns [u0, u0 + TW) of the node) ----
-  const int32_t ncols = min(p.TW, it.wn - u0);
-  if (!it.final_) {
-    AccT* __restrict__ ws = static_cast<AccT*>(p.ws) + it.dst;
-    for (int32_t r = warp; r < m; r += nwarps) {
-      const AccT* s = src + (size_t)r * p.RP;
-      AccT* o = ws + (int64_t)r * it.dst_pitch + u0;
-      for (int32_t j = lane; j < ncols; j += 32) o[j] = s[j];
+// Two Brady-Yong levels at once: four m-row blocks Q0..Q3 (rows base + e m)
+// become one 4m-row block.  With t'' = k and t = 4k + i, level by level
+// (t' = floor(t/2), child slopes floor(t'/2), shifts ceil(t'/2), ceil(t/2)):
+//   out[4k+i][j] = Q0[k][j] + Q1[k][j + k + b] + Q2[k][j + 2k + c]
+//                + Q3[k][j + 3k + b + c],   b = floor(i/2), c = ceil(i/2),
+// so the four outputs of one k need only ten shifted reads.  `rq` = g m + k
+// indexes the 16 (block group, k) pairs of a 64-row block.
+template <typename AccT>
+__device__ __forceinline__ void merge4_row(const AccT* src, int32_t rs, int32_t m, int32_t rq, int32_t j,
+                                           AccT o[4]) {
+  const int32_t g = rq / m, k = rq - (rq / m) * m;
+  const AccT* q0 = src + (size_t)(g * 4 * m + k) * rs + j;
+  const AccT* q1 = q0 + (size_t)m * rs + k;
+  const AccT* q2 = q0 + (size_t)2 * m * rs + 2 * k;
+  const AccT* q3 = q0 + (size_t)3 * m * rs + 3 * k;
+  const AccT a0 = q0[0];
+  const AccT b0 = q1[0], b1 = q1[1];
+  const AccT c0 = q2[0], c1 = q2[1], c2 = q2[2];
+  const AccT d0 = q3[0], d1 = q3[1], d2 = q3[2], d3 = q3[3];
+  o[0] = (a0 + b0) + (c0 + d0);
+  o[1] = (a0 + b0) + (c1 + d1);
+  o[2] = (a0 + b1) + (c1 + d2);
+  o[3] = (a0 + b1) + (c2 + d3);
+}
+
+template <typename AccT>
+__device__ __forceinline__ void merge4_pass(const AccT* src, int32_t rs, AccT* dst, int32_t rd, int32_t m,
+                                            int32_t width) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  for (int32_t rq = warp; rq < 16; rq += nwarps) {
+    const int32_t g = rq / m, k = rq - g * m;
+    AccT* d = dst + (size_t)(g * 4 * m + 4 * k) * rd;
+    for (int32_t j = lane; j < width; j += 32) {
+      AccT o[4];
+      merge4_row<AccT>(src, rs, m, rq, j, o);
+      d[j] = o[0];
+      d[rd + j] = o[1];
+      d[2 * rd + j] = o[2];
+      d[3 * rd + j] = o[3];
     }
-  } else {
-    AccT* __restrict__ out = static_cast<AccT*>(p.out) + it.dst;
-    for (int32_t r = warp; r < m; r += nwarps) {
-      const AccT* s = src + (size_t)r * p.RP;
-      AccT* o = out + (int64_t)r * it.dst_pitch;
-      for (int32_t j = lane; j < ncols; j += 32) {
+  }
+}
+
+// Fast path: a perfect 64-row Brady-Yong block in three two-level passes.
+// Widths: the last pass needs TW columns of the level-4 rows plus the largest
+// level-5/6 shift (48), the middle pass TW + 48 plus 12, the first TW + 60
+// plus 3 = the staged window TW + 63.
+template <typename InT, typename AccT>
+__device__ void fused_by64(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile, AccT* S,
+                           AccT* A) {
+  const int32_t TW = it.tw;
+  const int32_t u0 = tile * TW;
+  stage_rows<InT, AccT>(p, Q, it.a, 64, u0 - it.c, TW + 63, S, p.RS);
+  __syncthreads();
+  merge4_pass<AccT>(S, p.RS, A, p.RA, 1, TW + 60);  // levels 1-2
+  __syncthreads();
+  merge4_pass<AccT>(A, p.RA, S, p.RS, 4, TW + 48);  // levels 3-4
+  __syncthreads();
+  // levels 5-6 straight from registers to global memory
+  const int32_t ncols = min(TW, it.wn - u0);
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  AccT* __restrict__ base = (it.final_ ? static_cast<AccT*>(p.out) : static_cast<AccT*>(p.ws)) + it.dst;
+  for (int32_t k = warp; k < 16; k += nwarps) {
+    AccT* o = base + (int64_t)(4 * k) * it.dst_pitch;
+    for (int32_t j = lane; j < ncols; j += 32) {
+      AccT v[4];
+      merge4_row<AccT>(S, p.RS, 16, k, j, v);
+      if (!it.final_) {
+        const int32_t u = u0 + j;
+        o[u] = v[0];
+        o[it.dst_pitch + u] = v[1];
+        o[2 * (int64_t)it.dst_pitch + u] = v[2];
+        o[3 * (int64_t)it.dst_pitch + u] = v[3];
+      } else {
         int32_t X = Q.sigma * (u0 + j) + Q.kappa;
         if (X < 0) X += Q.W;
         if (X >= Q.W) X -= Q.W;
-        o[X] = s[j];
+        o[X] = v[0];
+        o[it.dst_pitch + X] = v[1];
+        o[2 * (int64_t)it.dst_pitch + X] = v[2];
+        o[3 * (int64_t)it.dst_pitch + X] = v[3];
       }
     }
+  }
+}
+
+template <typename InT, typename AccT>
+__global__ void __launch_bounds__(512, 2) fused_kernel(FusedParams p) {
+  const FusedItem it = p.items[blockIdx.x];
+  const int32_t tile = blockIdx.y;
+  if (tile >= it.ntiles) return;
+  const QuadDesc& Q = p.quad[it.q];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AccT* sm = reinterpret_cast<AccT*>(smem_raw);
+  if (it.kind == FUSED_BY64) {
+    fused_by64<InT, AccT>(p, it, Q, tile, sm, sm + (size_t)64 * p.RS);
+  } else {
+    fused_generic<InT, AccT>(p, it, Q, tile, sm, sm + (size_t)p.Fm * p.RP);
   }
 }
 
@@ -210,12 +321,19 @@ __global__ void __launch_bounds__(256) upper_kernel(const RowJob* __restrict__ r
 // ------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------
-void fused_geometry(const HostPlan& P, int32_t& rp, size_t& smem) {
-  // a window of TW + m - 1 columns, plus room for the largest shifted read
-  const int32_t Fm = P.max_fused_m;
-  rp = P.cfg.TW + Fm - 1 + P.max_fused_shift;
-  if (rp % 2 == 0) rp++;  // odd pitch: column-wise (transposed) staging is conflict-free
-  smem = (size_t)2 * Fm * rp * P.acc_size;
+void fused_geometry(const HostPlan& P, FusedGeometry& g) {
+  // generic path: a window of tw + m - 1 columns plus room for the largest shifted read
+  g.Fm = std::max(P.max_generic_m, 1);
+  g.RP = P.generic_tw + g.Fm - 1 + P.generic_shift;
+  if (g.RP % 2 == 0) g.RP++;  // odd pitch: column-wise (transposed) staging is conflict-free
+  size_t generic = P.max_generic_m > 0 ? (size_t)2 * g.Fm * g.RP * P.acc_size : 0;
+  // fast path: staged rows (TW + 63) and level-2 rows (TW + 60)
+  g.RS = P.cfg.TW + 63;
+  if (g.RS % 2 == 0) g.RS++;
+  g.RA = P.cfg.TW + 60;
+  if (g.RA % 2 == 0) g.RA++;
+  size_t by64 = P.n_by64 > 0 ? (size_t)64 * (g.RS + g.RA) * P.acc_size : 0;
+  g.smem = std::max(generic, by64);
 }
 
 int32_t forward_launches(const HostPlan& P) { return 1 + (int32_t)P.pass_bytes.size(); }
@@ -247,10 +365,11 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
   fp.items = D.fused;
   fp.ops = D.ops;
   for (int q = 0; q < 4; q++) fp.quad[q] = P.quad[q];
-  fp.TW = P.cfg.TW;
-  fp.RP = D.fused_rp;
-  fp.Fm = P.max_fused_m;
-  const size_t smem = D.fused_smem;
+  fp.RP = D.geo.RP;
+  fp.Fm = D.geo.Fm;
+  fp.RS = D.geo.RS;
+  fp.RA = D.geo.RA;
+  const size_t smem = D.geo.smem;
   auto kfn = fused_kernel<InT, AccT>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -8,6 +8,13 @@
 
 namespace fht {
 
+// Shared-memory geometry of the fused forward kernel.
+struct FusedGeometry {
+  int32_t RP = 0, Fm = 1;  // generic path: row pitch and rows per buffer
+  int32_t RS = 0, RA = 0;  // 64-row fast path: pitches of the two buffers
+  size_t smem = 0;         // dynamic shared memory (bytes)
+};
+
 struct DevicePlan {
   const HostPlan* host = nullptr;
   int device = 0;
@@ -18,12 +25,10 @@ struct DevicePlan {
   AdjTerm* aterms = nullptr;
   int32_t* aptr = nullptr;
   MergeOp* aops = nullptr;
-  int32_t fused_rp = 0;    // shared row pitch of the fused kernel (elements)
-  size_t fused_smem = 0;   // dynamic shared memory of the fused kernel (bytes)
+  FusedGeometry geo;
 };
 
-// Shared-memory geometry of the fused kernel for a plan.
-void fused_geometry(const HostPlan& P, int32_t& rp, size_t& smem);
+void fused_geometry(const HostPlan& P, FusedGeometry& g);
 
 // Enqueues the forward transform.  When `events` is non-null, events[2k] and
 // events[2k + 1] are recorded just before and after the k-th kernel launch.

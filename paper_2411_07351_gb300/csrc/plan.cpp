@@ -277,8 +277,10 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
         fi.dst = buf_row(nd.buf, nd.a);
         fi.dst_pitch = pitch;
       }
-      fi.ntiles = (fi.wn + cfg.TW - 1) / cfg.TW;
-      P.max_ntiles = std::max(P.max_ntiles, fi.ntiles);
+      // a 64-row subtree is a perfect Brady-Yong block under both split rules
+      fi.kind = nd.m == 64 ? FUSED_BY64 : FUSED_GENERIC;
+      fi.tw = 0;  // set once all items are known
+      fi.ntiles = 0;
       P.max_fused_m = std::max(P.max_fused_m, nd.m);
       P.fused.push_back(fi);
       // model bytes: the subtree's input rows once, its Hough rows once
@@ -363,6 +365,26 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
       if (nd.m > 1) P.adds += (int64_t)nd.m * (cfg.ext ? Q.L + nd.m - 1 : Q.W);
     P.ideal_bytes += (int64_t)Q.n * Q.L * P.in_size + qsize * acc;
   }
+  // tiles: fast-path items use tile_cols; generic items use half of it when
+  // both kinds share the launch, so that their shared windows stay smaller
+  for (const FusedItem& fi : P.fused) P.n_by64 += fi.kind == FUSED_BY64;
+  P.generic_tw = (P.n_by64 > 0) ? std::max(32, cfg.TW / 64 * 32) : cfg.TW;
+  for (FusedItem& fi : P.fused) {
+    fi.tw = fi.kind == FUSED_BY64 ? cfg.TW : P.generic_tw;
+    fi.ntiles = (fi.wn + fi.tw - 1) / fi.tw;
+    P.max_ntiles = std::max(P.max_ntiles, fi.ntiles);
+    if (fi.kind == FUSED_GENERIC) {
+      P.max_generic_m = std::max(P.max_generic_m, fi.m);
+      for (int32_t l = 0; l < fi.nlev; l++)
+        for (int32_t r = 0; r < fi.m; r++) {
+          const MergeOp& op = P.ops[(size_t)fi.prog + (size_t)l * fi.m + r];
+          if (op.bot >= 0) P.generic_shift = std::max<int32_t>(P.generic_shift, op.s);
+        }
+    }
+  }
+  // generic items first: they are few and slower, so they start in the first wave
+  std::stable_sort(P.fused.begin(), P.fused.end(),
+                   [](const FusedItem& x, const FusedItem& y) { return x.kind < y.kind; });
   P.out_elems = out_off;
   P.ws_bytes = kWsHeader + (size_t)ws_off * acc;
   // adjoint: one h x w gradient image per quadrant after the forward buffers

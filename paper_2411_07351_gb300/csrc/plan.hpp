@@ -78,6 +78,10 @@ struct HostPlan {
   int32_t max_ntiles = 0;
   int32_t max_fused_m = 1;
   int32_t max_fused_shift = 0;        // largest shift s of any fused merge
+  int32_t max_generic_m = 0;          // tallest subtree on the generic fused path (0: none)
+  int32_t generic_shift = 0;          // largest shift of a generic fused merge
+  int32_t generic_tw = 0;             // column tile of generic fused items
+  int32_t n_by64 = 0;                 // fused items on the 64-row Brady-Yong fast path
   int64_t adds = 0, model_bytes = 0, ideal_bytes = 0;
 };
 
@@ -87,7 +91,8 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& out);
 // Verifies, on the host, that every memory access the kernels derive from the
 // plan's tables stays inside its buffer (input, workspace, output, shared
 // window).  Returns "" or the first violation.
-std::string check_plan(const HostPlan& P, int32_t fused_rp, int32_t adj_rp, int32_t adj_padl);
+struct FusedGeometry;
+std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp, int32_t adj_padl);
 
 // Bytes of the status header at the start of every workspace.
 constexpr size_t kWsHeader = 256;

@@ -6,13 +6,14 @@
 #include <set>
 #include <string>
 
+#include "fht_launch.hpp"
 #include "plan.hpp"
 
 namespace fht {
 
 static std::string at(const char* what, int64_t i) { return std::string(what) + " #" + std::to_string(i) + ": "; }
 
-std::string check_plan(const HostPlan& P, int32_t fused_rp, int32_t adj_rp, int32_t adj_padl) {
+std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp, int32_t adj_padl) {
   const int64_t ws_elems = (int64_t)((P.ws_bytes - kWsHeader) / P.acc_size);
   const int64_t out_elems = P.out_elems;
   const int32_t TW = P.cfg.TW;
@@ -26,20 +27,44 @@ std::string check_plan(const HostPlan& P, int32_t fused_rp, int32_t adj_rp, int3
     if (it.m < 1 || it.a < 0 || it.a + it.m > Q.n) return at("fused", k) + "rows outside the view";
     if (it.m > P.max_fused_m) return at("fused", k) + "subtree taller than the shared buffers";
     if (!Q.ext && it.c != 0) return at("fused", k) + "cyclic window must start at a column >= 0";
-    if (it.ntiles < 1 || (int64_t)(it.ntiles - 1) * TW >= it.wn || (int64_t)it.ntiles * TW < it.wn)
+    const int32_t tw = it.tw;
+    if (tw < 32 || tw % 32) return at("fused", k) + "bad tile width";
+    if (it.ntiles < 1 || (int64_t)(it.ntiles - 1) * tw >= it.wn || (int64_t)it.ntiles * tw < it.wn)
       return at("fused", k) + "tile count does not cover the node width";
     if (it.ntiles > P.max_ntiles) return at("fused", k) + "more tiles than the grid";
-    const int32_t TWin = TW + it.m - 1;
+    const int32_t TWin = tw + it.m - 1;
     if (it.prog < 0 || (size_t)it.prog + (size_t)it.nlev * it.m > P.ops.size()) return at("fused", k) + "program";
-    for (int32_t l = 0; l < it.nlev; l++)
-      for (int32_t r = 0; r < it.m; r++) {
-        const MergeOp& op = P.ops[(size_t)it.prog + (size_t)l * it.m + r];
-        if (op.top < 0 || op.top >= it.m) return at("fused", k) + "merge reads a row outside the subtree";
-        if (op.bot >= it.m) return at("fused", k) + "merge reads a row outside the subtree";
-        if (op.bot >= 0 && (op.s < 0 || TWin - 1 + op.s >= fused_rp))
-          return at("fused", k) + "shifted read beyond the shared row";
+    if (it.kind == FUSED_BY64) {
+      // fast path: staged window TW + 63 in S, level-2 rows TW + 60 in A,
+      // level-4 rows TW + 48 back in S; reads reach +3, +12 and +48 beyond
+      if (it.m != 64 || it.nlev != 6) return at("fused", k) + "fast path needs a 64-row block";
+      if (tw + 63 > g.RS || tw + 60 > g.RA || (size_t)64 * (g.RS + g.RA) * P.acc_size > g.smem)
+        return at("fused", k) + "fast-path buffers too small";
+      if ((tw + 60 - 1) + 3 >= g.RS || (tw + 48 - 1) + 12 >= g.RA || (tw - 1) + 48 >= g.RS)
+        return at("fused", k) + "fast-path shifted read beyond a shared row";
+      // the program must be the Brady-Yong block the fast path hard-codes
+      for (int32_t l = 0; l < 6; l++) {
+        const int32_t b = 1 << (l + 1);
+        for (int32_t r = 0; r < 64; r++) {
+          const MergeOp& op = P.ops[(size_t)it.prog + (size_t)l * 64 + r];
+          const int32_t base = r / b * b, t = r - base;
+          if (op.top != base + t / 2 || op.bot != base + b / 2 + t / 2 || op.s != (t + 1) / 2)
+            return at("fused", k) + "64-row program is not the Brady-Yong block";
+        }
       }
-    if (TWin > fused_rp) return at("fused", k) + "window wider than the shared row";
+    } else {
+      if (it.m > g.Fm) return at("fused", k) + "subtree taller than the shared buffers";
+      if ((size_t)2 * g.Fm * g.RP * P.acc_size > g.smem) return at("fused", k) + "generic buffers too small";
+      for (int32_t l = 0; l < it.nlev; l++)
+        for (int32_t r = 0; r < it.m; r++) {
+          const MergeOp& op = P.ops[(size_t)it.prog + (size_t)l * it.m + r];
+          if (op.top < 0 || op.top >= it.m) return at("fused", k) + "merge reads a row outside the subtree";
+          if (op.bot >= it.m) return at("fused", k) + "merge reads a row outside the subtree";
+          if (op.bot >= 0 && (op.s < 0 || TWin - 1 + op.s >= g.RP))
+            return at("fused", k) + "shifted read beyond the shared row";
+        }
+      if (TWin > g.RP) return at("fused", k) + "window wider than the shared row";
+    }
     if (!it.final_) {
       if (it.wn > it.dst_pitch) return at("fused", k) + "node wider than the workspace pitch";
       if (it.dst < 0 || it.dst + (int64_t)(it.m - 1) * it.dst_pitch + it.wn > ws_elems)
