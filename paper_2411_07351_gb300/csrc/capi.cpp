@@ -53,7 +53,7 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 }
 
 void free_dev(fht::DevicePlan& d) {
-  void* ptrs[] = {d.fused, d.ops, d.rows, d.arows, d.aterms, d.aptr, d.aops};
+  void* ptrs[] = {d.fused, d.ops, d.rows, d.arows, d.aterms, d.aptr, d.aops, d.band_items, d.spine_rows, d.spine_terms};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d.fused = nullptr;
@@ -63,6 +63,9 @@ void free_dev(fht::DevicePlan& d) {
   d.aterms = nullptr;
   d.aptr = nullptr;
   d.aops = nullptr;
+  d.band_items = nullptr;
+  d.spine_rows = nullptr;
+  d.spine_terms = nullptr;
 }
 
 }  // namespace
@@ -141,7 +144,10 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
         (e = upload(&p->dev.arows, p->host.arows)) != cudaSuccess ||
         (e = upload(&p->dev.aterms, p->host.aterms)) != cudaSuccess ||
         (e = upload(&p->dev.aptr, p->host.aptr)) != cudaSuccess ||
-        (e = upload(&p->dev.aops, p->host.aops)) != cudaSuccess) {
+        (e = upload(&p->dev.aops, p->host.aops)) != cudaSuccess ||
+        (e = upload(&p->dev.band_items, p->host.band_items)) != cudaSuccess ||
+        (e = upload(&p->dev.spine_rows, p->host.spine_rows)) != cudaSuccess ||
+        (e = upload(&p->dev.spine_terms, p->host.spine_terms)) != cudaSuccess) {
       free_dev(p->dev);
       delete p;
       if (e == cudaErrorMemoryAllocation) return fail(FHT_ERR_NOMEM, "fht_plan: device allocation failed");

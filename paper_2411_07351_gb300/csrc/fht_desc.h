@@ -38,11 +38,46 @@ struct FusedItem {
   int32_t ntiles;     // column tiles of width tile_cols covering wn
   int32_t aprog;      // adjoint program: first row pointer (nlev * (m + 1) entries)
   int32_t antiles;    // adjoint column tiles of width tile_cols covering the view length L
-  int32_t kind;       // 0: generic program; 1: perfect 64-row Brady-Yong block (fast path)
+  int32_t kind;       // FUSED_GENERIC, FUSED_BY64 or FUSED_BAND
   int32_t tw;         // column tile of this item (forward)
+  // Brady-Yong block paths (BY64 and BAND): 64 shared rows = G groups of
+  // B = 2^L rows, each group merged into a B-row Brady-Yong block.
+  int32_t L;          // levels per group (6 for BY64)
+  int32_t B;          // BAND: blocks of 64 rows in the band
+  int32_t K0;         // BAND: first slope index of the blocks' rows (group g reads row K0 + g)
+  int32_t wsrc;       // BAND: width of a block row (columns outside are zero / wrap)
+  int32_t c_src;      // BAND: block column = window column x + c_src + K b
+  int32_t src_pitch;  // BAND: elements between block rows
+  int64_t src;        // BAND: workspace offset of row 0 of the band's first block
 };
 
-enum : int32_t { FUSED_GENERIC = 0, FUSED_BY64 = 1 };
+enum : int32_t { FUSED_GENERIC = 0, FUSED_BY64 = 1, FUSED_BAND = 2 };
+
+// The quadrant table passed by value to kernels.
+struct QuadDescs {
+  QuadDesc q[4];
+};
+
+// Kinds of forward kernel launches (fht_plan_launch_info).
+enum : int32_t { LAUNCH_FUSED = 0, LAUNCH_UPPER = 1, LAUNCH_BAND = 2, LAUNCH_SPINE = 3 };
+
+// One output row of a root whose tree is a Split_T spine over "parts"
+// (perfect bands of 2^k rows, 64-row blocks and one remainder subtree):
+//   H[t][u] = sum_p part_p[r_p(t)][u + off_p(t)]
+// cyclic: part index mod W; extended: zero outside [0, wpart).  The sum is
+// stored through the quadrant's column map.
+struct SpineRow {
+  int64_t dst;        // output offset of the row
+  int32_t q;          // quadrant
+  int32_t term_begin, term_count;
+  int32_t pad;
+};
+
+struct SpineTerm {
+  int64_t row;        // workspace offset of the part's row r_p(t)
+  int32_t wpart;      // part row width
+  int32_t off;        // column offset (reduced to [0, W) in the cyclic case)
+};
 
 // One row of one level of a fused program: dst row <- src[top] + src[bot] shifted by s.
 // bot < 0 means the row is carried unchanged to the next level.

@@ -205,45 +205,160 @@ __device__ __forceinline__ void merge4_pass(const AccT* src, int32_t rs, AccT* d
   }
 }
 
-// Fast path: a perfect 64-row Brady-Yong block in three two-level passes.
-// Widths: the last pass needs TW columns of the level-4 rows plus the largest
-// level-5/6 shift (48), the middle pass TW + 48 plus 12, the first TW + 60
-// plus 3 = the staged window TW + 63.
+// One Brady-Yong level: two m-row blocks Q0, Q1 (rows base, base + m) become
+// one 2m-row block: t = 2k + i has t1 = t2 = k and shift ceil(t/2) = k + i.
+template <typename AccT>
+__device__ __forceinline__ void merge2_row(const AccT* src, int32_t rs, int32_t m, int32_t rp, int32_t j,
+                                           AccT o[2]) {
+  const int32_t g = rp / m, k = rp - (rp / m) * m;
+  const AccT* q0 = src + (size_t)(g * 2 * m + k) * rs + j;
+  const AccT* q1 = q0 + (size_t)m * rs + k;
+  const AccT a0 = q0[0], b0 = q1[0], b1 = q1[1];
+  o[0] = a0 + b0;
+  o[1] = a0 + b1;
+}
+
+template <typename AccT>
+__device__ __forceinline__ void merge2_pass(const AccT* src, int32_t rs, AccT* dst, int32_t rd, int32_t m,
+                                            int32_t width) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  for (int32_t rp = warp; rp < 32; rp += nwarps) {
+    const int32_t g = rp / m, k = rp - g * m;
+    AccT* d = dst + (size_t)(g * 2 * m + 2 * k) * rd;
+    for (int32_t j = lane; j < width; j += 32) {
+      AccT o[2];
+      merge2_row<AccT>(src, rs, m, rp, j, o);
+      d[j] = o[0];
+      d[rd + j] = o[1];
+    }
+  }
+}
+
+// Stage the 64 gathered rows of a band item: shared row r = g B + b holds
+// row K = K0 + g of block b, pre-shifted by K b.  In a perfect band of B
+// blocks the output slope t = K B + i sums, over the blocks, row K of block b
+// at offset K b + pat_B(i)(b) (the Brady-Yong pattern of the B-row transform),
+// so after this staging the band is a B-row Brady-Yong transform per group.
+template <typename AccT>
+__device__ __forceinline__ void stage_gathered(const FusedParams& p, const FusedItem& it, const QuadDesc& Q,
+                                               int32_t x0, int32_t width, AccT* buf, int32_t rp) {
+  const AccT* __restrict__ ws = static_cast<const AccT*>(p.ws);
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  constexpr int U = 8;
+  for (int32_t r = warp; r < 64; r += nwarps) {
+    const int32_t g = r / it.B, b = r - g * it.B;
+    const int32_t K = it.K0 + g;
+    const AccT* __restrict__ row = ws + it.src + (int64_t)(64 * b + K) * it.src_pitch;
+    const int32_t base = x0 + K * b + it.c_src;
+    AccT* dst = buf + (size_t)r * rp;
+    for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
+      AccT v[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int32_t j = j0 + u * 32 + lane;
+        int32_t z = base + j;
+        bool ok = j < width;
+        if (Q.ext) {
+          ok = ok && z >= 0 && z < it.wsrc;
+        } else {
+          z = z % Q.W;  // base >= 0 in the cyclic case
+        }
+        v[u] = ok ? row[z] : AccT(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int32_t j = j0 + u * 32 + lane;
+        if (j < width) dst[j] = v[u];
+      }
+    }
+  }
+}
+
+// Store the four (or two) outputs of one register group into global rows
+// r0, r0 + 1, ... of the item's destination at node column u0 + j.
+template <typename AccT, int N>
+__device__ __forceinline__ void store_group(const FusedItem& it, const QuadDesc& Q, AccT* base, int32_t r0,
+                                            int32_t u, const AccT* v) {
+  int32_t X = u;
+  if (it.final_) {
+    X = Q.sigma * u + Q.kappa;
+    if (X < 0) X += Q.W;
+    if (X >= Q.W) X -= Q.W;
+  }
+#pragma unroll
+  for (int i = 0; i < N; i++) base[(int64_t)(r0 + i) * it.dst_pitch + X] = v[i];
+}
+
+// Brady-Yong block paths: 64 shared rows, G = 64 / 2^L groups, each group a
+// 2^L-row Brady-Yong transform done in two-level passes (one single level
+// first when L is odd).  The last pass goes from registers to global memory.
+// Widths: a pass whose shifts reach `sh` reads sh columns beyond its output,
+// so the staged window is TW + 2^L - 1 and each pass narrows it.
 template <typename InT, typename AccT>
-__device__ void fused_by64(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile, AccT* S,
-                           AccT* A) {
+__device__ void fused_block(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile, AccT* S,
+                            AccT* A) {
   const int32_t TW = it.tw;
   const int32_t u0 = tile * TW;
-  stage_rows<InT, AccT>(p, Q, it.a, 64, u0 - it.c, TW + 63, S, p.RS);
+  const int32_t span = (1 << it.L) - 1;
+  if (it.kind == FUSED_BY64) {
+    stage_rows<InT, AccT>(p, Q, it.a, 64, u0 - it.c, TW + span, S, p.RS);
+  } else {
+    stage_gathered<AccT>(p, it, Q, u0 - it.c, TW + span, S, p.RS);
+  }
   __syncthreads();
-  merge4_pass<AccT>(S, p.RS, A, p.RA, 1, TW + 60);  // levels 1-2
-  __syncthreads();
-  merge4_pass<AccT>(A, p.RA, S, p.RS, 4, TW + 48);  // levels 3-4
-  __syncthreads();
-  // levels 5-6 straight from registers to global memory
+  AccT* src = S;
+  AccT* dst = A;
+  int32_t rs = p.RS, rd = p.RA;
+  int32_t m = 1, rem = span, left = it.L;
+  if (left & 1 && left > 1) {
+    rem -= m;
+    merge2_pass<AccT>(src, rs, dst, rd, m, TW + rem);
+    __syncthreads();
+    AccT* t = src;
+    src = dst;
+    dst = t;
+    int32_t tr = rs;
+    rs = rd;
+    rd = tr;
+    m *= 2;
+    left -= 1;
+  }
+  while (left > 2) {
+    rem -= 3 * m;
+    merge4_pass<AccT>(src, rs, dst, rd, m, TW + rem);
+    __syncthreads();
+    AccT* t = src;
+    src = dst;
+    dst = t;
+    int32_t tr = rs;
+    rs = rd;
+    rd = tr;
+    m *= 4;
+    left -= 2;
+  }
+  // last one or two levels straight from registers to global memory
   const int32_t ncols = min(TW, it.wn - u0);
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t nwarps = blockDim.x >> 5;
   AccT* __restrict__ base = (it.final_ ? static_cast<AccT*>(p.out) : static_cast<AccT*>(p.ws)) + it.dst;
-  for (int32_t k = warp; k < 16; k += nwarps) {
-    AccT* o = base + (int64_t)(4 * k) * it.dst_pitch;
-    for (int32_t j = lane; j < ncols; j += 32) {
-      AccT v[4];
-      merge4_row<AccT>(S, p.RS, 16, k, j, v);
-      if (!it.final_) {
-        const int32_t u = u0 + j;
-        o[u] = v[0];
-        o[it.dst_pitch + u] = v[1];
-        o[2 * (int64_t)it.dst_pitch + u] = v[2];
-        o[3 * (int64_t)it.dst_pitch + u] = v[3];
-      } else {
-        int32_t X = Q.sigma * (u0 + j) + Q.kappa;
-        if (X < 0) X += Q.W;
-        if (X >= Q.W) X -= Q.W;
-        o[X] = v[0];
-        o[it.dst_pitch + X] = v[1];
-        o[2 * (int64_t)it.dst_pitch + X] = v[2];
-        o[3 * (int64_t)it.dst_pitch + X] = v[3];
+  if (left == 2) {
+    for (int32_t rq = warp; rq < 16; rq += nwarps) {
+      const int32_t g = rq / m, k = rq - g * m;
+      for (int32_t j = lane; j < ncols; j += 32) {
+        AccT v[4];
+        merge4_row<AccT>(src, rs, m, rq, j, v);
+        store_group<AccT, 4>(it, Q, base, g * 4 * m + 4 * k, u0 + j, v);
+      }
+    }
+  } else {
+    for (int32_t rp = warp; rp < 32; rp += nwarps) {
+      const int32_t g = rp / m, k = rp - g * m;
+      for (int32_t j = lane; j < ncols; j += 32) {
+        AccT v[2];
+        merge2_row<AccT>(src, rs, m, rp, j, v);
+        store_group<AccT, 2>(it, Q, base, g * 2 * m + 2 * k, u0 + j, v);
       }
     }
   }
@@ -257,8 +372,8 @@ __global__ void __launch_bounds__(512, 2) fused_kernel(FusedParams p) {
   const QuadDesc& Q = p.quad[it.q];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AccT* sm = reinterpret_cast<AccT*>(smem_raw);
-  if (it.kind == FUSED_BY64) {
-    fused_by64<InT, AccT>(p, it, Q, tile, sm, sm + (size_t)64 * p.RS);
+  if (it.kind != FUSED_GENERIC) {
+    fused_block<InT, AccT>(p, it, Q, tile, sm, sm + (size_t)64 * p.RS);
   } else {
     fused_generic<InT, AccT>(p, it, Q, tile, sm, sm + (size_t)p.Fm * p.RP);
   }
@@ -318,6 +433,56 @@ __global__ void __launch_bounds__(256) upper_kernel(const RowJob* __restrict__ r
   }
 }
 
+// Spine sum: one CTA per output row of a Split_T root, every thread keeping
+// U columns x all terms in flight.  Consecutive rows read neighbouring part
+// rows, so consecutive CTAs mostly hit L2.
+template <typename AccT>
+__global__ void __launch_bounds__(256) spine_kernel(const SpineRow* __restrict__ rows, int64_t nrows,
+                                                   const SpineTerm* __restrict__ terms, const AccT* __restrict__ ws,
+                                                   AccT* __restrict__ out, QuadDescs quads) {
+  constexpr int U = 4;
+  constexpr int MAXT = 32;
+  __shared__ SpineTerm st[MAXT];
+  for (int64_t k = blockIdx.x; k < nrows; k += gridDim.x) {
+    const SpineRow R = rows[k];
+    const QuadDesc& Q = quads.q[R.q];
+    __syncthreads();
+    if ((int32_t)threadIdx.x < R.term_count) st[threadIdx.x] = terms[R.term_begin + threadIdx.x];
+    __syncthreads();
+    AccT* dst = out + R.dst;
+    for (int32_t u0 = 0; u0 < Q.W; u0 += (int32_t)blockDim.x * U) {
+      AccT acc[U];
+#pragma unroll
+      for (int q = 0; q < U; q++) acc[q] = AccT(0);
+      for (int32_t c = 0; c < R.term_count; c++) {
+        const SpineTerm T = st[c];
+        const AccT* __restrict__ row = ws + T.row;
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+          const int32_t u = u0 + q * (int32_t)blockDim.x + (int32_t)threadIdx.x;
+          int32_t i = u + T.off;
+          if (Q.ext) {
+            if (u < Q.W && i >= 0 && i < T.wpart) acc[q] += row[i];
+          } else if (u < Q.W) {
+            if (i >= Q.W) i -= Q.W;
+            acc[q] += row[i];
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const int32_t u = u0 + q * (int32_t)blockDim.x + (int32_t)threadIdx.x;
+        if (u < Q.W) {
+          int32_t X = Q.sigma * u + Q.kappa;
+          if (X < 0) X += Q.W;
+          if (X >= Q.W) X -= Q.W;
+          dst[X] = acc[q];
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------
@@ -336,15 +501,24 @@ void fused_geometry(const HostPlan& P, FusedGeometry& g) {
   g.smem = std::max(generic, by64);
 }
 
-int32_t forward_launches(const HostPlan& P) { return 1 + (int32_t)P.pass_bytes.size(); }
+int32_t forward_launches(const HostPlan& P) {
+  if (P.bands) return 1 + (P.band_items.empty() ? 0 : 1) + (P.spine_rows.empty() ? 0 : 1);
+  return 1 + (int32_t)P.pass_bytes.size();
+}
 
 void forward_launch_info(const HostPlan& P, int32_t k, int32_t& kind, int64_t& bytes) {
   if (k == 0) {
-    kind = 0;
+    kind = LAUNCH_FUSED;
     bytes = P.fused_bytes;
-  } else {
-    kind = 1;
+  } else if (!P.bands) {
+    kind = LAUNCH_UPPER;
     bytes = P.pass_bytes[k - 1];
+  } else if (k == 1 && !P.band_items.empty()) {
+    kind = LAUNCH_BAND;
+    bytes = P.band_bytes;
+  } else {
+    kind = LAUNCH_SPINE;
+    bytes = P.spine_bytes;
   }
 }
 
@@ -380,6 +554,29 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
   launch++;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (P.bands) {
+    if (!P.band_items.empty()) {
+      fp.items = D.band_items;
+      dim3 bgrid((unsigned)P.band_items.size(), P.max_band_ntiles);
+      mark(0);
+      kfn<<<bgrid, P.cfg.threads, smem, st>>>(fp);
+      mark(1);
+      launch++;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (!P.spine_rows.empty()) {
+      QuadDescs qd;
+      for (int q = 0; q < 4; q++) qd.q[q] = P.quad[q];
+      const int64_t n = (int64_t)P.spine_rows.size();
+      mark(0);
+      spine_kernel<AccT><<<(unsigned)std::min<int64_t>(n, 1 << 30), 256, 0, st>>>(
+          D.spine_rows, n, D.spine_terms, wsa, static_cast<AccT*>(out), qd);
+      mark(1);
+      launch++;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   for (size_t p = 0; p + 1 < P.pass_begin.size(); p++) {
     const int64_t b = P.pass_begin[p], n = P.pass_begin[p + 1] - b;
     if (n <= 0) continue;

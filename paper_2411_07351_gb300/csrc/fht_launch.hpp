@@ -21,6 +21,9 @@ struct DevicePlan {
   FusedItem* fused = nullptr;
   MergeOp* ops = nullptr;
   RowJob* rows = nullptr;
+  FusedItem* band_items = nullptr;
+  SpineRow* spine_rows = nullptr;
+  SpineTerm* spine_terms = nullptr;
   AdjRow* arows = nullptr;
   AdjTerm* aterms = nullptr;
   int32_t* aptr = nullptr;
@@ -43,7 +46,7 @@ cudaError_t launch_adjoint(const DevicePlan& D, const void* gout, void* gin, int
                            cudaStream_t st);
 
 // Kernel launches of one forward transform, and the kind of launch k
-// (0: fused pass, 1: upper pass) with its model bytes.
+// (LAUNCH_FUSED, LAUNCH_UPPER, LAUNCH_BAND, LAUNCH_SPINE) with its model bytes.
 int32_t forward_launches(const HostPlan& P);
 void forward_launch_info(const HostPlan& P, int32_t k, int32_t& kind, int64_t& bytes);
 

@@ -130,6 +130,10 @@ static void build_adjoint_program(const std::vector<MergeOp>& ops, int32_t prog,
   }
 }
 
+static int32_t bi_width(const PlanConfig& cfg, const QuadDesc& Q, int32_t m) {
+  return cfg.ext ? Q.L + m - 1 : Q.W;
+}
+
 static int32_t dtype_in_size(int32_t dt) { return dt == 0 ? 1 : dt == 3 ? 8 : 4; }
 static int32_t dtype_acc_size(int32_t dt) { return dt == 3 ? 8 : 4; }
 
@@ -234,6 +238,27 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
     }
     const bool root_fused = !is_upper[rootidx];
     if (root_fused) nbuf = 0;  // the single fused subtree writes the output directly
+    // band schedule: walk the Split_T spine from the root; every left child is
+    // a power of two (a perfect band, or a 64-row block), the walk ends at a
+    // power of two or at the remainder subtree of at most 64 rows
+    const bool use_bands = cfg.split == Split::T && cfg.F == 64 && !root_fused;
+    std::vector<int32_t> spine, parts;
+    auto is_part = [&](int32_t i) {
+      const int32_t m = tr.nodes[i].m;
+      return m <= 64 || (m & (m - 1)) == 0;
+    };
+    if (use_bands) {
+      int32_t i = rootidx;
+      while (!is_part(i)) {
+        spine.push_back(i);
+        parts.push_back(tr.nodes[i].child[0]);
+        i = tr.nodes[i].child[1];
+      }
+      parts.push_back(i);
+      for (int32_t pi : parts)
+        if (tr.nodes[pi].m > 64 && pi != rootidx) nbuf = std::max(nbuf, 2);
+      P.bands = true;
+    }
     P.ws_quad_off[q] = ws_off;
     P.ws_pitch[q] = pitch;
     P.nbuf[q] = nbuf;
@@ -285,6 +310,83 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
       P.fused.push_back(fi);
       // model bytes: the subtree's input rows once, its Hough rows once
       P.fused_bytes += (int64_t)nd.m * Q.L * P.in_size + (int64_t)nd.m * fi.wn * acc;
+    }
+
+    if (use_bands) {
+      // part p of the spine lives in buffer 0 (<= 64 rows: written by the fused
+      // pass) or buffer 1 (a band: written by the band pass), or is the root
+      auto part_buf = [&](int32_t pi) { return tr.nodes[pi].m <= 64 ? 0 : 1; };
+      auto part_w = [&](int32_t pi) { return cfg.ext ? Q.L + tr.nodes[pi].m - 1 : Q.W; };
+      for (int32_t pi : parts) {
+        const TreeNode& band = tr.nodes[pi];
+        if (band.m <= 64) continue;
+        const bool fin = pi == rootidx;
+        const int32_t B = band.m / 64, G = 64 / B;
+        int32_t L = 0;
+        while ((1 << L) < B) L++;
+        for (int32_t K0 = 0; K0 < 64; K0 += G) {
+          FusedItem bi{};
+          bi.q = q;
+          bi.kind = FUSED_BAND;
+          bi.a = band.a;
+          bi.m = 64;
+          bi.L = L;
+          bi.B = B;
+          bi.K0 = K0;
+          bi.src = buf_row(0, band.a);
+          bi.src_pitch = pitch;
+          bi.wsrc = cfg.ext ? Q.L + 63 : Q.W;
+          bi.c_src = cfg.ext ? 63 : 0;
+          bi.wn = part_w(pi);
+          bi.c = cfg.ext ? band.m - 1 : 0;
+          bi.final_ = fin;
+          bi.dst = fin ? Q.out_off + (int64_t)K0 * B * Q.W : buf_row(1, band.a + K0 * B);
+          bi.dst_pitch = fin ? Q.W : pitch;
+          bi.tw = cfg.TW;
+          bi.ntiles = (bi.wn + bi.tw - 1) / bi.tw;
+          P.max_band_ntiles = std::max(P.max_band_ntiles, bi.ntiles);
+          P.band_items.push_back(bi);
+        }
+        // compulsory bytes: the band's blocks read once, the band written once
+        P.band_bytes += ((int64_t)band.m * (cfg.ext ? Q.L + 63 : Q.W) + (int64_t)band.m * bi_width(cfg, Q, band.m)) * acc;
+      }
+      if (!spine.empty()) {
+        // every output slope t: follow the spine, collecting (part, row, offset)
+        for (int32_t t = 0; t < tr.n; t++) {
+          SpineRow sr;
+          sr.dst = Q.out_off + (int64_t)t * Q.W;
+          sr.q = q;
+          sr.term_begin = (int32_t)P.spine_terms.size();
+          sr.pad = 0;
+          int32_t tn = t;
+          int64_t off = 0;  // accumulated shift in window (x) coordinates
+          auto add_term = [&](int32_t pi, int32_t row) {
+            const TreeNode& pt = tr.nodes[pi];
+            SpineTerm st;
+            st.row = buf_row(part_buf(pi), pt.a + row);
+            st.wpart = part_w(pi);
+            st.off = cfg.ext ? (int32_t)(off + pt.m - tr.n) : (int32_t)(off % Q.W);
+            P.spine_terms.push_back(st);
+          };
+          for (size_t k = 0; k < spine.size(); k++) {
+            const TreeNode& nd = tr.nodes[spine[k]];
+            const TreeNode& c0 = tr.nodes[nd.child[0]];
+            const TreeNode& c1 = tr.nodes[nd.child[1]];
+            int32_t t1, t2, sh;
+            merge_entry(nd.m, c0.m, c1.m, tn, t1, t2, sh);
+            add_term(nd.child[0], t1);
+            off += sh;
+            tn = t2;
+            if (k + 1 == spine.size()) add_term(nd.child[1], t2);
+          }
+          sr.term_count = (int32_t)P.spine_terms.size() - sr.term_begin;
+          P.max_spine_terms = std::max(P.max_spine_terms, sr.term_count);
+          P.spine_rows.push_back(sr);
+        }
+        int64_t parts_bytes = 0;
+        for (int32_t pi : parts) parts_bytes += (int64_t)tr.nodes[pi].m * part_w(pi);
+        P.spine_bytes += (parts_bytes + qsize) * acc;
+      }
     }
 
     // upper passes: one per tree height, shared by all quadrants
@@ -418,8 +520,9 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
     P.rows.insert(P.rows.end(), passes[k].begin(), passes[k].end());
     P.pass_begin.push_back((int64_t)P.rows.size());
     P.pass_bytes.push_back(bytes_by_height[k]);
-    P.model_bytes += bytes_by_height[k];
+    if (!P.bands) P.model_bytes += bytes_by_height[k];
   }
+  if (P.bands) P.model_bytes += P.band_bytes + P.spine_bytes;
   if (P.ops.empty()) P.ops.push_back(MergeOp{0, -1, 0, 0});
   for (const MergeOp& op : P.ops)
     if (op.bot >= 0) P.max_fused_shift = std::max<int32_t>(P.max_fused_shift, op.s);

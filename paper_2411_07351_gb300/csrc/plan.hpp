@@ -83,6 +83,16 @@ struct HostPlan {
   int32_t generic_tw = 0;             // column tile of generic fused items
   int32_t n_by64 = 0;                 // fused items on the 64-row Brady-Yong fast path
   int64_t adds = 0, model_bytes = 0, ideal_bytes = 0;
+  // band schedule (Split_T with 64-row fused blocks): one gathered
+  // Brady-Yong pass for every perfect band above the blocks, then one
+  // spine-sum pass, replacing the per-height passes
+  bool bands = false;
+  std::vector<FusedItem> band_items;
+  std::vector<SpineRow> spine_rows;
+  std::vector<SpineTerm> spine_terms;
+  int32_t max_band_ntiles = 0;
+  int64_t band_bytes = 0, spine_bytes = 0;
+  int32_t max_spine_terms = 0;
 };
 
 // Returns "" on success, else an error message.

@@ -110,6 +110,58 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
       }
     }
   }
+  // ---- band schedule ----
+  for (size_t k = 0; k < P.band_items.size(); k++) {
+    const FusedItem& it = P.band_items[k];
+    if (!P.bands || it.kind != FUSED_BAND) return at("band", k) + "not a band item";
+    if (it.q < 0 || it.q > 3 || !(P.cfg.quads & (1u << it.q))) return at("band", k) + "bad quadrant";
+    const QuadDesc& Q = P.quad[it.q];
+    if (it.B < 2 || it.B > 64 || (it.B & (it.B - 1)) || (1 << it.L) != it.B || it.m != 64)
+      return at("band", k) + "band must be 2..64 blocks of 64 rows";
+    if (it.K0 < 0 || it.K0 % (64 / it.B) || it.K0 + 64 / it.B > 64) return at("band", k) + "bad group range";
+    if (it.tw != TW || it.tw + 63 > g.RS || it.tw + 60 > g.RA) return at("band", k) + "band buffers too small";
+    if (it.ntiles < 1 || (int64_t)(it.ntiles - 1) * TW >= it.wn || (int64_t)it.ntiles * TW < it.wn ||
+        it.ntiles > P.max_band_ntiles)
+      return at("band", k) + "tiles do not cover the band";
+    if (!Q.ext && (it.c != 0 || it.c_src != 0 || it.wsrc != Q.W)) return at("band", k) + "cyclic offsets";
+    if (it.wsrc > it.src_pitch) return at("band", k) + "block row wider than its pitch";
+    if (it.src < 0 || it.src + (int64_t)(64 * (it.B - 1) + 63) * it.src_pitch + it.wsrc > ws_elems)
+      return at("band", k) + "block rows outside the workspace";
+    if (!it.final_) {
+      if (it.wn > it.dst_pitch || it.dst < 0 || it.dst + (int64_t)63 * it.dst_pitch + it.wn > ws_elems)
+        return at("band", k) + "band rows outside the workspace";
+    } else {
+      if (it.dst_pitch != Q.W || it.wn != Q.W || it.dst < 0 || it.dst + (int64_t)64 * Q.W > out_elems)
+        return at("band", k) + "final band rows outside the output";
+      for (int32_t u : {0, it.wn - 1}) {
+        const int64_t X = (int64_t)Q.sigma * u + Q.kappa;
+        if (X < -Q.W || X >= 2 * (int64_t)Q.W) return at("band", k) + "column map needs more than one wrap";
+      }
+    }
+  }
+  for (size_t k = 0; k < P.spine_rows.size(); k++) {
+    const SpineRow& R = P.spine_rows[k];
+    if (R.q < 0 || R.q > 3 || !(P.cfg.quads & (1u << R.q))) return at("spine", k) + "bad quadrant";
+    const QuadDesc& Q = P.quad[R.q];
+    if (R.term_count < 1 || R.term_count > 32 || R.term_begin < 0 ||
+        (size_t)R.term_begin + R.term_count > P.spine_terms.size())
+      return at("spine", k) + "terms";
+    if (R.dst < 0 || R.dst + Q.W > out_elems) return at("spine", k) + "row outside the output";
+    for (int32_t u : {0, Q.W - 1}) {
+      const int64_t X = (int64_t)Q.sigma * u + Q.kappa;
+      if (X < -Q.W || X >= 2 * (int64_t)Q.W) return at("spine", k) + "column map needs more than one wrap";
+    }
+    for (int32_t c = 0; c < R.term_count; c++) {
+      const SpineTerm& T = P.spine_terms[R.term_begin + c];
+      if (Q.ext) {
+        if (T.row < 0 || T.row + T.wpart > ws_elems) return at("spine", k) + "part row outside the workspace";
+      } else {
+        if (T.wpart != Q.W || T.off < 0 || T.off >= Q.W || T.row < 0 || T.row + Q.W > ws_elems)
+          return at("spine", k) + "cyclic part row";
+      }
+    }
+  }
+
   // ---- adjoint ----
   const int64_t adj_elems = (int64_t)((P.adj_ws_bytes - kWsHeader) / P.acc_size);
   const int64_t img = (int64_t)P.cfg.h * P.cfg.w;

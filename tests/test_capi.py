@@ -100,8 +100,13 @@ def test_host_only_plan_cannot_run(F):
 
 
 def test_byte_model_c2(F):
-    # 4095^2 float32, four quadrants: the per-height schedule moves 4.55 GB
-    # (extended) / 3.76 GB (cyclic); ideal = input once + output once.
+    # 4095^2 float32, four quadrants, extended; ideal = input once + output once.
+    # Band schedule (Split_T, 64-row blocks): fused pass + band pass + spine sum,
+    # 2.05 GB.  The per-height schedule (here forced by 32-row fused subtrees)
+    # moves one read + write of every node per tree height: 5.1 GB.
     p = F.Plan(4095, 4095, torch.float32, 15, "extended", device=-1)
     assert abs(p.info.ideal_bytes - (4 * 4095 * 4095 * 4 + 4 * 4095 * 8189 * 4)) == 0
-    assert 4.4e9 < p.info.model_bytes < 4.7e9
+    assert 2.0e9 < p.info.model_bytes < 2.1e9
+    assert p.info.upper_passes == 6
+    p32 = F.Plan(4095, 4095, torch.float32, 15, "extended", device=-1, fused_rows=32)
+    assert 5.0e9 < p32.info.model_bytes < 5.2e9
