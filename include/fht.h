@@ -117,9 +117,10 @@ fht_status fht_forward(fht_plan_t plan, const void* d_in, int64_t in_pitch, void
 /* Kernel launches one fht_forward of this plan enqueues. */
 fht_status fht_plan_launches(fht_plan_t plan, int32_t* count);
 
-/* Kind of the k-th launch of fht_forward (0: fused shared-memory pass,
- * 1: upper per-height pass) and the HBM bytes its schedule must move
- * (compulsory reads + writes of that launch). */
+/* Kind of the k-th launch of fht_forward (0: fused shared-memory pass over
+ * subtrees of at most 64 rows, 1: upper per-height pass, 2: band pass (perfect
+ * 2^k bands above the 64-row blocks), 3: spine sum of a Split_T root) and the
+ * HBM bytes its schedule must move (compulsory reads + writes of that launch). */
 fht_status fht_plan_launch_info(fht_plan_t plan, int32_t k, int32_t* kind, int64_t* model_bytes);
 
 /* fht_forward that also records events[2k] and events[2k + 1] (cudaEvent_t
