@@ -283,7 +283,7 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
         build_adjoint_program(P.ops, it->second.first, it->second.second, nd.m, P.aptr, P.aops, aoff);
         ait = aprog_cache.emplace(nd.m, aoff).first;
       }
-      FusedItem fi;
+      FusedItem fi{};
       fi.aprog = ait->second;
       fi.antiles = (Q.L + cfg.TW - 1) / cfg.TW;
       P.max_antiles = std::max(P.max_antiles, fi.antiles);
@@ -304,6 +304,7 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
       }
       // a 64-row subtree is a perfect Brady-Yong block under both split rules
       fi.kind = nd.m == 64 ? FUSED_BY64 : FUSED_GENERIC;
+      fi.L = fi.kind == FUSED_BY64 ? 6 : 0;
       fi.tw = 0;  // set once all items are known
       fi.ntiles = 0;
       P.max_fused_m = std::max(P.max_fused_m, nd.m);

@@ -20,6 +20,7 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
   for (size_t k = 0; k < P.fused.size(); k++) {
     const FusedItem& it = P.fused[k];
     if (it.q < 0 || it.q > 3 || !(P.cfg.quads & (1u << it.q))) return at("fused", k) + "bad quadrant";
+    if (it.kind != FUSED_GENERIC && it.kind != FUSED_BY64) return at("fused", k) + "bad kind";
     const QuadDesc& Q = P.quad[it.q];
     const int32_t img_rows = Q.transpose ? P.cfg.w : P.cfg.h;  // view rows are image rows or columns
     const int32_t img_len = Q.transpose ? P.cfg.h : P.cfg.w;
@@ -37,7 +38,7 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
     if (it.kind == FUSED_BY64) {
       // fast path: staged window TW + 63 in S, level-2 rows TW + 60 in A,
       // level-4 rows TW + 48 back in S; reads reach +3, +12 and +48 beyond
-      if (it.m != 64 || it.nlev != 6) return at("fused", k) + "fast path needs a 64-row block";
+      if (it.m != 64 || it.nlev != 6 || it.L != 6) return at("fused", k) + "fast path needs a 64-row block";
       if (tw + 63 > g.RS || tw + 60 > g.RA || (size_t)64 * (g.RS + g.RA) * P.acc_size > g.smem)
         return at("fused", k) + "fast-path buffers too small";
       if ((tw + 60 - 1) + 3 >= g.RS || (tw + 48 - 1) + 12 >= g.RA || (tw - 1) + 48 >= g.RS)
