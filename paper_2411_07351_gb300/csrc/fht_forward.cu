@@ -433,16 +433,18 @@ __global__ void __launch_bounds__(256) upper_kernel(const RowJob* __restrict__ r
   }
 }
 
-// Spine sum: one CTA per output row of a Split_T root, every thread keeping
-// U columns x all terms in flight.  Consecutive rows read neighbouring part
-// rows, so consecutive CTAs mostly hit L2.
+// Spine sum: one CTA per output row of a Split_T root.  Every thread owns U
+// columns and issues the loads of all terms (at most kMaxSpineTerms) before
+// adding, so U x terms loads are in flight per thread.  Consecutive rows read
+// neighbouring part rows, so consecutive CTAs mostly hit L2.
+constexpr int kMaxSpineTerms = 16;
+
 template <typename AccT>
 __global__ void __launch_bounds__(256) spine_kernel(const SpineRow* __restrict__ rows, int64_t nrows,
                                                    const SpineTerm* __restrict__ terms, const AccT* __restrict__ ws,
                                                    AccT* __restrict__ out, QuadDescs quads) {
-  constexpr int U = 4;
-  constexpr int MAXT = 32;
-  __shared__ SpineTerm st[MAXT];
+  constexpr int U = 2;
+  __shared__ SpineTerm st[kMaxSpineTerms];
   for (int64_t k = blockIdx.x; k < nrows; k += gridDim.x) {
     const SpineRow R = rows[k];
     const QuadDesc& Q = quads.q[R.q];
@@ -450,33 +452,38 @@ __global__ void __launch_bounds__(256) spine_kernel(const SpineRow* __restrict__
     if ((int32_t)threadIdx.x < R.term_count) st[threadIdx.x] = terms[R.term_begin + threadIdx.x];
     __syncthreads();
     AccT* dst = out + R.dst;
+    const int32_t nt = R.term_count;
     for (int32_t u0 = 0; u0 < Q.W; u0 += (int32_t)blockDim.x * U) {
-      AccT acc[U];
+      AccT v[kMaxSpineTerms][U];
 #pragma unroll
-      for (int q = 0; q < U; q++) acc[q] = AccT(0);
-      for (int32_t c = 0; c < R.term_count; c++) {
-        const SpineTerm T = st[c];
-        const AccT* __restrict__ row = ws + T.row;
+      for (int c = 0; c < kMaxSpineTerms; c++) {
 #pragma unroll
         for (int q = 0; q < U; q++) {
+          v[c][q] = AccT(0);
           const int32_t u = u0 + q * (int32_t)blockDim.x + (int32_t)threadIdx.x;
-          int32_t i = u + T.off;
-          if (Q.ext) {
-            if (u < Q.W && i >= 0 && i < T.wpart) acc[q] += row[i];
-          } else if (u < Q.W) {
-            if (i >= Q.W) i -= Q.W;
-            acc[q] += row[i];
+          if (c < nt && u < Q.W) {
+            const SpineTerm& T = st[c];
+            int32_t i = u + T.off;
+            if (Q.ext) {
+              if (i >= 0 && i < T.wpart) v[c][q] = __ldg(ws + T.row + i);
+            } else {
+              if (i >= Q.W) i -= Q.W;
+              v[c][q] = __ldg(ws + T.row + i);
+            }
           }
         }
       }
 #pragma unroll
       for (int q = 0; q < U; q++) {
+        AccT acc = v[0][q];
+#pragma unroll
+        for (int c = 1; c < kMaxSpineTerms; c++) acc += v[c][q];
         const int32_t u = u0 + q * (int32_t)blockDim.x + (int32_t)threadIdx.x;
         if (u < Q.W) {
           int32_t X = Q.sigma * u + Q.kappa;
           if (X < 0) X += Q.W;
           if (X >= Q.W) X -= Q.W;
-          dst[X] = acc[q];
+          dst[X] = acc;
         }
       }
     }

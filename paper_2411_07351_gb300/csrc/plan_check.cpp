@@ -144,7 +144,7 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
     const SpineRow& R = P.spine_rows[k];
     if (R.q < 0 || R.q > 3 || !(P.cfg.quads & (1u << R.q))) return at("spine", k) + "bad quadrant";
     const QuadDesc& Q = P.quad[R.q];
-    if (R.term_count < 1 || R.term_count > 32 || R.term_begin < 0 ||
+    if (R.term_count < 1 || R.term_count > 16 || R.term_begin < 0 ||
         (size_t)R.term_begin + R.term_count > P.spine_terms.size())
       return at("spine", k) + "terms";
     if (R.dst < 0 || R.dst + Q.W > out_elems) return at("spine", k) + "row outside the output";
