@@ -55,7 +55,7 @@ __device__ __forceinline__ void stage_rows(const FusedParams& p, const QuadDesc&
   if (!Q.transpose) {
     for (int32_t r = warp; r < m; r += nwarps) {
       AccT* dst = buf + (size_t)r * rp;
-      const int32_t row = a + r;
+      const InT* __restrict__ rowp = in + (int64_t)(a + r) * p.in_pitch;
       for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
         AccT v[U];
 #pragma unroll
@@ -68,7 +68,8 @@ __device__ __forceinline__ void stage_rows(const FusedParams& p, const QuadDesc&
           } else if (z >= Q.L) {
             z = z < 2 * Q.L ? z - Q.L : z % Q.L;  // x0 >= 0 in the cyclic case
           }
-          v[u] = ok ? view_load<InT, AccT>(in, p.in_pitch, Q, row, z) : AccT(0);
+          if (Q.flip) z = Q.L - 1 - z;
+          v[u] = ok ? (AccT)rowp[z] : AccT(0);
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
@@ -169,34 +170,44 @@ __device__ void fused_generic(const FusedParams& p, const FusedItem& it, const Q
 // so the four outputs of one k need only ten shifted reads.  `rq` = g m + k
 // indexes the 16 (block group, k) pairs of a 64-row block.
 template <typename AccT>
-__device__ __forceinline__ void merge4_row(const AccT* src, int32_t rs, int32_t m, int32_t rq, int32_t j,
-                                           AccT o[4]) {
-  const int32_t g = rq / m, k = rq - (rq / m) * m;
-  const AccT* q0 = src + (size_t)(g * 4 * m + k) * rs + j;
-  const AccT* q1 = q0 + (size_t)m * rs + k;
-  const AccT* q2 = q0 + (size_t)2 * m * rs + 2 * k;
-  const AccT* q3 = q0 + (size_t)3 * m * rs + 3 * k;
-  const AccT a0 = q0[0];
-  const AccT b0 = q1[0], b1 = q1[1];
-  const AccT c0 = q2[0], c1 = q2[1], c2 = q2[2];
-  const AccT d0 = q3[0], d1 = q3[1], d2 = q3[2], d3 = q3[3];
-  o[0] = (a0 + b0) + (c0 + d0);
-  o[1] = (a0 + b0) + (c1 + d1);
-  o[2] = (a0 + b1) + (c1 + d2);
-  o[3] = (a0 + b1) + (c2 + d3);
+__device__ __forceinline__ void merge4_at(const AccT* q0, const AccT* q1, const AccT* q2, const AccT* q3,
+                                          int32_t j, AccT o[4]) {
+  const AccT a0 = q0[j];
+  const AccT b0 = q1[j], b1 = q1[j + 1];
+  const AccT c0 = q2[j], c1 = q2[j + 1], c2 = q2[j + 2];
+  const AccT d0 = q3[j], d1 = q3[j + 1], d2 = q3[j + 2], d3 = q3[j + 3];
+  const AccT ab0 = a0 + b0, ab1 = a0 + b1;
+  o[0] = ab0 + (c0 + d0);
+  o[1] = ab0 + (c1 + d1);
+  o[2] = ab1 + (c1 + d2);
+  o[3] = ab1 + (c2 + d3);
 }
 
-template <typename AccT>
-__device__ __forceinline__ void merge4_pass(const AccT* src, int32_t rs, AccT* dst, int32_t rd, int32_t m,
-                                            int32_t width) {
+// Source row pointers of row-quad rq for blocks of M rows (compile-time M).
+template <int M, typename AccT>
+__device__ __forceinline__ void merge4_ptrs(const AccT* src, int32_t rs, int32_t rq, const AccT*& q0,
+                                            const AccT*& q1, const AccT*& q2, const AccT*& q3, int32_t& r0) {
+  const int32_t g = rq / M, k = rq % M;  // M is a power of two known at compile time
+  q0 = src + (g * 4 * M + k) * rs;
+  q1 = q0 + M * rs + k;
+  q2 = q0 + 2 * M * rs + 2 * k;
+  q3 = q0 + 3 * M * rs + 3 * k;
+  r0 = g * 4 * M + 4 * k;
+}
+
+template <int M, typename AccT>
+__device__ __forceinline__ void merge4_pass(const AccT* src, int32_t rs, AccT* dst, int32_t rd, int32_t width) {
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t nwarps = blockDim.x >> 5;
   for (int32_t rq = warp; rq < 16; rq += nwarps) {
-    const int32_t g = rq / m, k = rq - g * m;
-    AccT* d = dst + (size_t)(g * 4 * m + 4 * k) * rd;
+    const AccT *q0, *q1, *q2, *q3;
+    int32_t r0;
+    merge4_ptrs<M, AccT>(src, rs, rq, q0, q1, q2, q3, r0);
+    AccT* d = dst + r0 * rd;
+#pragma unroll 2
     for (int32_t j = lane; j < width; j += 32) {
       AccT o[4];
-      merge4_row<AccT>(src, rs, m, rq, j, o);
+      merge4_at<AccT>(q0, q1, q2, q3, j, o);
       d[j] = o[0];
       d[rd + j] = o[1];
       d[2 * rd + j] = o[2];
@@ -207,30 +218,28 @@ __device__ __forceinline__ void merge4_pass(const AccT* src, int32_t rs, AccT* d
 
 // One Brady-Yong level: two m-row blocks Q0, Q1 (rows base, base + m) become
 // one 2m-row block: t = 2k + i has t1 = t2 = k and shift ceil(t/2) = k + i.
-template <typename AccT>
-__device__ __forceinline__ void merge2_row(const AccT* src, int32_t rs, int32_t m, int32_t rp, int32_t j,
-                                           AccT o[2]) {
-  const int32_t g = rp / m, k = rp - (rp / m) * m;
-  const AccT* q0 = src + (size_t)(g * 2 * m + k) * rs + j;
-  const AccT* q1 = q0 + (size_t)m * rs + k;
-  const AccT a0 = q0[0], b0 = q1[0], b1 = q1[1];
-  o[0] = a0 + b0;
-  o[1] = a0 + b1;
+template <int M, typename AccT>
+__device__ __forceinline__ void merge2_ptrs(const AccT* src, int32_t rs, int32_t rp, const AccT*& q0,
+                                            const AccT*& q1, int32_t& r0) {
+  const int32_t g = rp / M, k = rp % M;
+  q0 = src + (g * 2 * M + k) * rs;
+  q1 = q0 + M * rs + k;
+  r0 = g * 2 * M + 2 * k;
 }
 
-template <typename AccT>
-__device__ __forceinline__ void merge2_pass(const AccT* src, int32_t rs, AccT* dst, int32_t rd, int32_t m,
-                                            int32_t width) {
+template <int M, typename AccT>
+__device__ __forceinline__ void merge2_pass(const AccT* src, int32_t rs, AccT* dst, int32_t rd, int32_t width) {
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t nwarps = blockDim.x >> 5;
   for (int32_t rp = warp; rp < 32; rp += nwarps) {
-    const int32_t g = rp / m, k = rp - g * m;
-    AccT* d = dst + (size_t)(g * 2 * m + 2 * k) * rd;
+    const AccT *q0, *q1;
+    int32_t r0;
+    merge2_ptrs<M, AccT>(src, rs, rp, q0, q1, r0);
+    AccT* d = dst + r0 * rd;
     for (int32_t j = lane; j < width; j += 32) {
-      AccT o[2];
-      merge2_row<AccT>(src, rs, m, rp, j, o);
-      d[j] = o[0];
-      d[rd + j] = o[1];
+      const AccT a = q0[j];
+      d[j] = a + q1[j];
+      d[rd + j] = a + q1[j + 1];
     }
   }
 }
@@ -291,11 +300,54 @@ __device__ __forceinline__ void store_group(const FusedItem& it, const QuadDesc&
   for (int i = 0; i < N; i++) base[(int64_t)(r0 + i) * it.dst_pitch + X] = v[i];
 }
 
+// Last two levels (merge4 with blocks of M rows) from shared memory straight
+// to global memory.
+template <int M, typename AccT>
+__device__ __forceinline__ void final_merge4(const FusedItem& it, const QuadDesc& Q, const AccT* src, int32_t rs,
+                                             AccT* base, int32_t u0, int32_t ncols) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  for (int32_t rq = warp; rq < 16; rq += nwarps) {
+    const AccT *q0, *q1, *q2, *q3;
+    int32_t r0;
+    merge4_ptrs<M, AccT>(src, rs, rq, q0, q1, q2, q3, r0);
+    AccT* o = base + (int64_t)r0 * it.dst_pitch;
+    for (int32_t j = lane; j < ncols; j += 32) {
+      AccT v[4];
+      merge4_at<AccT>(q0, q1, q2, q3, j, v);
+      store_group<AccT, 4>(it, Q, o, 0, u0 + j, v);
+    }
+  }
+}
+
+template <typename AccT>
+__device__ __forceinline__ void final_merge2_1(const FusedItem& it, const QuadDesc& Q, const AccT* src, int32_t rs,
+                                               AccT* base, int32_t u0, int32_t ncols) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  for (int32_t rp = warp; rp < 32; rp += nwarps) {
+    const AccT *q0, *q1;
+    int32_t r0;
+    merge2_ptrs<1, AccT>(src, rs, rp, q0, q1, r0);
+    AccT* o = base + (int64_t)r0 * it.dst_pitch;
+    for (int32_t j = lane; j < ncols; j += 32) {
+      const AccT a = q0[j];
+      AccT v[2] = {a + q1[j], a + q1[j + 1]};
+      store_group<AccT, 2>(it, Q, o, 0, u0 + j, v);
+    }
+  }
+}
+
 // Brady-Yong block paths: 64 shared rows, G = 64 / 2^L groups, each group a
 // 2^L-row Brady-Yong transform done in two-level passes (one single level
 // first when L is odd).  The last pass goes from registers to global memory.
 // Widths: a pass whose shifts reach `sh` reads sh columns beyond its output,
-// so the staged window is TW + 2^L - 1 and each pass narrows it.
+// so the staged window is TW + 2^L - 1 and each pass narrows it:
+//   L=6: merge4<1> (3), merge4<4> (12), final merge4<16> (48)
+//   L=5: merge2<1> (1), merge4<2> (6),  final merge4<8>  (24)
+//   L=4: merge4<1> (3), final merge4<4> (12)
+//   L=3: merge2<1> (1), final merge4<2> (6)
+//   L=2: final merge4<1> (3);   L=1: final merge2<1> (1)
 template <typename InT, typename AccT>
 __device__ void fused_block(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile, AccT* S,
                             AccT* A) {
@@ -308,59 +360,40 @@ __device__ void fused_block(const FusedParams& p, const FusedItem& it, const Qua
     stage_gathered<AccT>(p, it, Q, u0 - it.c, TW + span, S, p.RS);
   }
   __syncthreads();
-  AccT* src = S;
-  AccT* dst = A;
-  int32_t rs = p.RS, rd = p.RA;
-  int32_t m = 1, rem = span, left = it.L;
-  if (left & 1 && left > 1) {
-    rem -= m;
-    merge2_pass<AccT>(src, rs, dst, rd, m, TW + rem);
-    __syncthreads();
-    AccT* t = src;
-    src = dst;
-    dst = t;
-    int32_t tr = rs;
-    rs = rd;
-    rd = tr;
-    m *= 2;
-    left -= 1;
-  }
-  while (left > 2) {
-    rem -= 3 * m;
-    merge4_pass<AccT>(src, rs, dst, rd, m, TW + rem);
-    __syncthreads();
-    AccT* t = src;
-    src = dst;
-    dst = t;
-    int32_t tr = rs;
-    rs = rd;
-    rd = tr;
-    m *= 4;
-    left -= 2;
-  }
-  // last one or two levels straight from registers to global memory
   const int32_t ncols = min(TW, it.wn - u0);
-  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t nwarps = blockDim.x >> 5;
   AccT* __restrict__ base = (it.final_ ? static_cast<AccT*>(p.out) : static_cast<AccT*>(p.ws)) + it.dst;
-  if (left == 2) {
-    for (int32_t rq = warp; rq < 16; rq += nwarps) {
-      const int32_t g = rq / m, k = rq - g * m;
-      for (int32_t j = lane; j < ncols; j += 32) {
-        AccT v[4];
-        merge4_row<AccT>(src, rs, m, rq, j, v);
-        store_group<AccT, 4>(it, Q, base, g * 4 * m + 4 * k, u0 + j, v);
-      }
-    }
-  } else {
-    for (int32_t rp = warp; rp < 32; rp += nwarps) {
-      const int32_t g = rp / m, k = rp - g * m;
-      for (int32_t j = lane; j < ncols; j += 32) {
-        AccT v[2];
-        merge2_row<AccT>(src, rs, m, rp, j, v);
-        store_group<AccT, 2>(it, Q, base, g * 2 * m + 2 * k, u0 + j, v);
-      }
-    }
+  const int32_t RS = p.RS, RA = p.RA;
+  switch (it.L) {
+    case 6:
+      merge4_pass<1, AccT>(S, RS, A, RA, TW + 60);
+      __syncthreads();
+      merge4_pass<4, AccT>(A, RA, S, RS, TW + 48);
+      __syncthreads();
+      final_merge4<16, AccT>(it, Q, S, RS, base, u0, ncols);
+      break;
+    case 5:
+      merge2_pass<1, AccT>(S, RS, A, RA, TW + 30);
+      __syncthreads();
+      merge4_pass<2, AccT>(A, RA, S, RS, TW + 24);
+      __syncthreads();
+      final_merge4<8, AccT>(it, Q, S, RS, base, u0, ncols);
+      break;
+    case 4:
+      merge4_pass<1, AccT>(S, RS, A, RA, TW + 12);
+      __syncthreads();
+      final_merge4<4, AccT>(it, Q, A, RA, base, u0, ncols);
+      break;
+    case 3:
+      merge2_pass<1, AccT>(S, RS, A, RA, TW + 6);
+      __syncthreads();
+      final_merge4<2, AccT>(it, Q, A, RA, base, u0, ncols);
+      break;
+    case 2:
+      final_merge4<1, AccT>(it, Q, S, RS, base, u0, ncols);
+      break;
+    default:
+      final_merge2_1<AccT>(it, Q, S, RS, base, u0, ncols);
+      break;
   }
 }
 
@@ -433,59 +466,86 @@ __global__ void __launch_bounds__(256) upper_kernel(const RowJob* __restrict__ r
   }
 }
 
-// Spine sum: one CTA per output row of a Split_T root.  Every thread owns U
-// columns and issues the loads of all terms (at most kMaxSpineTerms) before
-// adding, so U x terms loads are in flight per thread.  Consecutive rows read
-// neighbouring part rows, so consecutive CTAs mostly hit L2.
+// Spine sum.  One CTA = kSpineRows consecutive output rows x one column tile
+// of kSpineTile columns; every thread owns 4 columns and loads all terms of a
+// row before adding (term count fixed at compile time per row).  The rows of
+// a CTA read neighbouring rows of the same parts at nearby offsets, so most
+// part reads hit L1; consecutive CTAs share rows through L2.
 constexpr int kMaxSpineTerms = 16;
+constexpr int kSpineRows = 16;
+constexpr int kSpineTile = 1024;
+
+template <int NT, typename AccT>
+__device__ __forceinline__ void spine_tile(const SpineTerm* st, const QuadDesc& Q, const AccT* __restrict__ ws,
+                                           AccT* __restrict__ dst, int32_t u0) {
+  AccT acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) acc[q] = AccT(0);
+  AccT v[NT][4];
+#pragma unroll
+  for (int c = 0; c < NT; c++) {
+    const int32_t off = st[c].off, wpart = st[c].wpart;
+    const AccT* __restrict__ row = ws + st[c].row;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int32_t u = u0 + q * 256 + (int32_t)threadIdx.x;
+      int32_t i = u + off;
+      bool ok = u < Q.W;
+      if (Q.ext) {
+        ok = ok && i >= 0 && i < wpart;
+      } else if (i >= Q.W) {
+        i -= Q.W;
+      }
+      v[c][q] = ok ? __ldg(row + i) : AccT(0);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NT; c++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) acc[q] += v[c][q];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int32_t u = u0 + q * 256 + (int32_t)threadIdx.x;
+    if (u < Q.W) {
+      int32_t X = Q.sigma * u + Q.kappa;
+      if (X < 0) X += Q.W;
+      if (X >= Q.W) X -= Q.W;
+      dst[X] = acc[q];
+    }
+  }
+}
 
 template <typename AccT>
 __global__ void __launch_bounds__(256) spine_kernel(const SpineRow* __restrict__ rows, int64_t nrows,
                                                    const SpineTerm* __restrict__ terms, const AccT* __restrict__ ws,
                                                    AccT* __restrict__ out, QuadDescs quads) {
-  constexpr int U = 2;
-  __shared__ SpineTerm st[kMaxSpineTerms];
-  for (int64_t k = blockIdx.x; k < nrows; k += gridDim.x) {
-    const SpineRow R = rows[k];
-    const QuadDesc& Q = quads.q[R.q];
-    __syncthreads();
-    if ((int32_t)threadIdx.x < R.term_count) st[threadIdx.x] = terms[R.term_begin + threadIdx.x];
-    __syncthreads();
-    AccT* dst = out + R.dst;
-    const int32_t nt = R.term_count;
-    for (int32_t u0 = 0; u0 < Q.W; u0 += (int32_t)blockDim.x * U) {
-      AccT v[kMaxSpineTerms][U];
-#pragma unroll
-      for (int c = 0; c < kMaxSpineTerms; c++) {
-#pragma unroll
-        for (int q = 0; q < U; q++) {
-          v[c][q] = AccT(0);
-          const int32_t u = u0 + q * (int32_t)blockDim.x + (int32_t)threadIdx.x;
-          if (c < nt && u < Q.W) {
-            const SpineTerm& T = st[c];
-            int32_t i = u + T.off;
-            if (Q.ext) {
-              if (i >= 0 && i < T.wpart) v[c][q] = __ldg(ws + T.row + i);
-            } else {
-              if (i >= Q.W) i -= Q.W;
-              v[c][q] = __ldg(ws + T.row + i);
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < U; q++) {
-        AccT acc = v[0][q];
-#pragma unroll
-        for (int c = 1; c < kMaxSpineTerms; c++) acc += v[c][q];
-        const int32_t u = u0 + q * (int32_t)blockDim.x + (int32_t)threadIdx.x;
-        if (u < Q.W) {
-          int32_t X = Q.sigma * u + Q.kappa;
-          if (X < 0) X += Q.W;
-          if (X >= Q.W) X -= Q.W;
-          dst[X] = acc;
-        }
-      }
+  __shared__ SpineTerm st[kSpineRows][kMaxSpineTerms];
+  __shared__ SpineRow sr[kSpineRows];
+  const int64_t r0 = (int64_t)blockIdx.x * kSpineRows;
+  const int32_t u0 = blockIdx.y * kSpineTile;
+  const int32_t nr = (int32_t)(nrows - r0 < kSpineRows ? nrows - r0 : kSpineRows);
+  if (threadIdx.x < nr) sr[threadIdx.x] = rows[r0 + threadIdx.x];
+  __syncthreads();
+  for (int32_t idx = threadIdx.x; idx < nr * kMaxSpineTerms; idx += blockDim.x) {
+    const int32_t r = idx / kMaxSpineTerms, c = idx % kMaxSpineTerms;
+    if (c < sr[r].term_count) st[r][c] = terms[sr[r].term_begin + c];
+  }
+  __syncthreads();
+  for (int32_t r = 0; r < nr; r++) {
+    const QuadDesc& Q = quads.q[sr[r].q];
+    if (u0 >= Q.W) continue;
+    AccT* dst = out + sr[r].dst;
+    switch (sr[r].term_count) {
+#define FHT_SPINE_CASE(N) \
+  case N:                 \
+    spine_tile<N, AccT>(st[r], Q, ws, dst, u0); \
+    break;
+      FHT_SPINE_CASE(1) FHT_SPINE_CASE(2) FHT_SPINE_CASE(3) FHT_SPINE_CASE(4) FHT_SPINE_CASE(5) FHT_SPINE_CASE(6)
+      FHT_SPINE_CASE(7) FHT_SPINE_CASE(8) FHT_SPINE_CASE(9) FHT_SPINE_CASE(10) FHT_SPINE_CASE(11)
+      FHT_SPINE_CASE(12) FHT_SPINE_CASE(13) FHT_SPINE_CASE(14) FHT_SPINE_CASE(15) FHT_SPINE_CASE(16)
+#undef FHT_SPINE_CASE
+      default:
+        break;
     }
   }
 }
@@ -575,9 +635,12 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
       QuadDescs qd;
       for (int q = 0; q < 4; q++) qd.q[q] = P.quad[q];
       const int64_t n = (int64_t)P.spine_rows.size();
+      int32_t maxW = 1;
+      for (int q = 0; q < 4; q++)
+        if (P.cfg.quads & (1u << q)) maxW = std::max(maxW, P.quad[q].W);
+      dim3 sgrid((unsigned)((n + kSpineRows - 1) / kSpineRows), (unsigned)((maxW + kSpineTile - 1) / kSpineTile));
       mark(0);
-      spine_kernel<AccT><<<(unsigned)std::min<int64_t>(n, 1 << 30), 256, 0, st>>>(
-          D.spine_rows, n, D.spine_terms, wsa, static_cast<AccT*>(out), qd);
+      spine_kernel<AccT><<<sgrid, 256, 0, st>>>(D.spine_rows, n, D.spine_terms, wsa, static_cast<AccT*>(out), qd);
       mark(1);
       launch++;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
