@@ -14,388 +14,10 @@
 #include <stdint.h>
 
 #include "fht_desc.h"
+#include "fht_device.cuh"
 #include "fht_launch.hpp"
 
 namespace fht {
-
-struct FusedParams {
-  const void* in;
-  int64_t in_pitch;
-  void* ws;   // AccT workspace base (after the header)
-  void* out;  // AccT output
-  const FusedItem* items;
-  const MergeOp* ops;
-  QuadDesc quad[4];
-  int32_t RP;  // generic path: shared row pitch (elements)
-  int32_t Fm;  // generic path: rows per shared buffer
-  int32_t RS;  // fast path: pitch of the staged input / level-4 rows
-  int32_t RA;  // fast path: pitch of the level-2 rows
-};
-
-template <typename InT, typename AccT>
-__device__ __forceinline__ AccT view_load(const InT* __restrict__ in, int64_t pitch, const QuadDesc& Q, int32_t i,
-                                          int32_t z) {
-  // z: view column, already reduced to [0, L) (cyclic) or checked (extended)
-  if (Q.flip) z = Q.L - 1 - z;
-  const InT v = Q.transpose ? in[(int64_t)z * pitch + i] : in[(int64_t)i * pitch + z];
-  return (AccT)v;
-}
-
-// Stage m view rows [a, a + m) x window columns [x0, x0 + width) into
-// buf (row pitch rp): wrapped (cyclic) or zero-filled (extended).  Loads are
-// issued in batches of U per thread before their shared stores so that several
-// global loads are in flight per thread.
-template <typename InT, typename AccT>
-__device__ __forceinline__ void stage_rows(const FusedParams& p, const QuadDesc& Q, int32_t a, int32_t m, int32_t x0,
-                                           int32_t width, AccT* buf, int32_t rp) {
-  const InT* __restrict__ in = static_cast<const InT*>(p.in);
-  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t nwarps = blockDim.x >> 5;
-  constexpr int U = 8;
-  if (!Q.transpose) {
-    for (int32_t r = warp; r < m; r += nwarps) {
-      AccT* dst = buf + (size_t)r * rp;
-      const InT* __restrict__ rowp = in + (int64_t)(a + r) * p.in_pitch;
-      for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
-        AccT v[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int32_t j = j0 + u * 32 + lane;
-          int32_t z = x0 + j;
-          bool ok = j < width;
-          if (Q.ext) {
-            ok = ok && z >= 0 && z < Q.L;
-          } else if (z >= Q.L) {
-            z = z < 2 * Q.L ? z - Q.L : z % Q.L;  // x0 >= 0 in the cyclic case
-          }
-          if (Q.flip) z = Q.L - 1 - z;
-          v[u] = ok ? (AccT)rowp[z] : AccT(0);
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int32_t j = j0 + u * 32 + lane;
-          if (j < width) dst[j] = v[u];
-        }
-      }
-    }
-  } else {
-    // transposed view: view row r is image column a + r; lanes run along r so
-    // that a warp reads consecutive image columns of one image row.
-    for (int32_t j = warp; j < width; j += nwarps) {
-      int32_t z = x0 + j;
-      bool valid = true;
-      if (Q.ext) {
-        valid = (z >= 0 && z < Q.L);
-      } else {
-        z %= Q.L;
-      }
-      for (int32_t r = lane; r < m; r += 32)
-        buf[(size_t)r * rp + j] = valid ? view_load<InT, AccT>(in, p.in_pitch, Q, a + r, z) : AccT(0);
-    }
-  }
-}
-
-// Store rows [0, m) x columns [0, ncols) of a shared buffer as the node's
-// Hough rows starting at node column u0.
-template <typename AccT>
-__device__ __forceinline__ void store_rows(const FusedParams& p, const FusedItem& it, const QuadDesc& Q,
-                                           const AccT* buf, int32_t rp, int32_t u0, int32_t ncols) {
-  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t nwarps = blockDim.x >> 5;
-  if (!it.final_) {
-    AccT* __restrict__ ws = static_cast<AccT*>(p.ws) + it.dst;
-    for (int32_t r = warp; r < it.m; r += nwarps) {
-      const AccT* s = buf + (size_t)r * rp;
-      AccT* o = ws + (int64_t)r * it.dst_pitch + u0;
-      for (int32_t j = lane; j < ncols; j += 32) o[j] = s[j];
-    }
-  } else {
-    AccT* __restrict__ out = static_cast<AccT*>(p.out) + it.dst;
-    for (int32_t r = warp; r < it.m; r += nwarps) {
-      const AccT* s = buf + (size_t)r * rp;
-      AccT* o = out + (int64_t)r * it.dst_pitch;
-      for (int32_t j = lane; j < ncols; j += 32) {
-        int32_t X = Q.sigma * (u0 + j) + Q.kappa;
-        if (X < 0) X += Q.W;
-        if (X >= Q.W) X -= Q.W;
-        o[X] = s[j];
-      }
-    }
-  }
-}
-
-// Generic path: any subtree of at most F rows, run level by level from its
-// program, ping-ponging between two shared buffers.
-template <typename InT, typename AccT>
-__device__ void fused_generic(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile,
-                              AccT* bufA, AccT* bufB) {
-  const int32_t m = it.m;
-  const int32_t TWin = it.tw + m - 1;
-  const int32_t u0 = tile * it.tw;
-  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t nwarps = blockDim.x >> 5;
-  stage_rows<InT, AccT>(p, Q, it.a, m, u0 - it.c, TWin, bufA, p.RP);
-  AccT* src = bufA;
-  AccT* dst = bufB;
-  const MergeOp* prog = p.ops + it.prog;
-  for (int32_t lev = 0; lev < it.nlev; lev++) {
-    __syncthreads();
-    const MergeOp* ops = prog + (size_t)lev * m;
-    for (int32_t r = warp; r < m; r += nwarps) {
-      const MergeOp op = ops[r];
-      AccT* d = dst + (size_t)r * p.RP;
-      const AccT* a = src + (size_t)op.top * p.RP;
-      if (op.bot >= 0) {
-        const AccT* b = src + (size_t)op.bot * p.RP + op.s;
-#pragma unroll 4
-        for (int32_t j = lane; j < TWin; j += 32) d[j] = a[j] + b[j];
-      } else {
-#pragma unroll 4
-        for (int32_t j = lane; j < TWin; j += 32) d[j] = a[j];
-      }
-    }
-    AccT* tmp = src;
-    src = dst;
-    dst = tmp;
-  }
-  __syncthreads();
-  store_rows<AccT>(p, it, Q, src, p.RP, u0, min(it.tw, it.wn - u0));
-}
-
-// Two Brady-Yong levels at once: four m-row blocks Q0..Q3 (rows base + e m)
-// become one 4m-row block.  With t'' = k and t = 4k + i, level by level
-// (t' = floor(t/2), child slopes floor(t'/2), shifts ceil(t'/2), ceil(t/2)):
-//   out[4k+i][j] = Q0[k][j] + Q1[k][j + k + b] + Q2[k][j + 2k + c]
-//                + Q3[k][j + 3k + b + c],   b = floor(i/2), c = ceil(i/2),
-// so the four outputs of one k need only ten shifted reads.  `rq` = g m + k
-// indexes the 16 (block group, k) pairs of a 64-row block.
-template <typename AccT>
-__device__ __forceinline__ void merge4_at(const AccT* q0, const AccT* q1, const AccT* q2, const AccT* q3,
-                                          int32_t j, AccT o[4]) {
-  const AccT a0 = q0[j];
-  const AccT b0 = q1[j], b1 = q1[j + 1];
-  const AccT c0 = q2[j], c1 = q2[j + 1], c2 = q2[j + 2];
-  const AccT d0 = q3[j], d1 = q3[j + 1], d2 = q3[j + 2], d3 = q3[j + 3];
-  const AccT ab0 = a0 + b0, ab1 = a0 + b1;
-  o[0] = ab0 + (c0 + d0);
-  o[1] = ab0 + (c1 + d1);
-  o[2] = ab1 + (c1 + d2);
-  o[3] = ab1 + (c2 + d3);
-}
-
-// Source row pointers of row-quad rq for blocks of M rows (compile-time M).
-template <int M, typename AccT>
-__device__ __forceinline__ void merge4_ptrs(const AccT* src, int32_t rs, int32_t rq, const AccT*& q0,
-                                            const AccT*& q1, const AccT*& q2, const AccT*& q3, int32_t& r0) {
-  const int32_t g = rq / M, k = rq % M;  // M is a power of two known at compile time
-  q0 = src + (g * 4 * M + k) * rs;
-  q1 = q0 + M * rs + k;
-  q2 = q0 + 2 * M * rs + 2 * k;
-  q3 = q0 + 3 * M * rs + 3 * k;
-  r0 = g * 4 * M + 4 * k;
-}
-
-template <int M, typename AccT>
-__device__ __forceinline__ void merge4_pass(const AccT* src, int32_t rs, AccT* dst, int32_t rd, int32_t width) {
-  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t nwarps = blockDim.x >> 5;
-  for (int32_t rq = warp; rq < 16; rq += nwarps) {
-    const AccT *q0, *q1, *q2, *q3;
-    int32_t r0;
-    merge4_ptrs<M, AccT>(src, rs, rq, q0, q1, q2, q3, r0);
-    AccT* d = dst + r0 * rd;
-#pragma unroll 2
-    for (int32_t j = lane; j < width; j += 32) {
-      AccT o[4];
-      merge4_at<AccT>(q0, q1, q2, q3, j, o);
-      d[j] = o[0];
-      d[rd + j] = o[1];
-      d[2 * rd + j] = o[2];
-      d[3 * rd + j] = o[3];
-    }
-  }
-}
-
-// One Brady-Yong level: two m-row blocks Q0, Q1 (rows base, base + m) become
-// one 2m-row block: t = 2k + i has t1 = t2 = k and shift ceil(t/2) = k + i.
-template <int M, typename AccT>
-__device__ __forceinline__ void merge2_ptrs(const AccT* src, int32_t rs, int32_t rp, const AccT*& q0,
-                                            const AccT*& q1, int32_t& r0) {
-  const int32_t g = rp / M, k = rp % M;
-  q0 = src + (g * 2 * M + k) * rs;
-  q1 = q0 + M * rs + k;
-  r0 = g * 2 * M + 2 * k;
-}
-
-template <int M, typename AccT>
-__device__ __forceinline__ void merge2_pass(const AccT* src, int32_t rs, AccT* dst, int32_t rd, int32_t width) {
-  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t nwarps = blockDim.x >> 5;
-  for (int32_t rp = warp; rp < 32; rp += nwarps) {
-    const AccT *q0, *q1;
-    int32_t r0;
-    merge2_ptrs<M, AccT>(src, rs, rp, q0, q1, r0);
-    AccT* d = dst + r0 * rd;
-    for (int32_t j = lane; j < width; j += 32) {
-      const AccT a = q0[j];
-      d[j] = a + q1[j];
-      d[rd + j] = a + q1[j + 1];
-    }
-  }
-}
-
-// Stage the 64 gathered rows of a band item: shared row r = g B + b holds
-// row K = K0 + g of block b, pre-shifted by K b.  In a perfect band of B
-// blocks the output slope t = K B + i sums, over the blocks, row K of block b
-// at offset K b + pat_B(i)(b) (the Brady-Yong pattern of the B-row transform),
-// so after this staging the band is a B-row Brady-Yong transform per group.
-template <typename AccT>
-__device__ __forceinline__ void stage_gathered(const FusedParams& p, const FusedItem& it, const QuadDesc& Q,
-                                               int32_t x0, int32_t width, AccT* buf, int32_t rp) {
-  const AccT* __restrict__ ws = static_cast<const AccT*>(p.ws);
-  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t nwarps = blockDim.x >> 5;
-  constexpr int U = 8;
-  for (int32_t r = warp; r < 64; r += nwarps) {
-    const int32_t g = r / it.B, b = r - g * it.B;
-    const int32_t K = it.K0 + g;
-    const AccT* __restrict__ row = ws + it.src + (int64_t)(64 * b + K) * it.src_pitch;
-    const int32_t base = x0 + K * b + it.c_src;
-    AccT* dst = buf + (size_t)r * rp;
-    for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
-      AccT v[U];
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int32_t j = j0 + u * 32 + lane;
-        int32_t z = base + j;
-        bool ok = j < width;
-        if (Q.ext) {
-          ok = ok && z >= 0 && z < it.wsrc;
-        } else {
-          z = z % Q.W;  // base >= 0 in the cyclic case
-        }
-        v[u] = ok ? row[z] : AccT(0);
-      }
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int32_t j = j0 + u * 32 + lane;
-        if (j < width) dst[j] = v[u];
-      }
-    }
-  }
-}
-
-// Store the four (or two) outputs of one register group into global rows
-// r0, r0 + 1, ... of the item's destination at node column u0 + j.
-template <typename AccT, int N>
-__device__ __forceinline__ void store_group(const FusedItem& it, const QuadDesc& Q, AccT* base, int32_t r0,
-                                            int32_t u, const AccT* v) {
-  int32_t X = u;
-  if (it.final_) {
-    X = Q.sigma * u + Q.kappa;
-    if (X < 0) X += Q.W;
-    if (X >= Q.W) X -= Q.W;
-  }
-#pragma unroll
-  for (int i = 0; i < N; i++) base[(int64_t)(r0 + i) * it.dst_pitch + X] = v[i];
-}
-
-// Last two levels (merge4 with blocks of M rows) from shared memory straight
-// to global memory.
-template <int M, typename AccT>
-__device__ __forceinline__ void final_merge4(const FusedItem& it, const QuadDesc& Q, const AccT* src, int32_t rs,
-                                             AccT* base, int32_t u0, int32_t ncols) {
-  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t nwarps = blockDim.x >> 5;
-  for (int32_t rq = warp; rq < 16; rq += nwarps) {
-    const AccT *q0, *q1, *q2, *q3;
-    int32_t r0;
-    merge4_ptrs<M, AccT>(src, rs, rq, q0, q1, q2, q3, r0);
-    AccT* o = base + (int64_t)r0 * it.dst_pitch;
-    for (int32_t j = lane; j < ncols; j += 32) {
-      AccT v[4];
-      merge4_at<AccT>(q0, q1, q2, q3, j, v);
-      store_group<AccT, 4>(it, Q, o, 0, u0 + j, v);
-    }
-  }
-}
-
-template <typename AccT>
-__device__ __forceinline__ void final_merge2_1(const FusedItem& it, const QuadDesc& Q, const AccT* src, int32_t rs,
-                                               AccT* base, int32_t u0, int32_t ncols) {
-  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t nwarps = blockDim.x >> 5;
-  for (int32_t rp = warp; rp < 32; rp += nwarps) {
-    const AccT *q0, *q1;
-    int32_t r0;
-    merge2_ptrs<1, AccT>(src, rs, rp, q0, q1, r0);
-    AccT* o = base + (int64_t)r0 * it.dst_pitch;
-    for (int32_t j = lane; j < ncols; j += 32) {
-      const AccT a = q0[j];
-      AccT v[2] = {a + q1[j], a + q1[j + 1]};
-      store_group<AccT, 2>(it, Q, o, 0, u0 + j, v);
-    }
-  }
-}
-
-// Brady-Yong block paths: 64 shared rows, G = 64 / 2^L groups, each group a
-// 2^L-row Brady-Yong transform done in two-level passes (one single level
-// first when L is odd).  The last pass goes from registers to global memory.
-// Widths: a pass whose shifts reach `sh` reads sh columns beyond its output,
-// so the staged window is TW + 2^L - 1 and each pass narrows it:
-//   L=6: merge4<1> (3), merge4<4> (12), final merge4<16> (48)
-//   L=5: merge2<1> (1), merge4<2> (6),  final merge4<8>  (24)
-//   L=4: merge4<1> (3), final merge4<4> (12)
-//   L=3: merge2<1> (1), final merge4<2> (6)
-//   L=2: final merge4<1> (3);   L=1: final merge2<1> (1)
-template <typename InT, typename AccT>
-__device__ void fused_block(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile, AccT* S,
-                            AccT* A) {
-  const int32_t TW = it.tw;
-  const int32_t u0 = tile * TW;
-  const int32_t span = (1 << it.L) - 1;
-  if (it.kind == FUSED_BY64) {
-    stage_rows<InT, AccT>(p, Q, it.a, 64, u0 - it.c, TW + span, S, p.RS);
-  } else {
-    stage_gathered<AccT>(p, it, Q, u0 - it.c, TW + span, S, p.RS);
-  }
-  __syncthreads();
-  const int32_t ncols = min(TW, it.wn - u0);
-  AccT* __restrict__ base = (it.final_ ? static_cast<AccT*>(p.out) : static_cast<AccT*>(p.ws)) + it.dst;
-  const int32_t RS = p.RS, RA = p.RA;
-  switch (it.L) {
-    case 6:
-      merge4_pass<1, AccT>(S, RS, A, RA, TW + 60);
-      __syncthreads();
-      merge4_pass<4, AccT>(A, RA, S, RS, TW + 48);
-      __syncthreads();
-      final_merge4<16, AccT>(it, Q, S, RS, base, u0, ncols);
-      break;
-    case 5:
-      merge2_pass<1, AccT>(S, RS, A, RA, TW + 30);
-      __syncthreads();
-      merge4_pass<2, AccT>(A, RA, S, RS, TW + 24);
-      __syncthreads();
-      final_merge4<8, AccT>(it, Q, S, RS, base, u0, ncols);
-      break;
-    case 4:
-      merge4_pass<1, AccT>(S, RS, A, RA, TW + 12);
-      __syncthreads();
-      final_merge4<4, AccT>(it, Q, A, RA, base, u0, ncols);
-      break;
-    case 3:
-      merge2_pass<1, AccT>(S, RS, A, RA, TW + 6);
-      __syncthreads();
-      final_merge4<2, AccT>(it, Q, A, RA, base, u0, ncols);
-      break;
-    case 2:
-      final_merge4<1, AccT>(it, Q, S, RS, base, u0, ncols);
-      break;
-    default:
-      final_merge2_1<AccT>(it, Q, S, RS, base, u0, ncols);
-      break;
-  }
-}
 
 template <typename InT, typename AccT>
 __global__ void __launch_bounds__(512, 2) fused_kernel(FusedParams p) {
@@ -406,21 +28,9 @@ __global__ void __launch_bounds__(512, 2) fused_kernel(FusedParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AccT* sm = reinterpret_cast<AccT*>(smem_raw);
   if (it.kind != FUSED_GENERIC) {
-    fused_block<InT, AccT>(p, it, Q, tile, sm, sm + (size_t)64 * p.RS);
+    fused_block<false, InT, AccT>(p, it, Q, tile, sm, sm + (size_t)64 * p.RS);
   } else {
     fused_generic<InT, AccT>(p, it, Q, tile, sm, sm + (size_t)p.Fm * p.RP);
-  }
-}
-
-template <typename AccT>
-__device__ __forceinline__ void store_row(AccT* dst, const RowJob& J, bool fin, int32_t u, AccT v) {
-  if (fin) {
-    int32_t X = (J.flags & ROW_NEG) ? J.kappa - u : u + J.kappa;
-    if (X < 0) X += J.W;
-    if (X >= J.W) X -= J.W;
-    dst[X] = v;
-  } else {
-    dst[u] = v;
   }
 }
 
@@ -466,55 +76,6 @@ __global__ void __launch_bounds__(256) upper_kernel(const RowJob* __restrict__ r
   }
 }
 
-// Spine sum.  One CTA = kSpineRows consecutive output rows x one column tile
-// of kSpineTile columns; every thread owns 4 columns and loads all terms of a
-// row before adding (term count fixed at compile time per row).  The rows of
-// a CTA read neighbouring rows of the same parts at nearby offsets, so most
-// part reads hit L1; consecutive CTAs share rows through L2.
-constexpr int kMaxSpineTerms = 16;
-constexpr int kSpineRows = 16;
-constexpr int kSpineTile = 1024;
-
-template <int NT, typename AccT>
-__device__ __forceinline__ void spine_tile(const SpineTerm* st, const QuadDesc& Q, const AccT* __restrict__ ws,
-                                           AccT* __restrict__ dst, int32_t u0) {
-  AccT acc[4];
-#pragma unroll
-  for (int q = 0; q < 4; q++) acc[q] = AccT(0);
-  AccT v[NT][4];
-#pragma unroll
-  for (int c = 0; c < NT; c++) {
-    const int32_t off = st[c].off, wpart = st[c].wpart;
-    const AccT* __restrict__ row = ws + st[c].row;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int32_t u = u0 + q * 256 + (int32_t)threadIdx.x;
-      int32_t i = u + off;
-      bool ok = u < Q.W;
-      if (Q.ext) {
-        ok = ok && i >= 0 && i < wpart;
-      } else if (i >= Q.W) {
-        i -= Q.W;
-      }
-      v[c][q] = ok ? __ldg(row + i) : AccT(0);
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < NT; c++)
-#pragma unroll
-    for (int q = 0; q < 4; q++) acc[q] += v[c][q];
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    const int32_t u = u0 + q * 256 + (int32_t)threadIdx.x;
-    if (u < Q.W) {
-      int32_t X = Q.sigma * u + Q.kappa;
-      if (X < 0) X += Q.W;
-      if (X >= Q.W) X -= Q.W;
-      dst[X] = acc[q];
-    }
-  }
-}
-
 template <typename AccT>
 __global__ void __launch_bounds__(256) spine_kernel(const SpineRow* __restrict__ rows, int64_t nrows,
                                                    const SpineTerm* __restrict__ terms, const AccT* __restrict__ ws,
@@ -538,7 +99,7 @@ __global__ void __launch_bounds__(256) spine_kernel(const SpineRow* __restrict__
     switch (sr[r].term_count) {
 #define FHT_SPINE_CASE(N) \
   case N:                 \
-    spine_tile<N, AccT>(st[r], Q, ws, dst, u0); \
+    spine_tile<false, N, AccT>(st[r], Q, ws, dst, u0); \
     break;
       FHT_SPINE_CASE(1) FHT_SPINE_CASE(2) FHT_SPINE_CASE(3) FHT_SPINE_CASE(4) FHT_SPINE_CASE(5) FHT_SPINE_CASE(6)
       FHT_SPINE_CASE(7) FHT_SPINE_CASE(8) FHT_SPINE_CASE(9) FHT_SPINE_CASE(10) FHT_SPINE_CASE(11)
