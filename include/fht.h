@@ -159,6 +159,53 @@ fht_status fht_forward_noalloc(fht_plan_t plan, const void* d_in, int64_t in_pit
 fht_status fht_adjoint(fht_plan_t plan, const void* d_gout, void* d_gin, int64_t gin_pitch, void* d_ws,
                        size_t ws_bytes, void* stream);
 
+/* ---- batched transforms: many images of uneven sizes in one persistent launch ----
+ *
+ * A job is one image: its plan (any size; all jobs of one submit share the
+ * dtype and the queue's device), input, output and workspace (at least the
+ * plan's workspace_bytes, 256-byte aligned, not shared with another job of
+ * the same submit).  fht_submit lists the work units of every job phase by
+ * phase (fused subtree tiles, then band tiles, then spine row groups, or one
+ * phase per tree height for per-height plans) and runs them all in one
+ * persistent launch: CTAs take units from a device counter; a unit of a later
+ * phase waits for the earlier phases of its own job through a per-job
+ * completion counter.  Waits are bounded (fht_queue_set_wait_limit, default
+ * 2 s); a wait that gives up records FHT_ERR_TIMEOUT in the queue's status
+ * word (read with fht_queue_status) and the kernel still returns.
+ * Submits to one queue must be ordered (one stream): they share its device
+ * tables.  Use one queue per stream for concurrent batches. */
+typedef struct {
+  fht_plan_t plan;
+  const void* d_in;
+  int64_t in_pitch; /* elements */
+  void* d_out;
+  void* d_ws;
+  size_t ws_bytes;
+  uint64_t tag;     /* returned by fht_queue_poll when the job's submit has finished */
+  uint32_t flags;   /* 0, or FHT_JOB_WITHHOLD_DEPENDENCY */
+  uint32_t reserved;
+} fht_job;
+
+/* Fault injection for tests of the bounded wait: the job's later-phase units
+ * wait for one unit more than the job has, so their waits run out and the
+ * submit ends with FHT_ERR_TIMEOUT in the status word (the job's output is
+ * then incomplete).  No GPU fault is involved. */
+#define FHT_JOB_WITHHOLD_DEPENDENCY 1u
+
+/* Create a queue on `device` holding up to max_jobs jobs and max_units work
+ * units per submit (device tables and pinned staging are allocated here). */
+fht_status fht_queue_create(fht_queue_t* q, int device, int32_t max_jobs, int64_t max_units);
+fht_status fht_queue_set_wait_limit(fht_queue_t q, int64_t wait_ns);
+/* Enqueue one persistent launch over all jobs on `stream` (cudaStream_t).
+ * FHT_ERR_BUSY when the jobs or their units exceed the queue's capacity. */
+fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* stream);
+/* Non-blocking: copies up to `cap` tags of jobs whose submit has finished. */
+fht_status fht_queue_poll(fht_queue_t q, uint64_t* done_tags, int32_t cap, int32_t* ndone);
+/* Synchronises `stream` and returns the queue's status word (FHT_OK or FHT_ERR_TIMEOUT). */
+fht_status fht_queue_status(fht_queue_t q, void* stream);
+fht_status fht_queue_reset_status(fht_queue_t q, void* stream);
+fht_status fht_queue_destroy(fht_queue_t q);
+
 /* Host-side verification of a plan: walks every table entry and checks that
  * each input, workspace, output and shared-memory index the kernels derive
  * from it lies inside its buffer.  No device access; works on host-only plans.

@@ -36,6 +36,14 @@ class fht_plan_info_t(ctypes.Structure):
                 ("upper_passes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class fht_job(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("d_in", ctypes.c_void_p), ("in_pitch", ctypes.c_int64),
+                ("d_out", ctypes.c_void_p), ("d_ws", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t),
+                ("tag", ctypes.c_uint64), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+FHT_JOB_WITHHOLD_DEPENDENCY = 1
+
 # name -> (restype, argtypes); mirrors include/fht.h
 _vp, _i32, _u32, _i64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_size_t
 SIGNATURES = {
@@ -50,6 +58,13 @@ SIGNATURES = {
     "fht_forward_timed": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp), _i32]),
     "fht_forward_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "fht_plan_destroy": (ctypes.c_int, [_vp]),
+    "fht_queue_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i32, _i64]),
+    "fht_queue_set_wait_limit": (ctypes.c_int, [_vp, _i64]),
+    "fht_submit": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(fht_job), _vp]),
+    "fht_queue_poll": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), _i32, ctypes.POINTER(_i32)]),
+    "fht_queue_status": (ctypes.c_int, [_vp, _vp]),
+    "fht_queue_reset_status": (ctypes.c_int, [_vp, _vp]),
+    "fht_queue_destroy": (ctypes.c_int, [_vp]),
     "fht_ws_status": (ctypes.c_int, [_vp, _vp]),
     "fht_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fht_last_error": (ctypes.c_char_p, []),

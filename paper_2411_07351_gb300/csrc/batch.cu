@@ -1,0 +1,493 @@
+// Batched transform: many images of uneven sizes in one persistent launch.
+//
+// The host turns every job (a plan + its buffers) into work units -- fused
+// subtree tiles, band tiles, spine row groups, or per-height row groups --
+// and lists them phase by phase across all jobs (all fused tiles of all jobs
+// first, then all band tiles, ...).  Persistent CTAs take units in list order
+// from one device counter.  A unit of a later phase of job j first waits until
+// job j's earlier-phase units have all finished (a per-job completion
+// counter).  Because units are taken in list order and a unit only waits for
+// units listed before it, which are already held by running CTAs, the wait
+// always ends; it is still bounded by a %globaltimer deadline, after which the
+// kernel records FHT_ERR_TIMEOUT in the queue's status word, skips the unit's
+// work and carries on, so a lost dependency can never hang the GPU.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fht.h"
+#include "fht_desc.h"
+#include "fht_device.cuh"
+#include "fht_launch.hpp"
+
+namespace fht {
+
+struct BatchJob {
+  FusedParams fp;                 // input, output, workspace, items, quadrants, geometry
+  const FusedItem* band_items;
+  const SpineRow* spine_rows;
+  const SpineTerm* spine_terms;
+  const RowJob* rows;
+};
+
+enum : int32_t { UNIT_FUSED = 0, UNIT_BAND = 1, UNIT_SPINE = 2, UNIT_UPPER = 3 };
+
+struct BatchUnit {
+  int32_t job;
+  int32_t kind;
+  int32_t index;  // fused / band item, first spine row, or first row job
+  int32_t tile;   // column tile (fused, band, spine) or row count (upper)
+  int32_t need;   // units of this job that must be finished first
+};
+
+constexpr int kUpperRowsPerUnit = 8;
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <typename AccT>
+__device__ void batch_upper_rows(const RowJob* __restrict__ rows, int32_t first, int32_t count, AccT* ws,
+                                 AccT* out) {
+  for (int32_t k = first; k < first + count; k++) {
+    const RowJob J = rows[k];
+    const AccT* top = ws + J.top;
+    const AccT* bot = ws + J.bot;
+    const bool fin = J.flags & ROW_FINAL;
+    const bool ext = J.flags & ROW_EXT;
+    AccT* dst = (fin ? out : ws) + J.dst;
+    for (int32_t u = threadIdx.x; u < J.wout; u += blockDim.x) {
+      AccT a = AccT(0), b = AccT(0);
+      if (ext) {
+        const int32_t i = u + J.dtop, i2 = u + J.dbot;
+        if (i >= 0 && i < J.wtop) a = __ldcg(top + i);
+        if (i2 >= 0 && i2 < J.wbot) b = __ldcg(bot + i2);
+      } else {
+        int32_t i2 = u + J.dbot;
+        if (i2 >= J.W) i2 -= J.W;
+        a = __ldcg(top + u);
+        b = __ldcg(bot + i2);
+      }
+      store_row(dst, J, fin, u, a + b);
+    }
+  }
+}
+
+template <typename AccT>
+__device__ void batch_spine(const BatchJob& jb, int32_t r0, int32_t tile, SpineTerm (*st)[kMaxSpineTerms],
+                            SpineRow* sr, int64_t nrows) {
+  const AccT* ws = static_cast<const AccT*>(jb.fp.ws);
+  AccT* out = static_cast<AccT*>(jb.fp.out);
+  const int32_t u0 = tile * kSpineTile;
+  const int32_t nr = (int32_t)(nrows - r0 < kSpineRows ? nrows - r0 : kSpineRows);
+  if ((int32_t)threadIdx.x < nr) sr[threadIdx.x] = jb.spine_rows[r0 + threadIdx.x];
+  __syncthreads();
+  for (int32_t idx = threadIdx.x; idx < nr * kMaxSpineTerms; idx += blockDim.x) {
+    const int32_t r = idx / kMaxSpineTerms, c = idx % kMaxSpineTerms;
+    if (c < sr[r].term_count) st[r][c] = jb.spine_terms[sr[r].term_begin + c];
+  }
+  __syncthreads();
+  if (threadIdx.x < 256) {
+    for (int32_t r = 0; r < nr; r++) {
+      const QuadDesc& Q = jb.fp.quad[sr[r].q];
+      if (u0 >= Q.W) continue;
+      AccT* dst = out + sr[r].dst;
+      switch (sr[r].term_count) {
+#define FHT_BATCH_SPINE_CASE(N) \
+  case N:                       \
+    spine_tile<true, N, AccT>(st[r], Q, ws, dst, u0); \
+    break;
+        FHT_BATCH_SPINE_CASE(1) FHT_BATCH_SPINE_CASE(2) FHT_BATCH_SPINE_CASE(3) FHT_BATCH_SPINE_CASE(4)
+        FHT_BATCH_SPINE_CASE(5) FHT_BATCH_SPINE_CASE(6) FHT_BATCH_SPINE_CASE(7) FHT_BATCH_SPINE_CASE(8)
+        FHT_BATCH_SPINE_CASE(9) FHT_BATCH_SPINE_CASE(10) FHT_BATCH_SPINE_CASE(11) FHT_BATCH_SPINE_CASE(12)
+        FHT_BATCH_SPINE_CASE(13) FHT_BATCH_SPINE_CASE(14) FHT_BATCH_SPINE_CASE(15) FHT_BATCH_SPINE_CASE(16)
+#undef FHT_BATCH_SPINE_CASE
+        default:
+          break;
+      }
+    }
+  }
+}
+
+// counters[0]: next unit; counters[1 + j]: finished units of job j.
+template <typename InT, typename AccT>
+__global__ void __launch_bounds__(512, 2) batch_kernel(const BatchJob* __restrict__ jobs,
+                                                      const BatchUnit* __restrict__ units, int32_t nunits,
+                                                      const int64_t* __restrict__ spine_nrows, int32_t* counters,
+                                                      int32_t* status, int64_t wait_ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int32_t s_unit;
+  __shared__ int32_t s_ok;
+  __shared__ SpineTerm st[kSpineRows][kMaxSpineTerms];
+  __shared__ SpineRow sr[kSpineRows];
+  AccT* sm = reinterpret_cast<AccT*>(smem_raw);
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(&counters[0], 1);
+    __syncthreads();
+    const int32_t ui = s_unit;
+    if (ui >= nunits) break;
+    const BatchUnit U = units[ui];
+    if (threadIdx.x == 0) {
+      int32_t ok = 1;
+      if (U.need > 0) {
+        const int32_t* done = &counters[1 + U.job];
+        if (ld_acquire(done) < U.need) {
+          const uint64_t t0 = global_ns();
+          while (ld_acquire(done) < U.need) {
+            if (*(volatile int32_t*)status != 0 || global_ns() - t0 > (uint64_t)wait_ns) {
+              atomicCAS(status, 0, (int32_t)FHT_ERR_TIMEOUT);
+              ok = 0;
+              break;
+            }
+            __nanosleep(200);
+          }
+        }
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (s_ok) {
+      const BatchJob& jb = jobs[U.job];
+      switch (U.kind) {
+        case UNIT_FUSED:
+        case UNIT_BAND: {
+          const FusedItem it = (U.kind == UNIT_FUSED ? jb.fp.items : jb.band_items)[U.index];
+          const QuadDesc& Q = jb.fp.quad[it.q];
+          if (U.tile < it.ntiles) {
+            if (it.kind != FUSED_GENERIC) {
+              fused_block<true, InT, AccT>(jb.fp, it, Q, U.tile, sm, sm + (size_t)64 * jb.fp.RS);
+            } else {
+              fused_generic<InT, AccT>(jb.fp, it, Q, U.tile, sm, sm + (size_t)jb.fp.Fm * jb.fp.RP);
+            }
+          }
+          break;
+        }
+        case UNIT_SPINE:
+          batch_spine<AccT>(jb, U.index, U.tile, st, sr, spine_nrows[U.job]);
+          break;
+        default:
+          batch_upper_rows<AccT>(jb.rows, U.index, U.tile, static_cast<AccT*>(jb.fp.ws),
+                                 static_cast<AccT*>(jb.fp.out));
+          break;
+      }
+    }
+    // publish this unit's writes before counting it done (skipped units are
+    // counted too, so that nothing waits on them)
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&counters[1 + U.job], 1);
+  }
+}
+
+}  // namespace fht
+
+// ----------------------------------------------------------------------------
+// host side
+// ----------------------------------------------------------------------------
+fht_status fht_capi_fail(fht_status st, const std::string& msg);
+const fht::DevicePlan* fht_capi_device_plan(fht_plan_t plan);
+
+struct fht_queue_s {
+  int device = 0;
+  int32_t max_jobs = 0;
+  int64_t max_units = 0;
+  int64_t wait_ns = 2000000000;  // 2 s
+  fht::BatchJob* d_jobs = nullptr;
+  fht::BatchUnit* d_units = nullptr;
+  int64_t* d_spine_nrows = nullptr;
+  int32_t* d_counters = nullptr;  // [1 + max_jobs]
+  int32_t* d_status = nullptr;
+  fht::BatchJob* h_jobs = nullptr;  // pinned staging
+  fht::BatchUnit* h_units = nullptr;
+  int64_t* h_spine_nrows = nullptr;
+  cudaEvent_t staged = nullptr;     // staging buffers free again after this event
+  bool staged_pending = false;
+  int32_t last_units = 0;
+  std::vector<uint64_t> pending_tags, done_tags;
+  cudaEvent_t done_evt = nullptr;
+  bool done_pending = false;
+};
+
+namespace {
+
+struct QueueDeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit QueueDeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~QueueDeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+void queue_free(fht_queue_s* q) {
+  if (q->d_jobs) cudaFree(q->d_jobs);
+  if (q->d_units) cudaFree(q->d_units);
+  if (q->d_spine_nrows) cudaFree(q->d_spine_nrows);
+  if (q->d_counters) cudaFree(q->d_counters);
+  if (q->d_status) cudaFree(q->d_status);
+  if (q->h_jobs) cudaFreeHost(q->h_jobs);
+  if (q->h_units) cudaFreeHost(q->h_units);
+  if (q->h_spine_nrows) cudaFreeHost(q->h_spine_nrows);
+  if (q->staged) cudaEventDestroy(q->staged);
+  if (q->done_evt) cudaEventDestroy(q->done_evt);
+}
+
+template <typename InT, typename AccT>
+cudaError_t launch_batch(fht_queue_s* q, int32_t nunits, size_t smem, cudaStream_t st) {
+  auto kfn = fht::batch_kernel<InT, AccT>;
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, sms = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 512, smem)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, q->device)) != cudaSuccess) return e;
+  const int grid = std::max(1, std::min<int>(nunits, std::max(1, per_sm) * sms));
+  kfn<<<grid, 512, smem, st>>>(q->d_jobs, q->d_units, nunits, q->d_spine_nrows, q->d_counters, q->d_status,
+                               q->wait_ns);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+fht_status fht_queue_create(fht_queue_t* out, int device, int32_t max_jobs, int64_t max_units) {
+  if (!out) return fht_capi_fail(FHT_ERR_INVALID, "fht_queue_create: out is NULL");
+  *out = nullptr;
+  if (max_jobs < 1 || max_units < 1 || max_units > INT32_MAX)
+    return fht_capi_fail(FHT_ERR_INVALID, "fht_queue_create: bad capacity");
+  fht_queue_s* q = new (std::nothrow) fht_queue_s();
+  if (!q) return fht_capi_fail(FHT_ERR_NOMEM, "fht_queue_create: host allocation failed");
+  q->device = device;
+  q->max_jobs = max_jobs;
+  q->max_units = max_units;
+  QueueDeviceGuard g(device);
+  if (!g.ok) {
+    delete q;
+    return fht_capi_fail(FHT_ERR_CUDA, "fht_queue_create: cannot select device");
+  }
+  cudaError_t e;
+  if ((e = cudaMalloc(&q->d_jobs, sizeof(fht::BatchJob) * max_jobs)) != cudaSuccess ||
+      (e = cudaMalloc(&q->d_units, sizeof(fht::BatchUnit) * max_units)) != cudaSuccess ||
+      (e = cudaMalloc(&q->d_spine_nrows, sizeof(int64_t) * max_jobs)) != cudaSuccess ||
+      (e = cudaMalloc(&q->d_counters, sizeof(int32_t) * (1 + (size_t)max_jobs))) != cudaSuccess ||
+      (e = cudaMalloc(&q->d_status, 256)) != cudaSuccess ||
+      (e = cudaMallocHost(&q->h_jobs, sizeof(fht::BatchJob) * max_jobs)) != cudaSuccess ||
+      (e = cudaMallocHost(&q->h_units, sizeof(fht::BatchUnit) * max_units)) != cudaSuccess ||
+      (e = cudaMallocHost(&q->h_spine_nrows, sizeof(int64_t) * max_jobs)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&q->staged, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&q->done_evt, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaMemset(q->d_status, 0, 256)) != cudaSuccess) {
+    queue_free(q);
+    delete q;
+    return fht_capi_fail(e == cudaErrorMemoryAllocation ? FHT_ERR_NOMEM : FHT_ERR_CUDA,
+                         std::string("fht_queue_create: ") + cudaGetErrorString(e));
+  }
+  *out = q;
+  return FHT_OK;
+}
+
+fht_status fht_queue_set_wait_limit(fht_queue_t q, int64_t wait_ns) {
+  if (!q || wait_ns < 1) return fht_capi_fail(FHT_ERR_INVALID, "fht_queue_set_wait_limit: bad argument");
+  q->wait_ns = wait_ns;
+  return FHT_OK;
+}
+
+fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* stream) {
+  if (!q) return fht_capi_fail(FHT_ERR_INVALID, "fht_submit: queue is NULL");
+  if (njobs < 1 || !jobs) return fht_capi_fail(FHT_ERR_INVALID, "fht_submit: no jobs");
+  if (njobs > q->max_jobs) return fht_capi_fail(FHT_ERR_BUSY, "fht_submit: more jobs than the queue holds");
+  cudaStream_t st = (cudaStream_t)stream;
+  QueueDeviceGuard g(q->device);
+  if (!g.ok) return fht_capi_fail(FHT_ERR_CUDA, "fht_submit: cannot select the queue's device");
+  // the staging buffers of the previous submit must have been copied out
+  if (q->staged_pending) {
+    cudaError_t e = cudaEventSynchronize(q->staged);
+    if (e != cudaSuccess) return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_submit: ") + cudaGetErrorString(e));
+    q->staged_pending = false;
+  }
+  int32_t dtype = -1;
+  size_t smem = 0;
+  int64_t nunits = 0;
+  // pass 1: validate and describe the jobs
+  for (int32_t j = 0; j < njobs; j++) {
+    const fht_job& J = jobs[j];
+    const fht::DevicePlan* D = fht_capi_device_plan(J.plan);
+    if (!D) return fht_capi_fail(FHT_ERR_INVALID, "fht_submit: job " + std::to_string(j) + " has no plan");
+    const fht::HostPlan& P = *D->host;
+    if (D->device != q->device)
+      return fht_capi_fail(FHT_ERR_INVALID, "fht_submit: job " + std::to_string(j) + " plan is on another device");
+    if (dtype < 0) dtype = P.cfg.dtype;
+    if (P.cfg.dtype != dtype) return fht_capi_fail(FHT_ERR_INVALID, "fht_submit: jobs of different dtypes");
+    if (!J.d_in || !J.d_out || !J.d_ws || J.in_pitch < P.cfg.w || J.ws_bytes < P.ws_bytes ||
+        ((uintptr_t)J.d_ws) % 256)
+      return fht_capi_fail(FHT_ERR_INVALID, "fht_submit: job " + std::to_string(j) + " buffers");
+    fht::BatchJob& B = q->h_jobs[j];
+    memset(&B, 0, sizeof(B));
+    B.fp.in = J.d_in;
+    B.fp.in_pitch = J.in_pitch;
+    B.fp.ws = static_cast<unsigned char*>(J.d_ws) + fht::kWsHeader;
+    B.fp.out = J.d_out;
+    B.fp.items = D->fused;
+    B.fp.ops = D->ops;
+    for (int k = 0; k < 4; k++) B.fp.quad[k] = P.quad[k];
+    B.fp.RP = D->geo.RP;
+    B.fp.Fm = D->geo.Fm;
+    B.fp.RS = D->geo.RS;
+    B.fp.RA = D->geo.RA;
+    B.band_items = D->band_items;
+    B.spine_rows = D->spine_rows;
+    B.spine_terms = D->spine_terms;
+    B.rows = D->rows;
+    q->h_spine_nrows[j] = (int64_t)P.spine_rows.size();
+    smem = std::max(smem, D->geo.smem);
+  }
+  // pass 2: units, phase by phase across all jobs
+  std::vector<int32_t> done_before(njobs, 0);
+  auto push = [&](int32_t job, int32_t kind, int32_t index, int32_t tile, int32_t need) -> bool {
+    if (nunits >= q->max_units) return false;
+    q->h_units[nunits++] = fht::BatchUnit{job, kind, index, tile, need};
+    return true;
+  };
+  int32_t max_phase = 0;
+  for (int32_t j = 0; j < njobs; j++) {
+    const fht::HostPlan& P = *fht_capi_device_plan(jobs[j].plan)->host;
+    max_phase = std::max<int32_t>(max_phase, P.bands ? 2 : (int32_t)P.pass_begin.size() - 1);
+  }
+  std::vector<int32_t> phase_units(njobs, 0);
+  for (int32_t phase = 0; phase <= max_phase; phase++) {
+    for (int32_t j = 0; j < njobs; j++) {
+      const fht::HostPlan& P = *fht_capi_device_plan(jobs[j].plan)->host;
+      const int32_t need = done_before[j];
+      const bool skip_dep = (jobs[j].flags & FHT_JOB_WITHHOLD_DEPENDENCY) != 0 && phase > 0;
+      const int32_t n = need + (skip_dep ? 1 : 0);  // a dependency nothing satisfies
+      int32_t count = 0;
+      bool ok = true;
+      if (phase == 0) {
+        for (size_t i = 0; i < P.fused.size() && ok; i++)
+          for (int32_t t = 0; t < P.fused[i].ntiles && ok; t++, count++) ok = push(j, fht::UNIT_FUSED, (int32_t)i, t, 0);
+      } else if (P.bands) {
+        if (phase == 1) {
+          for (size_t i = 0; i < P.band_items.size() && ok; i++)
+            for (int32_t t = 0; t < P.band_items[i].ntiles && ok; t++, count++)
+              ok = push(j, fht::UNIT_BAND, (int32_t)i, t, n);
+        } else if (phase == 2 && !P.spine_rows.empty()) {
+          int32_t maxW = 1;
+          for (int k = 0; k < 4; k++)
+            if (P.cfg.quads & (1u << k)) maxW = std::max(maxW, P.quad[k].W);
+          const int32_t tiles = (maxW + fht::kSpineTile - 1) / fht::kSpineTile;
+          for (int32_t t = 0; t < tiles && ok; t++)
+            for (size_t r = 0; r < P.spine_rows.size() && ok; r += fht::kSpineRows, count++)
+              ok = push(j, fht::UNIT_SPINE, (int32_t)r, t, n);
+        }
+      } else if (phase < (int32_t)P.pass_begin.size()) {
+        const int64_t b = P.pass_begin[phase - 1], e = P.pass_begin[phase];
+        for (int64_t r = b; r < e && ok; r += fht::kUpperRowsPerUnit, count++)
+          ok = push(j, fht::UNIT_UPPER, (int32_t)r, (int32_t)std::min<int64_t>(fht::kUpperRowsPerUnit, e - r), n);
+      }
+      if (!ok) return fht_capi_fail(FHT_ERR_BUSY, "fht_submit: more work units than the queue holds");
+      done_before[j] += count;
+    }
+  }
+  if (nunits == 0) return FHT_OK;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(q->d_jobs, q->h_jobs, sizeof(fht::BatchJob) * njobs, cudaMemcpyHostToDevice, st)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(q->d_units, q->h_units, sizeof(fht::BatchUnit) * nunits, cudaMemcpyHostToDevice, st)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(q->d_spine_nrows, q->h_spine_nrows, sizeof(int64_t) * njobs, cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(q->d_counters, 0, sizeof(int32_t) * (1 + (size_t)njobs), st)) != cudaSuccess ||
+      (e = cudaEventRecord(q->staged, st)) != cudaSuccess)
+    return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_submit: ") + cudaGetErrorString(e));
+  q->staged_pending = true;
+  switch (dtype) {
+    case 0:
+      e = launch_batch<uint8_t, int32_t>(q, (int32_t)nunits, smem, st);
+      break;
+    case 1:
+      e = launch_batch<int32_t, int32_t>(q, (int32_t)nunits, smem, st);
+      break;
+    case 2:
+      e = launch_batch<float, float>(q, (int32_t)nunits, smem, st);
+      break;
+    default:
+      e = launch_batch<double, double>(q, (int32_t)nunits, smem, st);
+      break;
+  }
+  if (e != cudaSuccess) return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_submit: ") + cudaGetErrorString(e));
+  q->last_units = (int32_t)nunits;
+  for (int32_t j = 0; j < njobs; j++) q->pending_tags.push_back(jobs[j].tag);
+  if ((e = cudaEventRecord(q->done_evt, st)) != cudaSuccess)
+    return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_submit: ") + cudaGetErrorString(e));
+  q->done_pending = true;
+  return FHT_OK;
+}
+
+fht_status fht_queue_poll(fht_queue_t q, uint64_t* done_tags, int32_t cap, int32_t* ndone) {
+  if (!q || !ndone || (cap > 0 && !done_tags)) return fht_capi_fail(FHT_ERR_INVALID, "fht_queue_poll: bad argument");
+  *ndone = 0;
+  QueueDeviceGuard g(q->device);
+  if (q->done_pending) {
+    cudaError_t e = cudaEventQuery(q->done_evt);
+    if (e == cudaSuccess) {
+      q->done_tags.insert(q->done_tags.end(), q->pending_tags.begin(), q->pending_tags.end());
+      q->pending_tags.clear();
+      q->done_pending = false;
+    } else if (e != cudaErrorNotReady) {
+      return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_queue_poll: ") + cudaGetErrorString(e));
+    }
+  }
+  const int32_t n = std::min<int32_t>(cap, (int32_t)q->done_tags.size());
+  for (int32_t i = 0; i < n; i++) done_tags[i] = q->done_tags[i];
+  q->done_tags.erase(q->done_tags.begin(), q->done_tags.begin() + n);
+  *ndone = n;
+  return FHT_OK;
+}
+
+fht_status fht_queue_status(fht_queue_t q, void* stream) {
+  if (!q) return fht_capi_fail(FHT_ERR_INVALID, "fht_queue_status: queue is NULL");
+  QueueDeviceGuard g(q->device);
+  int32_t word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, q->d_status, sizeof(word), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_queue_status: ") + cudaGetErrorString(e));
+  if (word == 0) return FHT_OK;
+  return fht_capi_fail((fht_status)word, "fht_queue_status: a batch wait gave up (dependency never finished)");
+}
+
+fht_status fht_queue_reset_status(fht_queue_t q, void* stream) {
+  if (!q) return fht_capi_fail(FHT_ERR_INVALID, "fht_queue_reset_status: queue is NULL");
+  QueueDeviceGuard g(q->device);
+  cudaError_t e = cudaMemsetAsync(q->d_status, 0, 256, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_queue_reset_status: ") + cudaGetErrorString(e));
+  return FHT_OK;
+}
+
+fht_status fht_queue_destroy(fht_queue_t q) {
+  if (!q) return FHT_OK;
+  {
+    QueueDeviceGuard g(q->device);
+    cudaDeviceSynchronize();
+    queue_free(q);
+  }
+  delete q;
+  return FHT_OK;
+}
+
+}  // extern "C"

@@ -56,9 +56,29 @@ __device__ __forceinline__ void stage_rows(const FusedParams& p, const QuadDesc&
   const int32_t nwarps = blockDim.x >> 5;
   constexpr int U = 8;
   if (!Q.transpose) {
+    // the window needs no wrap and no zero fill: plain loads from one pointer
+    const bool inside = x0 >= 0 && x0 + width <= Q.L;
     for (int32_t r = warp; r < m; r += nwarps) {
       AccT* dst = buf + (size_t)r * rp;
       const InT* __restrict__ rowp = in + (int64_t)(a + r) * p.in_pitch;
+      if (inside) {
+        const int32_t step = Q.flip ? -1 : 1;
+        const InT* __restrict__ src = rowp + (Q.flip ? Q.L - 1 - x0 : x0) + step * lane;
+        for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
+          AccT v[U];
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            const int32_t j = j0 + u * 32;
+            v[u] = (j + lane < width) ? (AccT)src[step * j] : AccT(0);
+          }
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            const int32_t j = j0 + u * 32 + lane;
+            if (j < width) dst[j] = v[u];
+          }
+        }
+        continue;
+      }
       for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
         AccT v[U];
 #pragma unroll
@@ -130,7 +150,7 @@ __device__ __forceinline__ void store_rows(const FusedParams& p, const FusedItem
 // Generic path: any subtree of at most F rows, run level by level from its
 // program, ping-ponging between two shared buffers.
 template <typename InT, typename AccT>
-__device__ void fused_generic(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile,
+__device__ __forceinline__ void fused_generic(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile,
                               AccT* bufA, AccT* bufB) {
   const int32_t m = it.m;
   const int32_t TWin = it.tw + m - 1;
@@ -265,6 +285,24 @@ __device__ __forceinline__ void stage_gathered(const FusedParams& p, const Fused
     const AccT* __restrict__ row = ws + it.src + (int64_t)(64 * b + K) * it.src_pitch;
     const int32_t base = x0 + K * b + it.c_src;
     AccT* dst = buf + (size_t)r * rp;
+    const int32_t lim = Q.ext ? it.wsrc : Q.W;
+    if (base >= 0 && base + width <= lim) {
+      const AccT* __restrict__ src = row + base + lane;
+      for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
+        AccT v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int32_t j = j0 + u * 32;
+          v[u] = (j + lane < width) ? ld_ws<kC>(src + j) : AccT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int32_t j = j0 + u * 32 + lane;
+          if (j < width) dst[j] = v[u];
+        }
+      }
+      continue;
+    }
     for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
       AccT v[U];
 #pragma unroll
@@ -352,7 +390,7 @@ __device__ __forceinline__ void final_merge2_1(const FusedItem& it, const QuadDe
 //   L=3: merge2<1> (1), final merge4<2> (6)
 //   L=2: final merge4<1> (3);   L=1: final merge2<1> (1)
 template <bool kC, typename InT, typename AccT>
-__device__ void fused_block(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile, AccT* S,
+__device__ __forceinline__ void fused_block(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile, AccT* S,
                             AccT* A) {
   const int32_t TW = it.tw;
   const int32_t u0 = tile * TW;
@@ -428,21 +466,30 @@ __device__ __forceinline__ void spine_tile(const SpineTerm* st, const QuadDesc& 
 #pragma unroll
   for (int q = 0; q < 4; q++) acc[q] = AccT(0);
   AccT v[NT][4];
+  const bool full = u0 + 1024 <= Q.W;
 #pragma unroll
   for (int c = 0; c < NT; c++) {
     const int32_t off = st[c].off, wpart = st[c].wpart;
     const AccT* __restrict__ row = ws + st[c].row;
+    // the whole tile reads one contiguous stretch of the part row
+    const bool clean = full && (Q.ext ? (u0 + off >= 0 && u0 + 1023 + off < wpart) : (u0 + 1023 + off < Q.W));
+    if (clean) {
+      const AccT* __restrict__ src = row + u0 + off + (int32_t)threadIdx.x;
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int32_t u = u0 + q * 256 + (int32_t)threadIdx.x;
-      int32_t i = u + off;
-      bool ok = u < Q.W;
-      if (Q.ext) {
-        ok = ok && i >= 0 && i < wpart;
-      } else if (i >= Q.W) {
-        i -= Q.W;
+      for (int q = 0; q < 4; q++) v[c][q] = ld_ws<kC>(src + q * 256);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int32_t u = u0 + q * 256 + (int32_t)threadIdx.x;
+        int32_t i = u + off;
+        bool ok = u < Q.W;
+        if (Q.ext) {
+          ok = ok && i >= 0 && i < wpart;
+        } else if (i >= Q.W) {
+          i -= Q.W;
+        }
+        v[c][q] = ok ? ld_ws<kC>(row + i) : AccT(0);
       }
-      v[c][q] = ok ? ld_ws<kC>(row + i) : AccT(0);
     }
   }
 #pragma unroll
