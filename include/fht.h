@@ -173,7 +173,11 @@ fht_status fht_adjoint(fht_plan_t plan, const void* d_gout, void* d_gin, int64_t
  * 2 s); a wait that gives up records FHT_ERR_TIMEOUT in the queue's status
  * word (read with fht_queue_status) and the kernel still returns.
  * Submits to one queue must be ordered (one stream): they share its device
- * tables.  Use one queue per stream for concurrent batches. */
+ * tables.  Use one queue per stream for concurrent batches.  A submit made
+ * while its stream is being captured into a CUDA graph becomes part of the
+ * graph (copies from the queue's staging buffers, counter reset, launch); the
+ * graph then owns the queue: replay it instead of submitting again, and do
+ * not poll for its tags. */
 typedef struct {
   fht_plan_t plan;
   const void* d_in;

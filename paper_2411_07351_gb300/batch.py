@@ -1,0 +1,84 @@
+"""Batched transforms through fht_submit: many images of uneven sizes in one
+persistent launch.  PyTorch allocates the outputs and workspaces; the
+persistent kernel does all the work."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _capi as C
+from .fht import Plan, PlanCache
+
+
+class BatchQueue:
+    """One fht_queue_t: device tables for up to max_jobs jobs / max_units units per submit."""
+
+    def __init__(self, device: int | None = None, max_jobs: int = 8192, max_units: int = 1 << 22):
+        self._lib = C.load()
+        self.device_index = torch.cuda.current_device() if device is None else int(device)
+        h = ctypes.c_void_p()
+        C.check(self._lib.fht_queue_create(ctypes.byref(h), self.device_index, max_jobs, max_units),
+                "fht_queue_create")
+        self._q = h
+        self.plans = PlanCache(capacity=4096)
+        self._keep = []  # buffers of the last submit
+
+    def set_wait_limit(self, seconds: float):
+        C.check(self._lib.fht_queue_set_wait_limit(self._q, int(seconds * 1e9)), "fht_queue_set_wait_limit")
+
+    def plan_for(self, x: torch.Tensor, quads: int, boundary: str, split: str) -> Plan:
+        return self.plans.get(x.shape[0], x.shape[1], x.dtype, quads, boundary, split, self.device_index)
+
+    def submit(self, images, quads: int = C.FHT_QALL, boundary: str = "cyclic", split: str = "T",
+               outs=None, workspaces=None, stream=None, flags=None, tags=None):
+        """Enqueue one persistent launch over `images` (2-D CUDA tensors of one dtype).
+
+        Returns (outputs, plans, workspaces); outputs are the packed quadrants of each image."""
+        n = len(images)
+        plans = [self.plan_for(x, quads, boundary, split) for x in images]
+        if outs is None:
+            outs = [p.new_output() for p in plans]
+        if workspaces is None:
+            workspaces = [p.new_workspace() for p in plans]
+        jobs = (C.fht_job * n)()
+        for k, (x, p, o, w) in enumerate(zip(images, plans, outs, workspaces)):
+            if x.stride(1) != 1:
+                raise ValueError("images must have unit column stride")
+            jobs[k].plan = p._h
+            jobs[k].d_in = x.data_ptr()
+            jobs[k].in_pitch = x.stride(0)
+            jobs[k].d_out = o.data_ptr()
+            jobs[k].d_ws = w.data_ptr()
+            jobs[k].ws_bytes = w.numel()
+            jobs[k].tag = k if tags is None else tags[k]
+            jobs[k].flags = 0 if flags is None else flags[k]
+        s = stream if stream is not None else torch.cuda.current_stream(torch.device("cuda", self.device_index))
+        C.check(self._lib.fht_submit(self._q, n, jobs, int(s.cuda_stream)), "fht_submit")
+        self._keep = [images, outs, workspaces, plans]
+        return outs, plans, workspaces
+
+    def status(self, stream=None) -> int:
+        s = stream if stream is not None else torch.cuda.current_stream(torch.device("cuda", self.device_index))
+        return int(self._lib.fht_queue_status(self._q, int(s.cuda_stream)))
+
+    def reset_status(self, stream=None):
+        s = stream if stream is not None else torch.cuda.current_stream(torch.device("cuda", self.device_index))
+        C.check(self._lib.fht_queue_reset_status(self._q, int(s.cuda_stream)), "fht_queue_reset_status")
+
+    def poll(self, cap: int = 4096) -> list[int]:
+        buf = (ctypes.c_uint64 * cap)()
+        n = ctypes.c_int32()
+        C.check(self._lib.fht_queue_poll(self._q, buf, cap, ctypes.byref(n)), "fht_queue_poll")
+        return [int(buf[i]) for i in range(n.value)]
+
+    def close(self):
+        if getattr(self, "_q", None):
+            self._lib.fht_queue_destroy(self._q)
+            self._q = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -315,8 +315,14 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
   cudaStream_t st = (cudaStream_t)stream;
   QueueDeviceGuard g(q->device);
   if (!g.ok) return fht_capi_fail(FHT_ERR_CUDA, "fht_submit: cannot select the queue's device");
+  // Under stream capture the copies below become graph nodes that read the
+  // staging buffers at every replay: the graph then owns the staging, and no
+  // host synchronisation may happen here.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
+  const bool capturing = cap == cudaStreamCaptureStatusActive;
   // the staging buffers of the previous submit must have been copied out
-  if (q->staged_pending) {
+  if (q->staged_pending && !capturing) {
     cudaError_t e = cudaEventSynchronize(q->staged);
     if (e != cudaSuccess) return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_submit: ") + cudaGetErrorString(e));
     q->staged_pending = false;
@@ -413,9 +419,9 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
       (e = cudaMemcpyAsync(q->d_spine_nrows, q->h_spine_nrows, sizeof(int64_t) * njobs, cudaMemcpyHostToDevice,
                            st)) != cudaSuccess ||
       (e = cudaMemsetAsync(q->d_counters, 0, sizeof(int32_t) * (1 + (size_t)njobs), st)) != cudaSuccess ||
-      (e = cudaEventRecord(q->staged, st)) != cudaSuccess)
+      (!capturing && (e = cudaEventRecord(q->staged, st)) != cudaSuccess))
     return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_submit: ") + cudaGetErrorString(e));
-  q->staged_pending = true;
+  q->staged_pending = !capturing;
   switch (dtype) {
     case 0:
       e = launch_batch<uint8_t, int32_t>(q, (int32_t)nunits, smem, st);
@@ -432,6 +438,7 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
   }
   if (e != cudaSuccess) return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_submit: ") + cudaGetErrorString(e));
   q->last_units = (int32_t)nunits;
+  if (capturing) return FHT_OK;
   for (int32_t j = 0; j < njobs; j++) q->pending_tags.push_back(jobs[j].tag);
   if ((e = cudaEventRecord(q->done_evt, st)) != cudaSuccess)
     return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_submit: ") + cudaGetErrorString(e));

@@ -1,0 +1,130 @@
+"""Batched persistent launch (fht_submit) against per-image fht_forward and
+the oracle: bit-exact for integer images, alone and in the mix, in any order."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2411_07351_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_07351_gb300 import build as B
+
+    B.build()
+    import paper_2411_07351_gb300 as F
+
+    return F
+
+
+@pytest.fixture(scope="module")
+def queue(F):
+    from paper_2411_07351_gb300.batch import BatchQueue
+
+    q = BatchQueue(max_jobs=512, max_units=1 << 20)
+    yield q
+    q.close()
+
+
+def _edge_maps(seed, count, lo=17, hi=511):
+    imgs = inputs.c3_batch(seed=seed, count=count, lo=lo, hi=hi)
+    return [torch.from_numpy(im).cuda() for im in imgs]
+
+
+def test_batch_matches_single_and_oracle(F, orc, queue):
+    xs = _edge_maps(3, 96)
+    outs, plans, _ = queue.submit(xs, 15, "cyclic")
+    torch.cuda.synchronize()
+    assert queue.status() == 0
+    for x, o, p in zip(xs, outs, plans):
+        ref = p.forward(x)
+        assert torch.equal(o, ref)
+    for k in (0, 5, 50):
+        im = xs[k].cpu().numpy().astype(np.int64)
+        assert np.array_equal(outs[k].cpu().numpy(), orc.fht(im, 15, orc.CYCLIC))
+
+
+@pytest.mark.parametrize("boundary", ["cyclic", "extended"])
+def test_batch_mixed_sizes_and_order(F, queue, boundary):
+    # tiny (fused only), 64 < n (spine), powers of two (band root), larger bands
+    g = np.random.default_rng(7)
+    sizes = [(17, 30), (64, 64), (65, 17), (128, 40), (200, 511), (511, 200), (256, 256), (1, 9), (300, 1)]
+    xs = [torch.from_numpy(g.integers(0, 256, s, dtype=np.uint8)).cuda() for s in sizes]
+    outs, plans, _ = queue.submit(xs, 15, boundary)
+    torch.cuda.synchronize()
+    assert queue.status() == 0
+    ref = [p.forward(x) for x, p in zip(xs, plans)]
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
+    order = list(range(len(xs)))[::-1]
+    outs2, _, _ = queue.submit([xs[i] for i in order], 15, boundary)
+    torch.cuda.synchronize()
+    for k, i in enumerate(order):
+        assert torch.equal(outs2[k], ref[i])
+
+
+def test_batch_float_and_split_s(F, queue):
+    g = np.random.default_rng(8)
+    xs = [torch.from_numpy(g.standard_normal(s).astype(np.float32)).cuda() for s in [(70, 90), (300, 129), (33, 500)]]
+    outs, plans, _ = queue.submit(xs, 15, "extended", "S")
+    torch.cuda.synchronize()
+    assert queue.status() == 0
+    for x, o, p in zip(xs, outs, plans):
+        assert torch.equal(o, p.forward(x))
+
+
+def test_batch_withheld_dependency_times_out(F):
+    """The bounded wait: a job whose later units wait for a unit that never
+    exists makes the kernel record FHT_ERR_TIMEOUT and return; the context
+    stays usable."""
+    from paper_2411_07351_gb300 import _capi
+    from paper_2411_07351_gb300.batch import BatchQueue
+
+    q = BatchQueue(max_jobs=8, max_units=1 << 16)
+    q.set_wait_limit(0.05)
+    xs = _edge_maps(5, 3, lo=100, hi=300)
+    q.submit(xs, 15, "cyclic", flags=[0, _capi.FHT_JOB_WITHHOLD_DEPENDENCY, 0])
+    torch.cuda.synchronize()
+    assert q.status() == _capi.FHT_ERR_TIMEOUT
+    q.reset_status()
+    outs, plans, _ = q.submit(xs, 15, "cyclic")
+    torch.cuda.synchronize()
+    assert q.status() == 0
+    for x, o, p in zip(xs, outs, plans):
+        assert torch.equal(o, p.forward(x))
+    q.close()
+
+
+def test_batch_poll_tags(F, queue):
+    xs = _edge_maps(9, 4)
+    queue.submit(xs, 15, "cyclic", tags=[11, 12, 13, 14])
+    torch.cuda.synchronize()
+    assert sorted(queue.poll()) == [11, 12, 13, 14]
+    assert queue.poll() == []
+
+
+def test_batch_graph_replay(F, queue):
+    """A fixed batch captured in a CUDA graph replays to the same results."""
+    xs = _edge_maps(10, 16)
+    outs, plans, ws = queue.submit(xs, 15, "cyclic")
+    torch.cuda.synchronize()
+    ref = [o.clone() for o in outs]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        for o in outs:
+            o.zero_()
+        with torch.cuda.graph(graph, stream=s, capture_error_mode="relaxed"):
+            queue.submit(xs, 15, "cyclic", outs=outs, workspaces=ws, stream=s)
+    torch.cuda.synchronize()
+    for o in outs:
+        o.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
