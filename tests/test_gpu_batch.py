@@ -100,6 +100,8 @@ def test_batch_withheld_dependency_times_out(F):
 
 
 def test_batch_poll_tags(F, queue):
+    torch.cuda.synchronize()
+    queue.poll(1 << 16)  # drain the tags of earlier submits
     xs = _edge_maps(9, 4)
     queue.submit(xs, 15, "cyclic", tags=[11, 12, 13, 14])
     torch.cuda.synchronize()
