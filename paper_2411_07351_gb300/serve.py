@@ -1,0 +1,203 @@
+"""Serving loop with continuous batching.
+
+Requests (images of any size) arrive over time.  The server keeps plans in
+an LRU cache and buffers in PyTorch's caching allocator, admits a request
+only while the device-memory budget (output + workspace of every admitted,
+unfinished request) has room, and on every turn of its loop submits all
+admitted requests that are not yet running as ONE persistent batched launch
+(fht_submit) on a stream whose previous batch has finished.  Batches on
+different streams overlap on the device; a request that arrives while others
+run joins the next batch as soon as memory and a stream are free.  Latency is
+arrival -> the host seeing the batch's completion event.
+
+``PlainServer`` is the comparison: one fht_forward per request, launched on
+one stream as soon as the request arrives.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _capi as C
+from .batch import BatchQueue
+from .fht import PlanCache
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds, on the server's clock
+    image: torch.Tensor     # 2-D CUDA tensor (may be a strided view)
+    out: torch.Tensor | None = None
+    ws: torch.Tensor | None = None
+    nbytes: int = 0
+    done: float | None = None
+    plan: object = None
+    batch_size: int = 0
+
+
+@dataclass
+class _Batch:
+    event: torch.cuda.Event
+    reqs: list
+    slot: int
+    stream: torch.cuda.Stream = field(default=None)
+
+
+class Server:
+    def __init__(self, device: int = 0, budget_bytes: int = 16 << 30, streams: int = 4, quads: int = C.FHT_QALL,
+                 boundary: str = "cyclic", split: str = "T", max_batch: int = 1024, keep_outputs: bool = True):
+        self.device = device
+        self.keep_outputs = keep_outputs
+        self.budget = budget_bytes
+        self.quads, self.boundary, self.split = quads, boundary, split
+        self.max_batch = max_batch
+        self.plans = PlanCache(capacity=4096)
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
+        self.queues = [BatchQueue(device=device, max_jobs=max_batch, max_units=1 << 22) for _ in range(streams)]
+        self.free_slots = collections.deque(range(streams))
+        self.waiting: collections.deque = collections.deque()   # arrived, not admitted
+        self.admitted: collections.deque = collections.deque()  # admitted, not launched
+        self.running: list[_Batch] = []
+        self.used = 0
+        self.finished: list[Request] = []
+        self.max_used = 0
+        self.batches = 0
+
+    def footprint(self, req: Request) -> int:
+        p = self.plans.get(req.image.shape[0], req.image.shape[1], req.image.dtype, self.quads, self.boundary,
+                           self.split, self.device)
+        req.plan = p
+        return p.out_elems * 4 + max(p.workspace_bytes, 256)
+
+    def arrive(self, req: Request):
+        self.waiting.append(req)
+
+    def _admit(self):
+        while self.waiting:
+            req = self.waiting[0]
+            need = req.nbytes or self.footprint(req)
+            req.nbytes = need
+            if self.used + need > self.budget and self.used > 0:
+                break
+            self.waiting.popleft()
+            self.used += need
+            self.max_used = max(self.max_used, self.used)
+            self.admitted.append(req)
+
+    def _retire(self, now_fn):
+        still = []
+        for b in self.running:
+            if b.event.query():
+                t = now_fn()
+                for r in b.reqs:
+                    r.done = t
+                    self.used -= r.nbytes
+                    r.ws = None  # workspace back to the caching allocator
+                    if not self.keep_outputs:
+                        r.out = None
+                    self.finished.append(r)
+                self.free_slots.append(b.slot)
+            else:
+                still.append(b)
+        self.running = still
+
+    def _launch(self):
+        while self.admitted and self.free_slots:
+            slot = self.free_slots.popleft()
+            reqs = []
+            while self.admitted and len(reqs) < self.max_batch:
+                reqs.append(self.admitted.popleft())
+            s = self.streams[slot]
+            with torch.cuda.stream(s):
+                for r in reqs:
+                    r.out = r.plan.new_output()
+                    r.ws = r.plan.new_workspace()
+                    r.batch_size = len(reqs)
+                self.queues[slot].submit([r.image for r in reqs], self.quads, self.boundary, self.split,
+                                         outs=[r.out for r in reqs], workspaces=[r.ws for r in reqs], stream=s)
+                ev = torch.cuda.Event()
+                ev.record(s)
+            self.running.append(_Batch(ev, reqs, slot, s))
+            self.batches += 1
+
+    def step(self, now_fn):
+        self._retire(now_fn)
+        self._admit()
+        self._launch()
+
+    def idle(self) -> bool:
+        return not (self.waiting or self.admitted or self.running)
+
+    def close(self):
+        for q in self.queues:
+            q.close()
+
+
+class PlainServer:
+    """One plain fht_forward per request, launched on arrival on one stream."""
+
+    def __init__(self, device: int = 0, quads: int = C.FHT_QALL, boundary: str = "cyclic", split: str = "T",
+                 keep_outputs: bool = True):
+        self.device = device
+        self.keep_outputs = keep_outputs
+        self.quads, self.boundary, self.split = quads, boundary, split
+        self.plans = PlanCache(capacity=4096)
+        self.stream = torch.cuda.Stream(device=device)
+        self.running: collections.deque = collections.deque()
+        self.finished: list[Request] = []
+        self.batches = 0
+
+    def arrive(self, req: Request):
+        p = self.plans.get(req.image.shape[0], req.image.shape[1], req.image.dtype, self.quads, self.boundary,
+                           self.split, self.device)
+        req.plan = p
+        with torch.cuda.stream(self.stream):
+            req.out = p.new_output()
+            req.ws = p.new_workspace()
+            p.forward(req.image, req.out, req.ws, stream=self.stream)
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+        req.batch_size = 1
+        self.running.append((ev, req))
+        self.batches += 1
+
+    def step(self, now_fn):
+        while self.running and self.running[0][0].query():
+            ev, r = self.running.popleft()
+            r.done = now_fn()
+            r.ws = None
+            if not self.keep_outputs:
+                r.out = None
+            self.finished.append(r)
+
+    def idle(self) -> bool:
+        return not self.running
+
+    def close(self):
+        pass
+
+
+def run_stream(server, requests):
+    """Feed `requests` (arrival-sorted Request objects) to `server` in real time.
+
+    Returns (finished requests, wall seconds from the first arrival to the last completion)."""
+    t0 = time.perf_counter()
+
+    def now():
+        return time.perf_counter() - t0
+
+    i = 0
+    n = len(requests)
+    while i < n or not server.idle():
+        t = now()
+        while i < n and requests[i].arrival <= t:
+            server.arrive(requests[i])
+            i += 1
+        server.step(now)
+    torch.cuda.synchronize()
+    end = max(r.done for r in server.finished)
+    return server.finished, end - (requests[0].arrival if requests else 0.0)
