@@ -75,7 +75,8 @@ typedef struct {
   int32_t fused_rows;  /* F: largest subtree merged in shared memory (2..64, power of two) */
   int32_t tile_cols;   /* column tile of the fused pass (multiple of 32) */
   int32_t threads;     /* threads per CTA of the fused pass (multiple of 32, <= 512) */
-  int32_t reserved[5];
+  int32_t with_adjoint;/* 1: build the adjoint tables now (otherwise on the first fht_adjoint) */
+  int32_t reserved[4];
 } fht_tuning_t;
 
 typedef struct {

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -14,6 +15,8 @@
 struct fht_plan_s {
   fht::HostPlan host;
   fht::DevicePlan dev;
+  void* d_tables = nullptr;  // one device allocation holding every table of the plan
+  std::mutex mu;             // serialises the lazy adjoint build
 };
 
 namespace {
@@ -43,19 +46,60 @@ struct DeviceGuard {
   }
 };
 
-template <typename T>
-cudaError_t upload(T** dst, const std::vector<T>& src) {
-  *dst = nullptr;
-  if (src.empty()) return cudaSuccess;
-  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * src.size());
+// Packs every table of the plan into one device allocation (sections aligned
+// to 256 bytes) with a single copy.
+struct TablePacker {
+  std::vector<unsigned char> host;
+  std::vector<std::pair<void**, size_t>> fix;  // (device pointer to set, offset)
+  template <typename T>
+  void add(T** dst, const std::vector<T>& v) {
+    *dst = nullptr;
+    if (v.empty()) return;
+    size_t off = (host.size() + 255) / 256 * 256;
+    host.resize(off + sizeof(T) * v.size());
+    memcpy(host.data() + off, v.data(), sizeof(T) * v.size());
+    fix.emplace_back(reinterpret_cast<void**>(dst), off);
+  }
+};
+
+cudaError_t upload_tables(fht_plan_s* p) {
+  fht::DevicePlan& d = p->dev;
+  const fht::HostPlan& h = p->host;
+  TablePacker tp;
+  tp.add(&d.fused, h.fused);
+  tp.add(&d.ops, h.ops);
+  tp.add(&d.rows, h.rows);
+  tp.add(&d.band_items, h.band_items);
+  tp.add(&d.spine_rows, h.spine_rows);
+  tp.add(&d.spine_terms, h.spine_terms);
+  if (h.has_adjoint) {
+    tp.add(&d.arows, h.arows);
+    tp.add(&d.aterms, h.aterms);
+    tp.add(&d.aptr, h.aptr);
+    tp.add(&d.aops, h.aops);
+  } else {
+    d.arows = nullptr;
+    d.aterms = nullptr;
+    d.aptr = nullptr;
+    d.aops = nullptr;
+  }
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, std::max<size_t>(tp.host.size(), 256));
   if (e != cudaSuccess) return e;
-  return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+  e = cudaMemcpy(buf, tp.host.data(), tp.host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(buf);
+    return e;
+  }
+  for (auto& f : tp.fix) *f.first = static_cast<unsigned char*>(buf) + f.second;
+  p->d_tables = buf;
+  return cudaSuccess;
 }
 
-void free_dev(fht::DevicePlan& d) {
-  void* ptrs[] = {d.fused, d.ops, d.rows, d.arows, d.aterms, d.aptr, d.aops, d.band_items, d.spine_rows, d.spine_terms};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+void free_dev(fht_plan_s* p) {
+  if (p->d_tables) cudaFree(p->d_tables);  // cudaFree waits for work that may still read the tables
+  p->d_tables = nullptr;
+  fht::DevicePlan& d = p->dev;
   d.fused = nullptr;
   d.ops = nullptr;
   d.rows = nullptr;
@@ -95,6 +139,7 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
     if (tuning->fused_rows) cfg.F = tuning->fused_rows;
     if (tuning->tile_cols) cfg.TW = tuning->tile_cols;
     if (tuning->threads) cfg.threads = tuning->threads;
+    cfg.with_adjoint = tuning->with_adjoint != 0;
     if (cfg.threads > 512) return fail(FHT_ERR_INVALID, "fht_plan: threads must be <= 512");
   }
   fht_plan_s* p = new (std::nothrow) fht_plan_s();
@@ -138,17 +183,8 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
       return fail(FHT_ERR_INVALID,
                   "fht_plan: fused tile needs " + need + " bytes of shared memory; lower tile_cols or fused_rows");
     }
-    if ((e = upload(&p->dev.fused, p->host.fused)) != cudaSuccess ||
-        (e = upload(&p->dev.ops, p->host.ops)) != cudaSuccess ||
-        (e = upload(&p->dev.rows, p->host.rows)) != cudaSuccess ||
-        (e = upload(&p->dev.arows, p->host.arows)) != cudaSuccess ||
-        (e = upload(&p->dev.aterms, p->host.aterms)) != cudaSuccess ||
-        (e = upload(&p->dev.aptr, p->host.aptr)) != cudaSuccess ||
-        (e = upload(&p->dev.aops, p->host.aops)) != cudaSuccess ||
-        (e = upload(&p->dev.band_items, p->host.band_items)) != cudaSuccess ||
-        (e = upload(&p->dev.spine_rows, p->host.spine_rows)) != cudaSuccess ||
-        (e = upload(&p->dev.spine_terms, p->host.spine_terms)) != cudaSuccess) {
-      free_dev(p->dev);
+    if ((e = upload_tables(p)) != cudaSuccess) {
+      free_dev(p);
       delete p;
       if (e == cudaErrorMemoryAllocation) return fail(FHT_ERR_NOMEM, "fht_plan: device allocation failed");
       return cuda_fail(e, "fht_plan: upload");
@@ -181,7 +217,7 @@ fht_status fht_plan_info(fht_plan_t plan, fht_plan_info_t* info) {
   info->ideal_bytes = P.ideal_bytes;
   info->fused_rows = P.cfg.F;
   info->tile_cols = P.cfg.TW;
-  info->upper_passes = (int32_t)P.pass_begin.size() - 1;
+  info->upper_passes = P.upper_heights;
   return FHT_OK;
 }
 
@@ -238,14 +274,36 @@ fht_status fht_adjoint(fht_plan_t plan, const void* d_gout, void* d_gin, int64_t
   if (plan->dev.device < 0) return fail(FHT_ERR_INVALID, "fht_adjoint: host-only plan (device < 0)");
   if (!d_gout || !d_gin || !d_ws) return fail(FHT_ERR_INVALID, "fht_adjoint: NULL buffer");
   if (gin_pitch < P.cfg.w) return fail(FHT_ERR_INVALID, "fht_adjoint: gin_pitch < w");
-  if (ws_bytes < P.adj_ws_bytes)
-    return fail(FHT_ERR_INVALID,
-                "fht_adjoint: workspace too small (need " + std::to_string(P.adj_ws_bytes) + " bytes)");
   if (((uintptr_t)d_ws) % 256) return fail(FHT_ERR_INVALID, "fht_adjoint: workspace must be 256-byte aligned");
   if (((uintptr_t)d_gout) % P.acc_size || ((uintptr_t)d_gin) % P.acc_size)
     return fail(FHT_ERR_INVALID, "fht_adjoint: misaligned buffer");
   DeviceGuard g(plan->dev.device);
   if (!g.ok) return fail(FHT_ERR_CUDA, "fht_adjoint: cannot select the plan's device");
+  {
+    // the adjoint tables are built on first use (plans made for the forward
+    // transform only never pay for them)
+    std::lock_guard<std::mutex> lock(plan->mu);
+    if (!plan->host.has_adjoint) {
+      fht::PlanConfig cfg = plan->host.cfg;
+      cfg.with_adjoint = true;
+      fht::HostPlan hp;
+      std::string err;
+      try {
+        err = fht::build_plan(cfg, hp);
+      } catch (const std::bad_alloc&) {
+        return fail(FHT_ERR_NOMEM, "fht_adjoint: host allocation failed while building tables");
+      }
+      if (!err.empty()) return fail(FHT_ERR_INVALID, "fht_adjoint: " + err);
+      free_dev(plan);
+      plan->host = std::move(hp);
+      fht::fused_geometry(plan->host, plan->dev.geo);
+      cudaError_t e = upload_tables(plan);
+      if (e != cudaSuccess) return cuda_fail(e, "fht_adjoint: table upload");
+    }
+  }
+  if (ws_bytes < P.adj_ws_bytes)
+    return fail(FHT_ERR_INVALID,
+                "fht_adjoint: workspace too small (need " + std::to_string(P.adj_ws_bytes) + " bytes)");
   cudaError_t e = fht::launch_adjoint(plan->dev, d_gout, d_gin, gin_pitch, d_ws, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "fht_adjoint");
   return FHT_OK;
@@ -269,7 +327,7 @@ fht_status fht_plan_destroy(fht_plan_t plan) {
   }
   {
     DeviceGuard g(plan->dev.device);
-    free_dev(plan->dev);
+    free_dev(plan);
   }
   delete plan;
   return FHT_OK;

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <map>
+#include <set>
 
 namespace fht {
 
@@ -170,6 +171,7 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
   int64_t ws_off = 0;  // elements of the accumulator type after the header
   std::vector<std::vector<RowJob>> passes;
   std::vector<int64_t> bytes_by_height;
+  std::set<int32_t> heights_seen;
 
   for (int q = 0; q < 4; q++) {
     if (!(cfg.quads & (1u << q))) continue;
@@ -277,14 +279,17 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
         build_program(tr, i, P.ops, nlev);
         it = prog_cache.emplace(nd.m, std::make_pair(off, nlev)).first;
       }
-      auto ait = aprog_cache.find(nd.m);
-      if (ait == aprog_cache.end()) {
-        int32_t aoff = 0;
-        build_adjoint_program(P.ops, it->second.first, it->second.second, nd.m, P.aptr, P.aops, aoff);
-        ait = aprog_cache.emplace(nd.m, aoff).first;
-      }
       FusedItem fi{};
-      fi.aprog = ait->second;
+      fi.aprog = -1;
+      if (cfg.with_adjoint) {
+        auto ait = aprog_cache.find(nd.m);
+        if (ait == aprog_cache.end()) {
+          int32_t aoff = 0;
+          build_adjoint_program(P.ops, it->second.first, it->second.second, nd.m, P.aptr, P.aops, aoff);
+          ait = aprog_cache.emplace(nd.m, aoff).first;
+        }
+        fi.aprog = ait->second;
+      }
       fi.antiles = (Q.L + cfg.TW - 1) / cfg.TW;
       P.max_antiles = std::max(P.max_antiles, fi.antiles);
       fi.q = q;
@@ -400,11 +405,13 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
         passes.resize(nd.height + 1);
         bytes_by_height.resize(nd.height + 1, 0);
       }
+      heights_seen.insert(nd.height);
       const bool fin = (i == rootidx);
       const int32_t wout = cfg.ext ? Q.L + nd.m - 1 : Q.W;
       const int32_t wtop = cfg.ext ? Q.L + c0.m - 1 : Q.W;
       const int32_t wbot = cfg.ext ? Q.L + c1.m - 1 : Q.W;
-      for (int32_t t = 0; t < nd.m; t++) {
+      // per-height forward rows: only for trees that do not use the band schedule
+      for (int32_t t = 0; t < (use_bands ? 0 : nd.m); t++) {
         int32_t t1, t2, s;
         merge_entry(nd.m, c0.m, c1.m, t, t1, t2, s);
         RowJob rj;
@@ -428,6 +435,7 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
       }
       bytes_by_height[nd.height] += ((int64_t)c0.m * wtop + (int64_t)c1.m * wbot + (int64_t)nd.m * wout) * acc;
       // adjoint: each child row gathers the parent rows that read it
+      if (!cfg.with_adjoint) continue;
       if ((int32_t)apasses.size() <= nd.height) {
         apasses.resize(nd.height + 1);
         aterms_by_h.resize(nd.height + 1);
@@ -510,6 +518,8 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
     P.aterms.insert(P.aterms.end(), aterms_by_h[k].begin(), aterms_by_h[k].end());
     P.apass_begin.push_back((int64_t)P.arows.size());
   }
+  P.has_adjoint = cfg.with_adjoint;
+  P.upper_heights = (int32_t)heights_seen.size();
   if (P.aterms.empty()) P.aterms.push_back(AdjTerm{0, 0});
   if (P.aops.empty()) P.aops.push_back(MergeOp{0, 0, 0, 0});
   if (P.aptr.empty()) P.aptr.push_back(0);

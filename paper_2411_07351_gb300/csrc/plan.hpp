@@ -48,6 +48,7 @@ struct PlanConfig {
   int32_t F = 64;          // fused rows
   int32_t TW = 128;        // fused column tile
   int32_t threads = 256;   // fused CTA size
+  bool with_adjoint = false;  // also build the adjoint tables
 };
 
 struct HostPlan {
@@ -74,6 +75,8 @@ struct HostPlan {
   std::vector<int32_t> aptr;         // fused adjoint programs: CSR row pointers into aops
   std::vector<MergeOp> aops;         // (top = forward dst row r, s = shift): g[k][j] += g'[r][j - s]
   size_t adj_ws_bytes = 0;
+  bool has_adjoint = false;          // adjoint tables built (cfg.with_adjoint)
+  int32_t upper_heights = 0;         // tree heights above the fused subtrees (per-height passes)
   int32_t max_antiles = 0;
   int32_t max_ntiles = 0;
   int32_t max_fused_m = 1;

@@ -164,6 +164,7 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
   }
 
   // ---- adjoint ----
+  if (!P.has_adjoint) return "";
   const int64_t adj_elems = (int64_t)((P.adj_ws_bytes - kWsHeader) / P.acc_size);
   const int64_t img = (int64_t)P.cfg.h * P.cfg.w;
   for (int q = 0; q < 4; q++) {

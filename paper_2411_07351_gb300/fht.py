@@ -37,7 +37,7 @@ class Plan:
 
     def __init__(self, h: int, w: int, dtype=torch.float32, quads: int = C.FHT_QALL,
                  boundary: str = "cyclic", split: str = "T", device: int | None = None,
-                 fused_rows: int = 0, tile_cols: int = 0, threads: int = 0):
+                 fused_rows: int = 0, tile_cols: int = 0, threads: int = 0, with_adjoint: bool = False):
         self._lib = C.load()
         if dtype not in DTYPES:
             raise ValueError(f"unsupported dtype {dtype}")
@@ -50,11 +50,16 @@ class Plan:
         if device is None:
             device = torch.cuda.current_device()
         self.device_index = int(device)
-        tun = C.fht_tuning_t(fused_rows, tile_cols, threads)
+        tun = C.fht_tuning_t(fused_rows, tile_cols, threads, int(with_adjoint))
         handle = ctypes.c_void_p()
-        C.check(self._lib.fht_plan(ctypes.byref(handle), self.h, self.w, self.fht_dtype, self.quads,
-                                   BOUNDARY[boundary], SPLIT[split], self.device_index, ctypes.byref(tun)),
-                "fht_plan")
+        args = (ctypes.byref(handle), self.h, self.w, self.fht_dtype, self.quads, BOUNDARY[boundary], SPLIT[split],
+                self.device_index, ctypes.byref(tun))
+        st = self._lib.fht_plan(*args)
+        if st == C.FHT_ERR_NOMEM and self.device_index >= 0:
+            # the plan's tables are allocated outside PyTorch: give back cached blocks once
+            torch.cuda.empty_cache()
+            st = self._lib.fht_plan(*args)
+        C.check(st, "fht_plan")
         self._h = handle
         info = C.fht_plan_info_t()
         C.check(self._lib.fht_plan_info(self._h, ctypes.byref(info)), "fht_plan_info")
@@ -98,6 +103,11 @@ class Plan:
                                       ws.numel() * ws.element_size(), _stream_handle(x.device, stream)),
                 "fht_forward")
         return out
+
+    def _refresh_info(self):
+        info = C.fht_plan_info_t()
+        C.check(self._lib.fht_plan_info(self._h, ctypes.byref(info)), "fht_plan_info")
+        self.info = info
 
     def adjoint(self, gout: torch.Tensor, gin: torch.Tensor | None = None, ws: torch.Tensor | None = None,
                 stream=None) -> torch.Tensor:

@@ -138,44 +138,63 @@ class Server:
 
 
 class PlainServer:
-    """One plain fht_forward per request, launched on arrival on one stream."""
+    """One plain fht_forward per request, launched in arrival order on one
+    stream, under the same device-memory budget as the batched server."""
 
-    def __init__(self, device: int = 0, quads: int = C.FHT_QALL, boundary: str = "cyclic", split: str = "T",
-                 keep_outputs: bool = True):
+    def __init__(self, device: int = 0, budget_bytes: int = 16 << 30, quads: int = C.FHT_QALL,
+                 boundary: str = "cyclic", split: str = "T", keep_outputs: bool = True):
         self.device = device
+        self.budget = budget_bytes
         self.keep_outputs = keep_outputs
         self.quads, self.boundary, self.split = quads, boundary, split
         self.plans = PlanCache(capacity=4096)
         self.stream = torch.cuda.Stream(device=device)
+        self.waiting: collections.deque = collections.deque()
         self.running: collections.deque = collections.deque()
         self.finished: list[Request] = []
+        self.used = 0
+        self.max_used = 0
         self.batches = 0
 
     def arrive(self, req: Request):
-        p = self.plans.get(req.image.shape[0], req.image.shape[1], req.image.dtype, self.quads, self.boundary,
-                           self.split, self.device)
-        req.plan = p
-        with torch.cuda.stream(self.stream):
-            req.out = p.new_output()
-            req.ws = p.new_workspace()
-            p.forward(req.image, req.out, req.ws, stream=self.stream)
-            ev = torch.cuda.Event()
-            ev.record(self.stream)
-        req.batch_size = 1
-        self.running.append((ev, req))
-        self.batches += 1
+        self.waiting.append(req)
+
+    def _launch(self):
+        while self.waiting:
+            req = self.waiting[0]
+            if req.plan is None:
+                req.plan = self.plans.get(req.image.shape[0], req.image.shape[1], req.image.dtype, self.quads,
+                                          self.boundary, self.split, self.device)
+                req.nbytes = req.plan.out_elems * 4 + max(req.plan.workspace_bytes, 256)
+            if self.used + req.nbytes > self.budget and self.used > 0:
+                return
+            self.waiting.popleft()
+            self.used += req.nbytes
+            self.max_used = max(self.max_used, self.used)
+            p = req.plan
+            with torch.cuda.stream(self.stream):
+                req.out = p.new_output()
+                req.ws = p.new_workspace()
+                p.forward(req.image, req.out, req.ws, stream=self.stream)
+                ev = torch.cuda.Event()
+                ev.record(self.stream)
+            req.batch_size = 1
+            self.running.append((ev, req))
+            self.batches += 1
 
     def step(self, now_fn):
         while self.running and self.running[0][0].query():
             ev, r = self.running.popleft()
             r.done = now_fn()
             r.ws = None
+            self.used -= r.nbytes
             if not self.keep_outputs:
                 r.out = None
             self.finished.append(r)
+        self._launch()
 
     def idle(self) -> bool:
-        return not self.running
+        return not (self.running or self.waiting)
 
     def close(self):
         pass
