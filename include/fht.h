@@ -204,7 +204,11 @@ fht_status fht_queue_set_wait_limit(fht_queue_t q, int64_t wait_ns);
 /* Enqueue one persistent launch over all jobs on `stream` (cudaStream_t).
  * FHT_ERR_BUSY when the jobs or their units exceed the queue's capacity. */
 fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* stream);
-/* Non-blocking: copies up to `cap` tags of jobs whose submit has finished. */
+/* Non-blocking: copies up to `cap` tags of finished jobs.  Each job is
+ * reported once, as soon as its own last unit has finished (the kernel sets
+ * the job's host-mapped completion flag), so early jobs of a batch are seen
+ * before the rest of the batch ends.  Their outputs may then be read from
+ * another stream. */
 fht_status fht_queue_poll(fht_queue_t q, uint64_t* done_tags, int32_t cap, int32_t* ndone);
 /* Synchronises `stream` and returns the queue's status word (FHT_OK or FHT_ERR_TIMEOUT). */
 fht_status fht_queue_status(fht_queue_t q, void* stream);

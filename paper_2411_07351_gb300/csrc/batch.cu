@@ -32,6 +32,9 @@ struct BatchJob {
   const SpineRow* spine_rows;
   const SpineTerm* spine_terms;
   const RowJob* rows;
+  int32_t total_units;            // units of this job in the submit
+  uint32_t gen;                   // submit generation written to the job's completion flag
+  uint32_t* flag;                 // host-mapped completion flag of the job slot
 };
 
 enum : int32_t { UNIT_FUSED = 0, UNIT_BAND = 1, UNIT_SPINE = 2, UNIT_UPPER = 3 };
@@ -99,26 +102,8 @@ __device__ void batch_spine(const BatchJob& jb, int32_t r0, int32_t tile, SpineT
     if (c < sr[r].term_count) st[r][c] = jb.spine_terms[sr[r].term_begin + c];
   }
   __syncthreads();
-  if (threadIdx.x < 256) {
-    for (int32_t r = 0; r < nr; r++) {
-      const QuadDesc& Q = jb.fp.quad[sr[r].q];
-      if (u0 >= Q.W) continue;
-      AccT* dst = out + sr[r].dst;
-      switch (sr[r].term_count) {
-#define FHT_BATCH_SPINE_CASE(N) \
-  case N:                       \
-    spine_tile<true, N, AccT>(st[r], Q, ws, dst, u0); \
-    break;
-        FHT_BATCH_SPINE_CASE(1) FHT_BATCH_SPINE_CASE(2) FHT_BATCH_SPINE_CASE(3) FHT_BATCH_SPINE_CASE(4)
-        FHT_BATCH_SPINE_CASE(5) FHT_BATCH_SPINE_CASE(6) FHT_BATCH_SPINE_CASE(7) FHT_BATCH_SPINE_CASE(8)
-        FHT_BATCH_SPINE_CASE(9) FHT_BATCH_SPINE_CASE(10) FHT_BATCH_SPINE_CASE(11) FHT_BATCH_SPINE_CASE(12)
-        FHT_BATCH_SPINE_CASE(13) FHT_BATCH_SPINE_CASE(14) FHT_BATCH_SPINE_CASE(15) FHT_BATCH_SPINE_CASE(16)
-#undef FHT_BATCH_SPINE_CASE
-        default:
-          break;
-      }
-    }
-  }
+  // 512 threads x 2 columns: the same 1024-column tile as the plain spine kernel
+  spine_rows_tile<true, 512, 2, AccT>(sr, st, nr, jb.fp.quad, ws, out, u0);
 }
 
 // counters[0]: next unit; counters[1 + j]: finished units of job j.
@@ -187,7 +172,15 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchJob* __restric
     // counted too, so that nothing waits on them)
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(&counters[1 + U.job], 1);
+    if (threadIdx.x == 0) {
+      const int32_t finished = atomicAdd(&counters[1 + U.job], 1) + 1;
+      const BatchJob& jb = jobs[U.job];
+      if (finished == jb.total_units) {
+        // the job's last unit: tell the host through its mapped completion flag
+        __threadfence_system();
+        asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(jb.flag), "r"(jb.gen) : "memory");
+      }
+    }
   }
 }
 
@@ -215,9 +208,16 @@ struct fht_queue_s {
   cudaEvent_t staged = nullptr;     // staging buffers free again after this event
   bool staged_pending = false;
   int32_t last_units = 0;
-  std::vector<uint64_t> pending_tags, done_tags;
+  uint32_t* h_flags = nullptr;      // host-mapped completion flags, one per job slot
+  uint32_t* d_flags = nullptr;      // the same memory as seen by the device
+  uint32_t gen = 0;                 // generation of the latest submit
+  struct Outstanding {
+    uint32_t gen;
+    std::vector<uint64_t> tags;
+    std::vector<char> reported;
+  };
+  std::vector<Outstanding> outstanding;
   cudaEvent_t done_evt = nullptr;
-  bool done_pending = false;
 };
 
 namespace {
@@ -246,6 +246,7 @@ void queue_free(fht_queue_s* q) {
   if (q->h_spine_nrows) cudaFreeHost(q->h_spine_nrows);
   if (q->staged) cudaEventDestroy(q->staged);
   if (q->done_evt) cudaEventDestroy(q->done_evt);
+  if (q->h_flags) cudaFreeHost(q->h_flags);
 }
 
 template <typename InT, typename AccT>
@@ -292,12 +293,15 @@ fht_status fht_queue_create(fht_queue_t* out, int device, int32_t max_jobs, int6
       (e = cudaMallocHost(&q->h_spine_nrows, sizeof(int64_t) * max_jobs)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&q->staged, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&q->done_evt, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaMemset(q->d_status, 0, 256)) != cudaSuccess) {
+      (e = cudaMemset(q->d_status, 0, 256)) != cudaSuccess ||
+      (e = cudaHostAlloc(&q->h_flags, sizeof(uint32_t) * max_jobs, cudaHostAllocMapped)) != cudaSuccess ||
+      (e = cudaHostGetDevicePointer(&q->d_flags, q->h_flags, 0)) != cudaSuccess) {
     queue_free(q);
     delete q;
     return fht_capi_fail(e == cudaErrorMemoryAllocation ? FHT_ERR_NOMEM : FHT_ERR_CUDA,
                          std::string("fht_queue_create: ") + cudaGetErrorString(e));
   }
+  memset(q->h_flags, 0, sizeof(uint32_t) * max_jobs);
   *out = q;
   return FHT_OK;
 }
@@ -411,6 +415,12 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
     }
   }
   if (nunits == 0) return FHT_OK;
+  q->gen++;
+  for (int32_t j = 0; j < njobs; j++) {
+    q->h_jobs[j].total_units = done_before[j];
+    q->h_jobs[j].gen = q->gen;
+    q->h_jobs[j].flag = q->d_flags + j;
+  }
   cudaError_t e;
   if ((e = cudaMemcpyAsync(q->d_jobs, q->h_jobs, sizeof(fht::BatchJob) * njobs, cudaMemcpyHostToDevice, st)) !=
           cudaSuccess ||
@@ -439,30 +449,44 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
   if (e != cudaSuccess) return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_submit: ") + cudaGetErrorString(e));
   q->last_units = (int32_t)nunits;
   if (capturing) return FHT_OK;
-  for (int32_t j = 0; j < njobs; j++) q->pending_tags.push_back(jobs[j].tag);
+  {
+    fht_queue_s::Outstanding o;
+    o.gen = q->gen;
+    o.tags.reserve(njobs);
+    for (int32_t j = 0; j < njobs; j++) o.tags.push_back(jobs[j].tag);
+    o.reported.assign(njobs, 0);
+    q->outstanding.push_back(std::move(o));
+  }
   if ((e = cudaEventRecord(q->done_evt, st)) != cudaSuccess)
     return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_submit: ") + cudaGetErrorString(e));
-  q->done_pending = true;
   return FHT_OK;
 }
 
 fht_status fht_queue_poll(fht_queue_t q, uint64_t* done_tags, int32_t cap, int32_t* ndone) {
   if (!q || !ndone || (cap > 0 && !done_tags)) return fht_capi_fail(FHT_ERR_INVALID, "fht_queue_poll: bad argument");
   *ndone = 0;
-  QueueDeviceGuard g(q->device);
-  if (q->done_pending) {
-    cudaError_t e = cudaEventQuery(q->done_evt);
-    if (e == cudaSuccess) {
-      q->done_tags.insert(q->done_tags.end(), q->pending_tags.begin(), q->pending_tags.end());
-      q->pending_tags.clear();
-      q->done_pending = false;
-    } else if (e != cudaErrorNotReady) {
-      return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_queue_poll: ") + cudaGetErrorString(e));
+  // per-job completion flags: a job is reported as soon as its last unit has
+  // finished, before the rest of its batch
+  int32_t n = 0;
+  for (size_t k = 0; k < q->outstanding.size() && n < cap; k++) {
+    fht_queue_s::Outstanding& o = q->outstanding[k];
+    for (size_t j = 0; j < o.tags.size() && n < cap; j++) {
+      if (o.reported[j]) continue;
+      const uint32_t f = __atomic_load_n(&q->h_flags[j], __ATOMIC_ACQUIRE);
+      if ((int32_t)(f - o.gen) >= 0) {
+        o.reported[j] = 1;
+        done_tags[n++] = o.tags[j];
+      }
     }
   }
-  const int32_t n = std::min<int32_t>(cap, (int32_t)q->done_tags.size());
-  for (int32_t i = 0; i < n; i++) done_tags[i] = q->done_tags[i];
-  q->done_tags.erase(q->done_tags.begin(), q->done_tags.begin() + n);
+  // drop submits whose jobs have all been reported
+  while (!q->outstanding.empty()) {
+    const fht_queue_s::Outstanding& o = q->outstanding.front();
+    bool all = true;
+    for (char r : o.reported) all = all && r;
+    if (!all) break;
+    q->outstanding.erase(q->outstanding.begin());
+  }
   *ndone = n;
   return FHT_OK;
 }

@@ -45,75 +45,99 @@ __device__ __forceinline__ AccT view_load(const InT* __restrict__ in, int64_t pi
 }
 
 // Stage m view rows [a, a + m) x window columns [x0, x0 + width) into
-// buf (row pitch rp): wrapped (cyclic) or zero-filled (extended).  Loads are
-// issued in batches of U per thread before their shared stores so that several
-// global loads are in flight per thread.
+// buf (row pitch rp): wrapped (cyclic) or zero-filled (extended).  Each lane
+// issues the loads of two rows (or four transposed columns) before any shared
+// store, so a warp has up to 16 global loads per lane in flight.
+template <typename InT, typename AccT>
+__device__ __forceinline__ AccT load_view_elem(const InT* __restrict__ rowp, const QuadDesc& Q, int32_t z) {
+  // z: window column in view coordinates (any integer)
+  if (Q.ext) {
+    if (z < 0 || z >= Q.L) return AccT(0);
+  } else if (z >= Q.L) {
+    z = z < 2 * Q.L ? z - Q.L : z % Q.L;  // z >= 0 in the cyclic case
+  }
+  if (Q.flip) z = Q.L - 1 - z;
+  return (AccT)rowp[z];
+}
+
 template <typename InT, typename AccT>
 __device__ __forceinline__ void stage_rows(const FusedParams& p, const QuadDesc& Q, int32_t a, int32_t m, int32_t x0,
                                            int32_t width, AccT* buf, int32_t rp) {
   const InT* __restrict__ in = static_cast<const InT*>(p.in);
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t nwarps = blockDim.x >> 5;
-  constexpr int U = 8;
+  constexpr int NCH = 8;  // 32-column chunks held per row (windows up to 256 columns in one sweep)
   if (!Q.transpose) {
     // the window needs no wrap and no zero fill: plain loads from one pointer
     const bool inside = x0 >= 0 && x0 + width <= Q.L;
-    for (int32_t r = warp; r < m; r += nwarps) {
-      AccT* dst = buf + (size_t)r * rp;
-      const InT* __restrict__ rowp = in + (int64_t)(a + r) * p.in_pitch;
-      if (inside) {
-        const int32_t step = Q.flip ? -1 : 1;
-        const InT* __restrict__ src = rowp + (Q.flip ? Q.L - 1 - x0 : x0) + step * lane;
-        for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
-          AccT v[U];
+    const int32_t step = Q.flip ? -1 : 1;
+    for (int32_t jb = 0; jb < width; jb += 32 * NCH) {
+      for (int32_t r0 = warp; r0 < m; r0 += 2 * nwarps) {
+        AccT v[2][NCH];
 #pragma unroll
-          for (int u = 0; u < U; u++) {
-            const int32_t j = j0 + u * 32;
-            v[u] = (j + lane < width) ? (AccT)src[step * j] : AccT(0);
-          }
+        for (int rr = 0; rr < 2; rr++) {
+          const int32_t r = r0 + rr * nwarps;
+          const InT* __restrict__ rowp = in + (int64_t)(a + min(r, m - 1)) * p.in_pitch;
+          const InT* __restrict__ src = rowp + (Q.flip ? Q.L - 1 - x0 : x0) + step * (jb + lane);
 #pragma unroll
-          for (int u = 0; u < U; u++) {
-            const int32_t j = j0 + u * 32 + lane;
-            if (j < width) dst[j] = v[u];
+          for (int c = 0; c < NCH; c++) {
+            const int32_t j = jb + c * 32 + lane;
+            const bool ok = r < m && j < width;
+            if (inside) {
+              v[rr][c] = ok ? (AccT)src[step * c * 32] : AccT(0);
+            } else {
+              v[rr][c] = ok ? load_view_elem<InT, AccT>(rowp, Q, x0 + j) : AccT(0);
+            }
           }
         }
-        continue;
-      }
-      for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
-        AccT v[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int32_t j = j0 + u * 32 + lane;
-          int32_t z = x0 + j;
-          bool ok = j < width;
-          if (Q.ext) {
-            ok = ok && z >= 0 && z < Q.L;
-          } else if (z >= Q.L) {
-            z = z < 2 * Q.L ? z - Q.L : z % Q.L;  // x0 >= 0 in the cyclic case
+        for (int rr = 0; rr < 2; rr++) {
+          const int32_t r = r0 + rr * nwarps;
+          if (r >= m) continue;
+          AccT* dst = buf + (size_t)r * rp;
+#pragma unroll
+          for (int c = 0; c < NCH; c++) {
+            const int32_t j = jb + c * 32 + lane;
+            if (j < width) dst[j] = v[rr][c];
           }
-          if (Q.flip) z = Q.L - 1 - z;
-          v[u] = ok ? (AccT)rowp[z] : AccT(0);
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int32_t j = j0 + u * 32 + lane;
-          if (j < width) dst[j] = v[u];
         }
       }
     }
   } else {
-    // transposed view: view row r is image column a + r; lanes run along r so
-    // that a warp reads consecutive image columns of one image row.
-    for (int32_t j = warp; j < width; j += nwarps) {
-      int32_t z = x0 + j;
-      bool valid = true;
-      if (Q.ext) {
-        valid = (z >= 0 && z < Q.L);
-      } else {
-        z %= Q.L;
+    // transposed view: view row r is image column a + r, window column j is an
+    // image row; lanes run along r so that a warp reads consecutive image
+    // columns of one image row.
+    constexpr int JB = 4;
+    for (int32_t j0 = warp; j0 < width; j0 += JB * nwarps) {
+      AccT v[JB][2];
+#pragma unroll
+      for (int jj = 0; jj < JB; jj++) {
+        const int32_t j = j0 + jj * nwarps;
+        int32_t z = x0 + j;
+        bool valid = j < width;
+        if (Q.ext) {
+          valid = valid && z >= 0 && z < Q.L;
+        } else {
+          z %= Q.L;
+        }
+        if (Q.flip) z = Q.L - 1 - z;
+        const InT* __restrict__ rowp = in + (int64_t)(valid ? z : 0) * p.in_pitch + a;
+#pragma unroll
+        for (int rr = 0; rr < 2; rr++) {
+          const int32_t r = lane + 32 * rr;
+          v[jj][rr] = (valid && r < m) ? (AccT)rowp[r] : AccT(0);
+        }
       }
-      for (int32_t r = lane; r < m; r += 32)
-        buf[(size_t)r * rp + j] = valid ? view_load<InT, AccT>(in, p.in_pitch, Q, a + r, z) : AccT(0);
+#pragma unroll
+      for (int jj = 0; jj < JB; jj++) {
+        const int32_t j = j0 + jj * nwarps;
+        if (j >= width) continue;
+#pragma unroll
+        for (int rr = 0; rr < 2; rr++) {
+          const int32_t r = lane + 32 * rr;
+          if (r < m) buf[(size_t)r * rp + j] = v[jj][rr];
+        }
+      }
     }
   }
 }
@@ -278,49 +302,45 @@ __device__ __forceinline__ void stage_gathered(const FusedParams& p, const Fused
   const AccT* __restrict__ ws = static_cast<const AccT*>(p.ws);
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t nwarps = blockDim.x >> 5;
-  constexpr int U = 8;
-  for (int32_t r = warp; r < 64; r += nwarps) {
-    const int32_t g = r / it.B, b = r - g * it.B;
-    const int32_t K = it.K0 + g;
-    const AccT* __restrict__ row = ws + it.src + (int64_t)(64 * b + K) * it.src_pitch;
-    const int32_t base = x0 + K * b + it.c_src;
-    AccT* dst = buf + (size_t)r * rp;
-    const int32_t lim = Q.ext ? it.wsrc : Q.W;
-    if (base >= 0 && base + width <= lim) {
-      const AccT* __restrict__ src = row + base + lane;
-      for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
-        AccT v[U];
+  constexpr int NCH = 8;
+  const int32_t lim = Q.ext ? it.wsrc : Q.W;
+  for (int32_t jb = 0; jb < width; jb += 32 * NCH) {
+    for (int32_t r0 = warp; r0 < 64; r0 += 2 * nwarps) {
+      AccT v[2][NCH];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int32_t j = j0 + u * 32;
-          v[u] = (j + lane < width) ? ld_ws<kC>(src + j) : AccT(0);
-        }
+      for (int rr = 0; rr < 2; rr++) {
+        const int32_t r = min(r0 + rr * nwarps, 63);
+        const bool rok = r0 + rr * nwarps < 64;
+        const int32_t g = r / it.B, b = r - g * it.B;
+        const int32_t K = it.K0 + g;
+        const AccT* __restrict__ row = ws + it.src + (int64_t)(64 * b + K) * it.src_pitch;
+        const int32_t base = x0 + K * b + it.c_src;  // >= 0 in the cyclic case
+        const bool inside = base >= 0 && base + width <= lim;
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int32_t j = j0 + u * 32 + lane;
-          if (j < width) dst[j] = v[u];
+        for (int c = 0; c < NCH; c++) {
+          const int32_t j = jb + c * 32 + lane;
+          int32_t z = base + j;
+          bool ok = rok && j < width;
+          if (!inside) {
+            if (Q.ext) {
+              ok = ok && z >= 0 && z < it.wsrc;
+            } else {
+              z = z % Q.W;
+            }
+          }
+          v[rr][c] = ok ? ld_ws<kC>(row + z) : AccT(0);
         }
       }
-      continue;
-    }
-    for (int32_t j0 = 0; j0 < width; j0 += 32 * U) {
-      AccT v[U];
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int32_t j = j0 + u * 32 + lane;
-        int32_t z = base + j;
-        bool ok = j < width;
-        if (Q.ext) {
-          ok = ok && z >= 0 && z < it.wsrc;
-        } else {
-          z = z % Q.W;  // base >= 0 in the cyclic case
+      for (int rr = 0; rr < 2; rr++) {
+        const int32_t r = r0 + rr * nwarps;
+        if (r >= 64) continue;
+        AccT* dst = buf + (size_t)r * rp;
+#pragma unroll
+        for (int c = 0; c < NCH; c++) {
+          const int32_t j = jb + c * 32 + lane;
+          if (j < width) dst[j] = v[rr][c];
         }
-        v[u] = ok ? ld_ws<kC>(row + z) : AccT(0);
-      }
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int32_t j = j0 + u * 32 + lane;
-        if (j < width) dst[j] = v[u];
       }
     }
   }
@@ -459,28 +479,28 @@ constexpr int kMaxSpineTerms = 16;
 constexpr int kSpineRows = 16;
 constexpr int kSpineTile = 1024;
 
-template <bool kC, int NT, typename AccT>
+// One output row x one column tile of BS * QPT columns: every thread owns QPT
+// columns spaced BS apart.
+template <bool kC, int NT, int BS, int QPT, typename AccT>
 __device__ __forceinline__ void spine_tile(const SpineTerm* st, const QuadDesc& Q, const AccT* __restrict__ ws,
                                            AccT* __restrict__ dst, int32_t u0) {
-  AccT acc[4];
-#pragma unroll
-  for (int q = 0; q < 4; q++) acc[q] = AccT(0);
-  AccT v[NT][4];
-  const bool full = u0 + 1024 <= Q.W;
+  AccT v[NT][QPT];
+  const bool full = u0 + BS * QPT <= Q.W;
 #pragma unroll
   for (int c = 0; c < NT; c++) {
     const int32_t off = st[c].off, wpart = st[c].wpart;
     const AccT* __restrict__ row = ws + st[c].row;
     // the whole tile reads one contiguous stretch of the part row
-    const bool clean = full && (Q.ext ? (u0 + off >= 0 && u0 + 1023 + off < wpart) : (u0 + 1023 + off < Q.W));
+    const bool clean =
+        full && (Q.ext ? (u0 + off >= 0 && u0 + BS * QPT - 1 + off < wpart) : (u0 + BS * QPT - 1 + off < Q.W));
     if (clean) {
       const AccT* __restrict__ src = row + u0 + off + (int32_t)threadIdx.x;
 #pragma unroll
-      for (int q = 0; q < 4; q++) v[c][q] = ld_ws<kC>(src + q * 256);
+      for (int q = 0; q < QPT; q++) v[c][q] = ld_ws<kC>(src + q * BS);
     } else {
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const int32_t u = u0 + q * 256 + (int32_t)threadIdx.x;
+      for (int q = 0; q < QPT; q++) {
+        const int32_t u = u0 + q * BS + (int32_t)threadIdx.x;
         int32_t i = u + off;
         bool ok = u < Q.W;
         if (Q.ext) {
@@ -493,17 +513,40 @@ __device__ __forceinline__ void spine_tile(const SpineTerm* st, const QuadDesc& 
     }
   }
 #pragma unroll
-  for (int c = 0; c < NT; c++)
+  for (int q = 0; q < QPT; q++) {
+    AccT acc = v[0][q];
 #pragma unroll
-    for (int q = 0; q < 4; q++) acc[q] += v[c][q];
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    const int32_t u = u0 + q * 256 + (int32_t)threadIdx.x;
+    for (int c = 1; c < NT; c++) acc += v[c][q];
+    const int32_t u = u0 + q * BS + (int32_t)threadIdx.x;
     if (u < Q.W) {
       int32_t X = Q.sigma * u + Q.kappa;
       if (X < 0) X += Q.W;
       if (X >= Q.W) X -= Q.W;
-      dst[X] = acc[q];
+      dst[X] = acc;
+    }
+  }
+}
+
+// Rows [r0, r0 + nr) of a spine (terms staged in shared memory by the caller)
+// for the column tile starting at u0.
+template <bool kC, int BS, int QPT, typename AccT>
+__device__ __forceinline__ void spine_rows_tile(const SpineRow* sr, SpineTerm (*st)[kMaxSpineTerms], int32_t nr,
+                                                const QuadDesc* quads, const AccT* ws, AccT* out, int32_t u0) {
+  for (int32_t r = 0; r < nr; r++) {
+    const QuadDesc& Q = quads[sr[r].q];
+    if (u0 >= Q.W) continue;
+    AccT* dst = out + sr[r].dst;
+    switch (sr[r].term_count) {
+#define FHT_SPINE_CASE(N)                                        \
+  case N:                                                        \
+    spine_tile<kC, N, BS, QPT, AccT>(st[r], Q, ws, dst, u0);     \
+    break;
+      FHT_SPINE_CASE(1) FHT_SPINE_CASE(2) FHT_SPINE_CASE(3) FHT_SPINE_CASE(4) FHT_SPINE_CASE(5) FHT_SPINE_CASE(6)
+      FHT_SPINE_CASE(7) FHT_SPINE_CASE(8) FHT_SPINE_CASE(9) FHT_SPINE_CASE(10) FHT_SPINE_CASE(11)
+      FHT_SPINE_CASE(12) FHT_SPINE_CASE(13) FHT_SPINE_CASE(14) FHT_SPINE_CASE(15) FHT_SPINE_CASE(16)
+#undef FHT_SPINE_CASE
+      default:
+        break;
     }
   }
 }

@@ -92,23 +92,7 @@ __global__ void __launch_bounds__(256) spine_kernel(const SpineRow* __restrict__
     if (c < sr[r].term_count) st[r][c] = terms[sr[r].term_begin + c];
   }
   __syncthreads();
-  for (int32_t r = 0; r < nr; r++) {
-    const QuadDesc& Q = quads.q[sr[r].q];
-    if (u0 >= Q.W) continue;
-    AccT* dst = out + sr[r].dst;
-    switch (sr[r].term_count) {
-#define FHT_SPINE_CASE(N) \
-  case N:                 \
-    spine_tile<false, N, AccT>(st[r], Q, ws, dst, u0); \
-    break;
-      FHT_SPINE_CASE(1) FHT_SPINE_CASE(2) FHT_SPINE_CASE(3) FHT_SPINE_CASE(4) FHT_SPINE_CASE(5) FHT_SPINE_CASE(6)
-      FHT_SPINE_CASE(7) FHT_SPINE_CASE(8) FHT_SPINE_CASE(9) FHT_SPINE_CASE(10) FHT_SPINE_CASE(11)
-      FHT_SPINE_CASE(12) FHT_SPINE_CASE(13) FHT_SPINE_CASE(14) FHT_SPINE_CASE(15) FHT_SPINE_CASE(16)
-#undef FHT_SPINE_CASE
-      default:
-        break;
-    }
-  }
+  spine_rows_tile<false, 256, 4, AccT>(sr, st, nr, quads.q, ws, out, u0);
 }
 
 // ------------------------------------------------------------------------

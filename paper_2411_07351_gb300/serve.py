@@ -45,12 +45,15 @@ class _Batch:
     reqs: list
     slot: int
     stream: torch.cuda.Stream = field(default=None)
+    by_rid: dict = field(default_factory=dict)
 
 
 class Server:
     def __init__(self, device: int = 0, budget_bytes: int = 16 << 30, streams: int = 4, quads: int = C.FHT_QALL,
-                 boundary: str = "cyclic", split: str = "T", max_batch: int = 1024, keep_outputs: bool = True):
+                 boundary: str = "cyclic", split: str = "T", max_batch: int = 1024, keep_outputs: bool = True,
+                 max_batch_pixels: int = 16 << 20):
         self.device = device
+        self.max_batch_pixels = max_batch_pixels
         self.keep_outputs = keep_outputs
         self.budget = budget_bytes
         self.quads, self.boundary, self.split = quads, boundary, split
@@ -91,15 +94,20 @@ class Server:
     def _retire(self, now_fn):
         still = []
         for b in self.running:
-            if b.event.query():
-                t = now_fn()
+            # requests finish one by one (per-job completion flags) ...
+            for rid in self.queues[b.slot].poll(cap=len(b.reqs)):
+                r = b.by_rid.pop(rid, None)
+                if r is None:
+                    continue
+                r.done = now_fn()
+                self.used -= r.nbytes
+                if not self.keep_outputs:
+                    r.out = None
+                self.finished.append(r)
+            # ... and the stream slot frees up when the whole launch has ended
+            if not b.by_rid and b.event.query():
                 for r in b.reqs:
-                    r.done = t
-                    self.used -= r.nbytes
-                    r.ws = None  # workspace back to the caching allocator
-                    if not self.keep_outputs:
-                        r.out = None
-                    self.finished.append(r)
+                    r.ws = None  # workspaces go back once the launch has ended
                 self.free_slots.append(b.slot)
             else:
                 still.append(b)
@@ -108,9 +116,11 @@ class Server:
     def _launch(self):
         while self.admitted and self.free_slots:
             slot = self.free_slots.popleft()
-            reqs = []
-            while self.admitted and len(reqs) < self.max_batch:
-                reqs.append(self.admitted.popleft())
+            reqs, pix = [], 0
+            while self.admitted and len(reqs) < self.max_batch and (not reqs or pix < self.max_batch_pixels):
+                r = self.admitted.popleft()
+                pix += r.image.numel()
+                reqs.append(r)
             s = self.streams[slot]
             with torch.cuda.stream(s):
                 for r in reqs:
@@ -118,10 +128,11 @@ class Server:
                     r.ws = r.plan.new_workspace()
                     r.batch_size = len(reqs)
                 self.queues[slot].submit([r.image for r in reqs], self.quads, self.boundary, self.split,
-                                         outs=[r.out for r in reqs], workspaces=[r.ws for r in reqs], stream=s)
+                                         outs=[r.out for r in reqs], workspaces=[r.ws for r in reqs], stream=s,
+                                         tags=[r.rid for r in reqs])
                 ev = torch.cuda.Event()
                 ev.record(s)
-            self.running.append(_Batch(ev, reqs, slot, s))
+            self.running.append(_Batch(ev, reqs, slot, s, {r.rid: r for r in reqs}))
             self.batches += 1
 
     def step(self, now_fn):

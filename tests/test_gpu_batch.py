@@ -107,6 +107,12 @@ def test_batch_poll_tags(F, queue):
     torch.cuda.synchronize()
     assert sorted(queue.poll()) == [11, 12, 13, 14]
     assert queue.poll() == []
+    # jobs are reported one by one: after a submit finishes, polling with a
+    # small cap returns the tags in pieces
+    queue.submit(xs, 15, "cyclic", tags=[21, 22, 23, 24])
+    torch.cuda.synchronize()
+    got = queue.poll(cap=3) + queue.poll(cap=3)
+    assert sorted(got) == [21, 22, 23, 24]
 
 
 def test_batch_graph_replay(F, queue):
