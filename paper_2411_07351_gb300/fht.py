@@ -37,8 +37,15 @@ class Plan:
 
     def __init__(self, h: int, w: int, dtype=torch.float32, quads: int = C.FHT_QALL,
                  boundary: str = "cyclic", split: str = "T", device: int | None = None,
-                 fused_rows: int = 0, tile_cols: int = 0, threads: int = 0, with_adjoint: bool = False):
+                 fused_rows: int = 0, tile_cols: int = 0, threads: int = 0, with_adjoint: bool = False,
+                 tuning: str | None = None):
         self._lib = C.load()
+        if tuning == "auto" and not (tile_cols or threads):
+            from .tune import lookup
+
+            best = lookup(h, w, dtype, quads, boundary, split)
+            if best:
+                tile_cols, threads = int(best["tile_cols"]), int(best["threads"])
         if dtype not in DTYPES:
             raise ValueError(f"unsupported dtype {dtype}")
         self.h, self.w = int(h), int(w)

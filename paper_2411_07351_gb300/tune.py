@@ -1,0 +1,108 @@
+"""Autotuner for the forward transform's launch shape.
+
+For a size bucket it times ``fht_forward`` with each candidate (column tile
+of the fused / band passes x threads per CTA) using CUDA events, keeps the
+fastest and records it in a JSON cache keyed by (h bucket, w bucket, dtype,
+quadrants, boundary, split).  ``Plan(..., tuning="auto")`` reads the cache.
+Every candidate computes the same result (the tests check this); only speed
+differs.
+
+Cache file: $FHT_TUNE_CACHE, else ~/.cache/fht_tune.json.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+import threading
+
+import torch
+
+from . import _capi as C
+
+CANDIDATES = [(tc, th) for tc in (64, 96, 128, 192, 256) for th in (256, 512)]
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    return os.environ.get("FHT_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "fht_tune.json"))
+
+
+def bucket(n: int) -> int:
+    """Sizes are bucketed on a half-octave grid (64, 91, 128, 181, 256, ...)."""
+    return int(round(2 ** (round(2 * math.log2(max(n, 1))) / 2)))
+
+
+def key(h, w, dtype, quads, boundary, split) -> str:
+    return f"{bucket(h)}x{bucket(w)}:{str(dtype).replace('torch.', '')}:q{quads}:{boundary}:{split}"
+
+
+def load_cache() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(d: dict):
+    path = cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def lookup(h, w, dtype, quads, boundary, split):
+    with _lock:
+        return load_cache().get(key(h, w, dtype, quads, boundary, split))
+
+
+def _time_plan(plan, x, reps: int) -> float:
+    out, ws = plan.new_output(), plan.new_workspace()
+    for _ in range(3):
+        plan.forward(x, out, ws)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.forward(x, out, ws)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def tune(h: int, w: int, dtype=torch.float32, quads: int = C.FHT_QALL, boundary: str = "cyclic", split: str = "T",
+         candidates=None, reps: int = 10, device: int | None = None, save: bool = True) -> dict:
+    """Time every candidate on a seeded image of this size; return (and cache) the best."""
+    from .fht import Plan
+
+    dev = torch.cuda.current_device() if device is None else device
+    g = torch.Generator(device=f"cuda:{dev}").manual_seed(1234)
+    if dtype == torch.uint8:
+        x = torch.randint(0, 256, (h, w), generator=g, device=f"cuda:{dev}", dtype=torch.int32).to(torch.uint8)
+    elif dtype == torch.int32:
+        x = torch.randint(-100, 100, (h, w), generator=g, device=f"cuda:{dev}", dtype=torch.int32)
+    else:
+        x = torch.randn((h, w), generator=g, device=f"cuda:{dev}", dtype=dtype)
+    results = []
+    for tc, th in candidates or CANDIDATES:
+        try:
+            p = Plan(h, w, dtype, quads, boundary, split, dev, tile_cols=tc, threads=th)
+        except C.FHTError:
+            continue  # e.g. too much shared memory for this dtype
+        results.append((_time_plan(p, x, reps), tc, th))
+        p.close()
+    results.sort()
+    ms, tc, th = results[0]
+    entry = {"tile_cols": tc, "threads": th, "ms": ms, "candidates": [[r[1], r[2], r[0]] for r in results]}
+    if save:
+        with _lock:
+            d = load_cache()
+            d[key(h, w, dtype, quads, boundary, split)] = entry
+            save_cache(d)
+    return entry
