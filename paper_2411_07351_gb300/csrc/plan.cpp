@@ -44,6 +44,33 @@ void merge_entry(int32_t m, int32_t m0, int32_t m1, int32_t t, int32_t& t1, int3
   s = t - t2;
 }
 
+// Nearest integer to q + r / d (0 <= r < d), ties to even.
+static inline int32_t round_qr(int64_t q, int64_t r, int64_t d) {
+  if (2 * r > d) return (int32_t)(q + 1);
+  if (2 * r < d) return (int32_t)q;
+  return (int32_t)(q + (q & 1));
+}
+
+void merge_table(int32_t m, int32_t m0, int32_t m1, std::vector<MergeRow>& out) {
+  out.resize(m);
+  const int64_t d = m - 1;
+  int64_t q0 = 0, r0 = 0, q1 = 0, r1 = 0;  // t (m0 - 1) = q0 d + r0, t (m1 - 1) = q1 d + r1
+  for (int32_t t = 0; t < m; t++) {
+    const int32_t t1 = round_qr(q0, r0, d), t2 = round_qr(q1, r1, d);
+    out[t] = MergeRow{t1, t2, t - t2};
+    r0 += m0 - 1;  // m_i - 1 < d, so one subtraction restores r < d
+    if (r0 >= d) {
+      r0 -= d;
+      q0++;
+    }
+    r1 += m1 - 1;
+    if (r1 >= d) {
+      r1 -= d;
+      q1++;
+    }
+  }
+}
+
 static int32_t build_rec(Tree& tr, int32_t a, int32_t m, Split rule) {
   TreeNode nd;
   nd.a = a;
@@ -96,9 +123,10 @@ static void build_program(const Tree& tr, int32_t r, std::vector<MergeOp>& ops, 
       const TreeNode& nd = tr.nodes[i];
       const TreeNode& c0 = tr.nodes[nd.child[0]];
       const TreeNode& c1 = tr.nodes[nd.child[1]];
+      std::vector<MergeRow> mtab;
+      merge_table(nd.m, c0.m, c1.m, mtab);
       for (int32_t t = 0; t < nd.m; t++) {
-        int32_t t1, t2, s;
-        merge_entry(nd.m, c0.m, c1.m, t, t1, t2, s);
+        const int32_t t1 = mtab[t].t1, t2 = mtab[t].t2, s = mtab[t].s;
         MergeOp op;
         op.top = (int16_t)(c0.a - base + t1);
         op.bot = (int16_t)(c1.a - base + t2);
@@ -357,6 +385,12 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
         P.band_bytes += ((int64_t)band.m * (cfg.ext ? Q.L + 63 : Q.W) + (int64_t)band.m * bi_width(cfg, Q, band.m)) * acc;
       }
       if (!spine.empty()) {
+        std::vector<std::vector<MergeRow>> stab(spine.size());
+        for (size_t k = 0; k < spine.size(); k++) {
+          const TreeNode& nd = tr.nodes[spine[k]];
+          merge_table(nd.m, tr.nodes[nd.child[0]].m, tr.nodes[nd.child[1]].m, stab[k]);
+        }
+        P.spine_terms.reserve(P.spine_terms.size() + (size_t)tr.n * (spine.size() + 1));
         // every output slope t: follow the spine, collecting (part, row, offset)
         for (int32_t t = 0; t < tr.n; t++) {
           SpineRow sr;
@@ -371,17 +405,16 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
             SpineTerm st;
             st.row = buf_row(part_buf(pi), pt.a + row);
             st.wpart = part_w(pi);
-            st.off = cfg.ext ? (int32_t)(off + pt.m - tr.n) : (int32_t)(off % Q.W);
+            st.off = cfg.ext ? (int32_t)(off + pt.m - tr.n) : (int32_t)off;  // off kept reduced mod W
             P.spine_terms.push_back(st);
           };
           for (size_t k = 0; k < spine.size(); k++) {
             const TreeNode& nd = tr.nodes[spine[k]];
-            const TreeNode& c0 = tr.nodes[nd.child[0]];
-            const TreeNode& c1 = tr.nodes[nd.child[1]];
-            int32_t t1, t2, sh;
-            merge_entry(nd.m, c0.m, c1.m, tn, t1, t2, sh);
+            const MergeRow& mr = stab[k][tn];
+            const int32_t t1 = mr.t1, t2 = mr.t2, sh = mr.s;
             add_term(nd.child[0], t1);
             off += sh;
+            if (!cfg.ext && off >= Q.W) off = off < 2 * (int64_t)Q.W ? off - Q.W : off % Q.W;
             tn = t2;
             if (k + 1 == spine.size()) add_term(nd.child[1], t2);
           }
@@ -410,10 +443,11 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
       const int32_t wout = cfg.ext ? Q.L + nd.m - 1 : Q.W;
       const int32_t wtop = cfg.ext ? Q.L + c0.m - 1 : Q.W;
       const int32_t wbot = cfg.ext ? Q.L + c1.m - 1 : Q.W;
+      std::vector<MergeRow> mtab;
+      if (!use_bands || cfg.with_adjoint) merge_table(nd.m, c0.m, c1.m, mtab);
       // per-height forward rows: only for trees that do not use the band schedule
       for (int32_t t = 0; t < (use_bands ? 0 : nd.m); t++) {
-        int32_t t1, t2, s;
-        merge_entry(nd.m, c0.m, c1.m, t, t1, t2, s);
+        const int32_t t1 = mtab[t].t1, t2 = mtab[t].t2, s = mtab[t].s;
         RowJob rj;
         rj.dst = fin ? Q.out_off + (int64_t)t * Q.W : buf_row(nd.buf, nd.a + t);
         rj.top = buf_row(c0.buf, c0.a + t1);
@@ -444,8 +478,7 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
         const TreeNode& ch = c == 0 ? c0 : c1;
         std::vector<std::vector<AdjTerm>> lists(ch.m);
         for (int32_t t = 0; t < nd.m; t++) {
-          int32_t t1, t2, s;
-          merge_entry(nd.m, c0.m, c1.m, t, t1, t2, s);
+          const int32_t t1 = mtab[t].t1, t2 = mtab[t].t2, s = mtab[t].s;
           int32_t e;
           if (c == 0) {
             e = cfg.ext ? c1.m : 0;  // -dtop

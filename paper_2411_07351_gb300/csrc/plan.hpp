@@ -39,6 +39,13 @@ Tree build_tree(int32_t n, Split rule);
 // t -> (t1, t2, s) with t1 = [t(m0-1)/(m-1)], t2 = [t(m1-1)/(m-1)], s = t - t2.
 void merge_entry(int32_t m, int32_t m0, int32_t m1, int32_t t, int32_t& t1, int32_t& t2, int32_t& s);
 
+// The whole table of one node, t = 0..m-1, computed without division: the
+// quotient and remainder of t (m_i - 1) / (m - 1) are stepped as t grows.
+struct MergeRow {
+  int32_t t1, t2, s;
+};
+void merge_table(int32_t m, int32_t m0, int32_t m1, std::vector<MergeRow>& out);
+
 struct PlanConfig {
   int32_t h = 0, w = 0;
   int32_t dtype = 0;       // fht_dtype

@@ -16,6 +16,8 @@ one stream as soon as the request arrives.
 from __future__ import annotations
 
 import collections
+import concurrent.futures as cf
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -37,6 +39,40 @@ class Request:
     done: float | None = None
     plan: object = None
     batch_size: int = 0
+    plan_future: object = None
+
+
+class PlanBuilder:
+    """Builds plans on a thread pool (the C call releases the GIL), one
+    future per distinct shape, so that the serving thread never waits for a
+    plan it does not need yet."""
+
+    def __init__(self, device: int, quads: int, boundary: str, split: str, workers: int = 8):
+        self.device, self.quads, self.boundary, self.split = device, quads, boundary, split
+        self.cache = PlanCache(capacity=8192)
+        self.pool = cf.ThreadPoolExecutor(max_workers=workers)
+        self.futures: dict = {}
+        self.lock = threading.Lock()
+
+    def _build(self, h, w, dtype):
+        torch.cuda.set_device(self.device)
+        return self.cache.get(h, w, dtype, self.quads, self.boundary, self.split, self.device)
+
+    def request(self, req: "Request"):
+        k = (req.image.shape[0], req.image.shape[1], req.image.dtype)
+        with self.lock:
+            f = self.futures.get(k)
+            if f is None:
+                f = self.pool.submit(self._build, *k)
+                self.futures[k] = f
+                if len(self.futures) > 16384:  # forget old futures; plans stay in the LRU cache
+                    for old in list(self.futures)[:4096]:
+                        if self.futures[old].done():
+                            del self.futures[old]
+        req.plan_future = f
+
+    def close(self):
+        self.pool.shutdown(wait=True)
 
 
 @dataclass
@@ -58,7 +94,7 @@ class Server:
         self.budget = budget_bytes
         self.quads, self.boundary, self.split = quads, boundary, split
         self.max_batch = max_batch
-        self.plans = PlanCache(capacity=4096)
+        self.builder = PlanBuilder(device, quads, boundary, split)
         self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
         self.queues = [BatchQueue(device=device, max_jobs=max_batch, max_units=1 << 22) for _ in range(streams)]
         self.free_slots = collections.deque(range(streams))
@@ -70,20 +106,19 @@ class Server:
         self.max_used = 0
         self.batches = 0
 
-    def footprint(self, req: Request) -> int:
-        p = self.plans.get(req.image.shape[0], req.image.shape[1], req.image.dtype, self.quads, self.boundary,
-                           self.split, self.device)
-        req.plan = p
-        return p.out_elems * 4 + max(p.workspace_bytes, 256)
-
     def arrive(self, req: Request):
+        self.builder.request(req)
         self.waiting.append(req)
 
     def _admit(self):
         while self.waiting:
             req = self.waiting[0]
-            need = req.nbytes or self.footprint(req)
-            req.nbytes = need
+            if req.plan is None:
+                if not req.plan_future.done():
+                    break  # admission stays in arrival order
+                req.plan = req.plan_future.result()
+                req.nbytes = req.plan.out_elems * 4 + max(req.plan.workspace_bytes, 256)
+            need = req.nbytes
             if self.used + need > self.budget and self.used > 0:
                 break
             self.waiting.popleft()
@@ -144,6 +179,7 @@ class Server:
         return not (self.waiting or self.admitted or self.running)
 
     def close(self):
+        self.builder.close()
         for q in self.queues:
             q.close()
 
@@ -158,7 +194,7 @@ class PlainServer:
         self.budget = budget_bytes
         self.keep_outputs = keep_outputs
         self.quads, self.boundary, self.split = quads, boundary, split
-        self.plans = PlanCache(capacity=4096)
+        self.builder = PlanBuilder(device, quads, boundary, split)
         self.stream = torch.cuda.Stream(device=device)
         self.waiting: collections.deque = collections.deque()
         self.running: collections.deque = collections.deque()
@@ -168,14 +204,16 @@ class PlainServer:
         self.batches = 0
 
     def arrive(self, req: Request):
+        self.builder.request(req)
         self.waiting.append(req)
 
     def _launch(self):
         while self.waiting:
             req = self.waiting[0]
             if req.plan is None:
-                req.plan = self.plans.get(req.image.shape[0], req.image.shape[1], req.image.dtype, self.quads,
-                                          self.boundary, self.split, self.device)
+                if not req.plan_future.done():
+                    return
+                req.plan = req.plan_future.result()
                 req.nbytes = req.plan.out_elems * 4 + max(req.plan.workspace_bytes, 256)
             if self.used + req.nbytes > self.budget and self.used > 0:
                 return
@@ -208,7 +246,7 @@ class PlainServer:
         return not (self.running or self.waiting)
 
     def close(self):
-        pass
+        self.builder.close()
 
 
 def run_stream(server, requests):
