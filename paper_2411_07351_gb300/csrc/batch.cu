@@ -103,7 +103,7 @@ __device__ void batch_spine(const BatchJob& jb, int32_t r0, int32_t tile, SpineT
   }
   __syncthreads();
   // 512 threads x 2 columns: the same 1024-column tile as the plain spine kernel
-  spine_rows_tile<true, 512, 2, AccT>(sr, st, nr, jb.fp.quad, ws, out, u0);
+  spine_rows_tile<true, 512, 2, AccT, false>(sr, st, nr, jb.fp.quad, ws, out, u0);
 }
 
 // counters[0]: next unit; counters[1 + j]: finished units of job j.

@@ -527,11 +527,97 @@ __device__ __forceinline__ void spine_tile(const SpineTerm* st, const QuadDesc& 
   }
 }
 
+// Loads of one spine row's terms for this thread's QPT columns
+// u = u0 + tid + q BS.  Branch-free: for each term the columns that read
+// inside the part row (extended) or that wrap (cyclic) form one contiguous
+// range of q BS, found from two thresholds; every load uses the term's
+// hoisted pointer with a compile-time offset.
+template <bool kC, int NT, int BS, int QPT, typename AccT>
+__device__ __forceinline__ void spine_load(const SpineTerm* st, const QuadDesc& Q, const AccT* __restrict__ ws,
+                                           int32_t u0, AccT (&v)[NT][QPT]) {
+  const int32_t base_u = u0 + (int32_t)threadIdx.x;
+  const int32_t live = Q.W - base_u;  // column q is inside the output row iff q BS < live
+#pragma unroll
+  for (int c = 0; c < NT; c++) {
+    const int32_t off = st[c].off;
+    const AccT* __restrict__ src = ws + st[c].row + (base_u + off);
+    if (Q.ext) {
+      const int32_t lo = -(base_u + off), hi = st[c].wpart - (base_u + off);  // valid iff lo <= q BS < hi
+#pragma unroll
+      for (int q = 0; q < QPT; q++)
+        v[c][q] = (q * BS >= lo && q * BS < hi && q * BS < live) ? ld_ws<kC>(src + q * BS) : AccT(0);
+    } else {
+      const int32_t wrap = Q.W - (base_u + off);  // q BS >= wrap reads W columns back
+#pragma unroll
+      for (int q = 0; q < QPT; q++) {
+        const AccT* p = (q * BS >= wrap) ? src - Q.W : src;
+        v[c][q] = (q * BS < live) ? ld_ws<kC>(p + q * BS) : AccT(0);
+      }
+    }
+  }
+}
+
+template <int NT, int BS, int QPT, typename AccT>
+__device__ __forceinline__ void spine_store(const QuadDesc& Q, AccT* __restrict__ dst, int32_t u0,
+                                            const AccT (&v)[NT][QPT]) {
+#pragma unroll
+  for (int q = 0; q < QPT; q++) {
+    AccT acc = v[0][q];
+#pragma unroll
+    for (int c = 1; c < NT; c++) acc += v[c][q];
+    const int32_t u = u0 + q * BS + (int32_t)threadIdx.x;
+    if (u < Q.W) {
+      int32_t X = Q.sigma * u + Q.kappa;
+      if (X < 0) X += Q.W;
+      if (X >= Q.W) X -= Q.W;
+      dst[X] = acc;
+    }
+  }
+}
+
+// All nr rows share one quadrant and one term count: the loads of row r + 1
+// are issued before row r is summed and stored, so two rows of loads are in
+// flight per thread.
+template <bool kC, int NT, int BS, int QPT, typename AccT>
+__device__ __forceinline__ void spine_group_pipelined(const SpineRow* sr, SpineTerm (*st)[kMaxSpineTerms],
+                                                      int32_t nr, const QuadDesc& Q, const AccT* ws, AccT* out,
+                                                      int32_t u0) {
+  AccT a[NT][QPT], b[NT][QPT];
+  spine_load<kC, NT, BS, QPT, AccT>(st[0], Q, ws, u0, a);
+  for (int32_t r = 0; r < nr; r += 2) {
+    if (r + 1 < nr) spine_load<kC, NT, BS, QPT, AccT>(st[r + 1], Q, ws, u0, b);
+    spine_store<NT, BS, QPT, AccT>(Q, out + sr[r].dst, u0, a);
+    if (r + 1 >= nr) break;
+    if (r + 2 < nr) spine_load<kC, NT, BS, QPT, AccT>(st[r + 2], Q, ws, u0, a);
+    spine_store<NT, BS, QPT, AccT>(Q, out + sr[r + 1].dst, u0, b);
+  }
+}
+
 // Rows [r0, r0 + nr) of a spine (terms staged in shared memory by the caller)
 // for the column tile starting at u0.
-template <bool kC, int BS, int QPT, typename AccT>
+template <bool kC, int BS, int QPT, typename AccT, bool kPipe = true>
 __device__ __forceinline__ void spine_rows_tile(const SpineRow* sr, SpineTerm (*st)[kMaxSpineTerms], int32_t nr,
                                                 const QuadDesc* quads, const AccT* ws, AccT* out, int32_t u0) {
+  bool uniform = kPipe && nr > 0;
+  for (int32_t r = 1; r < nr; r++)
+    uniform = uniform && sr[r].q == sr[0].q && sr[r].term_count == sr[0].term_count;
+  if constexpr (kPipe) {
+  if (uniform) {
+    const QuadDesc& Q = quads[sr[0].q];
+    if (u0 >= Q.W) return;
+    switch (sr[0].term_count) {
+#define FHT_SPINE_PIPE(N)                                                                 \
+  case N:                                                                                 \
+    spine_group_pipelined<kC, N, BS, QPT, AccT>(sr, st, nr, Q, ws, out, u0);              \
+    return;
+      FHT_SPINE_PIPE(1) FHT_SPINE_PIPE(2) FHT_SPINE_PIPE(3) FHT_SPINE_PIPE(4) FHT_SPINE_PIPE(5)
+      FHT_SPINE_PIPE(6) FHT_SPINE_PIPE(7) FHT_SPINE_PIPE(8)
+#undef FHT_SPINE_PIPE
+      default:
+        break;  // more terms: the row-by-row path below
+    }
+  }
+  }
   for (int32_t r = 0; r < nr; r++) {
     const QuadDesc& Q = quads[sr[r].q];
     if (u0 >= Q.W) continue;
