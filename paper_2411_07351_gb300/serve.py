@@ -3,9 +3,11 @@
 Requests (images of any size) arrive over time.  The server keeps plans in
 an LRU cache and buffers in PyTorch's caching allocator, admits a request
 only while the device-memory budget (output + workspace of every admitted,
-unfinished request) has room, and on every turn of its loop submits all
-admitted requests that are not yet running as ONE persistent batched launch
-(fht_submit) on a stream whose previous batch has finished.  Batches on
+unfinished request) has room, and on every turn of its loop submits the
+admitted small requests that are not yet running as ONE persistent batched
+launch (fht_submit) on a stream whose previous launch has finished; a large
+request (at least ``plain_pixels``) fills the GPU by itself and runs the
+per-image kernels on a stream of its own.  Batches on
 different streams overlap on the device; a request that arrives while others
 run joins the next batch as soon as memory and a stream are free.  Latency is
 arrival -> the host seeing the batch's completion event.
@@ -82,14 +84,16 @@ class _Batch:
     slot: int
     stream: torch.cuda.Stream = field(default=None)
     by_rid: dict = field(default_factory=dict)
+    plain: bool = False
 
 
 class Server:
     def __init__(self, device: int = 0, budget_bytes: int = 16 << 30, streams: int = 4, quads: int = C.FHT_QALL,
                  boundary: str = "cyclic", split: str = "T", max_batch: int = 1024, keep_outputs: bool = True,
-                 max_batch_pixels: int = 16 << 20):
+                 max_batch_pixels: int = 16 << 20, plain_pixels: int = 1 << 20):
         self.device = device
         self.max_batch_pixels = max_batch_pixels
+        self.plain_pixels = plain_pixels
         self.keep_outputs = keep_outputs
         self.budget = budget_bytes
         self.quads, self.boundary, self.split = quads, boundary, split
@@ -129,6 +133,19 @@ class Server:
     def _retire(self, now_fn):
         still = []
         for b in self.running:
+            if b.plain:
+                if b.event.query():
+                    r = b.reqs[0]
+                    r.done = now_fn()
+                    self.used -= r.nbytes
+                    r.ws = None
+                    if not self.keep_outputs:
+                        r.out = None
+                    self.finished.append(r)
+                    self.free_slots.append(b.slot)
+                else:
+                    still.append(b)
+                continue
             # requests finish one by one (per-job completion flags) ...
             for rid in self.queues[b.slot].poll(cap=len(b.reqs)):
                 r = b.by_rid.pop(rid, None)
@@ -151,12 +168,28 @@ class Server:
     def _launch(self):
         while self.admitted and self.free_slots:
             slot = self.free_slots.popleft()
+            s = self.streams[slot]
+            head = self.admitted[0]
+            if head.image.numel() >= self.plain_pixels:
+                # a large request fills the GPU by itself: the per-image kernels,
+                # no persistent batch
+                r = self.admitted.popleft()
+                with torch.cuda.stream(s):
+                    r.out = r.plan.new_output()
+                    r.ws = r.plan.new_workspace()
+                    r.plan.forward(r.image, r.out, r.ws, stream=s)
+                    ev = torch.cuda.Event()
+                    ev.record(s)
+                r.batch_size = 1
+                self.running.append(_Batch(ev, [r], slot, s, {r.rid: r}, plain=True))
+                self.batches += 1
+                continue
             reqs, pix = [], 0
-            while self.admitted and len(reqs) < self.max_batch and (not reqs or pix < self.max_batch_pixels):
+            while (self.admitted and len(reqs) < self.max_batch and pix < self.max_batch_pixels
+                   and self.admitted[0].image.numel() < self.plain_pixels):
                 r = self.admitted.popleft()
                 pix += r.image.numel()
                 reqs.append(r)
-            s = self.streams[slot]
             with torch.cuda.stream(s):
                 for r in reqs:
                     r.out = r.plan.new_output()
