@@ -43,11 +43,13 @@ struct BatchUnit {
   int32_t job;
   int32_t kind;
   int32_t index;  // fused / band item, first spine row, or first row job
-  int32_t tile;   // column tile (fused, band, spine) or row count (upper)
+  int32_t tile;   // first column tile (fused, band), column tile (spine) or row count (upper)
   int32_t need;   // units of this job that must be finished first
+  int32_t ntiles; // fused / band: column tiles handled by this unit
 };
 
 constexpr int kUpperRowsPerUnit = 8;
+constexpr int kTilesPerUnit = 4;
 
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
@@ -118,11 +120,14 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchJob* __restric
   __shared__ SpineTerm st[kSpineRows][kMaxSpineTerms];
   __shared__ SpineRow sr[kSpineRows];
   AccT* sm = reinterpret_cast<AccT*>(smem_raw);
+  int32_t next = 0;  // thread 0: the unit index taken for the following turn
+  if (threadIdx.x == 0) s_unit = atomicAdd(&counters[0], 1);
   for (;;) {
-    if (threadIdx.x == 0) s_unit = atomicAdd(&counters[0], 1);
     __syncthreads();
     const int32_t ui = s_unit;
     if (ui >= nunits) break;
+    // take the next unit now, so the atomic's latency hides behind this unit's work
+    if (threadIdx.x == 0) next = atomicAdd(&counters[0], 1);
     const BatchUnit U = units[ui];
     if (threadIdx.x == 0) {
       int32_t ok = 1;
@@ -150,11 +155,12 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchJob* __restric
         case UNIT_BAND: {
           const FusedItem it = (U.kind == UNIT_FUSED ? jb.fp.items : jb.band_items)[U.index];
           const QuadDesc& Q = jb.fp.quad[it.q];
-          if (U.tile < it.ntiles) {
+          for (int32_t tile = U.tile; tile < U.tile + U.ntiles && tile < it.ntiles; tile++) {
+            if (tile > U.tile) __syncthreads();  // the previous tile's shared reads are done
             if (it.kind != FUSED_GENERIC) {
-              fused_block<true, InT, AccT>(jb.fp, it, Q, U.tile, sm, sm + (size_t)64 * jb.fp.RS);
+              fused_block<true, InT, AccT>(jb.fp, it, Q, tile, sm, sm + (size_t)64 * jb.fp.RS);
             } else {
-              fused_generic<InT, AccT>(jb.fp, it, Q, U.tile, sm, sm + (size_t)jb.fp.Fm * jb.fp.RP);
+              fused_generic<InT, AccT>(jb.fp, it, Q, tile, sm, sm + (size_t)jb.fp.Fm * jb.fp.RP);
             }
           }
           break;
@@ -180,6 +186,7 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchJob* __restric
         __threadfence_system();
         asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(jb.flag), "r"(jb.gen) : "memory");
       }
+      s_unit = next;
     }
   }
 }
@@ -369,9 +376,9 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
   }
   // pass 2: units, phase by phase across all jobs
   std::vector<int32_t> done_before(njobs, 0);
-  auto push = [&](int32_t job, int32_t kind, int32_t index, int32_t tile, int32_t need) -> bool {
+  auto push = [&](int32_t job, int32_t kind, int32_t index, int32_t tile, int32_t need, int32_t ntiles = 1) -> bool {
     if (nunits >= q->max_units) return false;
-    q->h_units[nunits++] = fht::BatchUnit{job, kind, index, tile, need};
+    q->h_units[nunits++] = fht::BatchUnit{job, kind, index, tile, need, ntiles};
     return true;
   };
   int32_t max_phase = 0;
@@ -388,14 +395,16 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
       const int32_t n = need + (skip_dep ? 1 : 0);  // a dependency nothing satisfies
       int32_t count = 0;
       bool ok = true;
+      const int32_t tpu = fht::kTilesPerUnit;
       if (phase == 0) {
         for (size_t i = 0; i < P.fused.size() && ok; i++)
-          for (int32_t t = 0; t < P.fused[i].ntiles && ok; t++, count++) ok = push(j, fht::UNIT_FUSED, (int32_t)i, t, 0);
+          for (int32_t t = 0; t < P.fused[i].ntiles && ok; t += tpu, count++)
+            ok = push(j, fht::UNIT_FUSED, (int32_t)i, t, 0, tpu);
       } else if (P.bands) {
         if (phase == 1) {
           for (size_t i = 0; i < P.band_items.size() && ok; i++)
-            for (int32_t t = 0; t < P.band_items[i].ntiles && ok; t++, count++)
-              ok = push(j, fht::UNIT_BAND, (int32_t)i, t, n);
+            for (int32_t t = 0; t < P.band_items[i].ntiles && ok; t += tpu, count++)
+              ok = push(j, fht::UNIT_BAND, (int32_t)i, t, n, tpu);
         } else if (phase == 2 && !P.spine_rows.empty()) {
           int32_t maxW = 1;
           for (int k = 0; k < 4; k++)
