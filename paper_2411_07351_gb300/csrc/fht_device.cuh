@@ -537,11 +537,18 @@ __device__ __forceinline__ void spine_load(const SpineTerm* st, const QuadDesc& 
                                            int32_t u0, AccT (&v)[NT][QPT]) {
   const int32_t base_u = u0 + (int32_t)threadIdx.x;
   const int32_t live = Q.W - base_u;  // column q is inside the output row iff q BS < live
+  const bool full = u0 + BS * QPT <= Q.W;
 #pragma unroll
   for (int c = 0; c < NT; c++) {
     const int32_t off = st[c].off;
     const AccT* __restrict__ src = ws + st[c].row + (base_u + off);
-    if (Q.ext) {
+    // CTA-uniform test: the whole tile reads one in-bounds stretch of the part row
+    const bool clean = full && (Q.ext ? (u0 + off >= 0 && u0 + BS * QPT + off <= st[c].wpart)
+                                      : (u0 + BS * QPT + off <= Q.W));
+    if (clean) {
+#pragma unroll
+      for (int q = 0; q < QPT; q++) v[c][q] = ld_ws<kC>(src + q * BS);
+    } else if (Q.ext) {
       const int32_t lo = -(base_u + off), hi = st[c].wpart - (base_u + off);  // valid iff lo <= q BS < hi
 #pragma unroll
       for (int q = 0; q < QPT; q++)
