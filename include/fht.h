@@ -76,7 +76,9 @@ typedef struct {
   int32_t tile_cols;   /* column tile of the fused pass (multiple of 32) */
   int32_t threads;     /* threads per CTA of the fused pass (multiple of 32, <= 512) */
   int32_t with_adjoint;/* 1: build the adjoint tables now (otherwise on the first fht_adjoint) */
-  int32_t reserved[4];
+  int32_t rounding;    /* child slopes [t k_P]: 0 = exact, ties to even (default);
+                          1 = k_P = (m_P - 1)/(m - 1) in double, then rint(t k_P) (Algorithm 1 read literally) */
+  int32_t reserved[3];
 } fht_tuning_t;
 
 typedef struct {
@@ -214,6 +216,15 @@ fht_status fht_queue_poll(fht_queue_t q, uint64_t* done_tags, int32_t cap, int32
 fht_status fht_queue_status(fht_queue_t q, void* stream);
 fht_status fht_queue_reset_status(fht_queue_t q, void* stream);
 fht_status fht_queue_destroy(fht_queue_t q);
+
+/* The accuracy experiment of Sections 4-5: for every n in [n_lo, n_hi], the
+ * exact numerator of the maximum orthotropic error of the generating patterns
+ * of Algorithm 2 under `split`,
+ *   d_num[n - n_lo] = max over t, x in [0, n) of |x t - pat(n,t)(x) (n - 1)|,
+ * so that E(n) = d_num / (n - 1) (0 for n = 1).  d_num: device int64 array of
+ * n_hi - n_lo + 1 entries, overwritten.  Enqueued on `stream`.  Cost grows as
+ * n^2 log n per n (every pattern is generated). */
+fht_status fht_pattern_errors(int32_t n_lo, int32_t n_hi, fht_split split, int64_t* d_num, void* stream);
 
 /* Host-side verification of a plan: walks every table entry and checks that
  * each input, workspace, output and shared-memory index the kernels derive

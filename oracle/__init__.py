@@ -46,7 +46,7 @@ def build(force: bool = False) -> str:
     stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -72,6 +72,9 @@ def _load():
                          "orc_adjoint_f64", "orc_adjoint_brute_f64"):
                 getattr(lib, name).argtypes = [i32, i32, vp, u32, i32, i32, vp]
             lib.orc_brute_at_f64.argtypes = [i32, i32, vp, i32, i32, i64, vp, vp, vp, vp, vp]
+            lib.orc_set_rounding.argtypes = [i32]
+            lib.orc_child_slope.argtypes = [i32, i32, i32]
+            lib.orc_child_slope.restype = i32
             lib.orc_brady_yong_i64.argtypes = [i32, i32, vp, vp]
             lib.orc_brady_yong_i64.restype = ctypes.c_int
             _lib = lib
@@ -80,6 +83,21 @@ def _load():
 
 def _ptr(a: np.ndarray) -> int:
     return a.ctypes.data
+
+
+ROUND_EXACT, ROUND_FLOAT = 0, 1
+
+
+def set_rounding(rule: int):
+    """Child-slope rounding for every later call: ROUND_EXACT (ties to even on the
+    exact rational, the default) or ROUND_FLOAT (k = (n_P - 1)/(n - 1) in double,
+    then rint(t k))."""
+    _load().orc_set_rounding(rule)
+
+
+def child_slope(n: int, ni: int, t: int) -> int:
+    """[t (ni - 1)/(n - 1)] under the current rounding rule."""
+    return int(_load().orc_child_slope(n, ni, t))
 
 
 def split(n: int, rule: int = SPLIT_T) -> tuple[int, int]:

@@ -28,6 +28,7 @@
  *
  * All arithmetic is int64 (integer images) or double (float images).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -67,8 +68,22 @@ int64_t orc_round_half_even(int64_t a, int64_t d) {
   return q + (q & 1);
 }
 
+/* Rounding of the child slopes.  0 (default): [x] = nearest integer to the
+ * exact rational, ties to even.  1: Algorithm 1 read literally in floating
+ * point -- k_P = (n_P - 1)/(n - 1) as a double, then t k_P rounded to the
+ * nearest integer (ties to even, the default FP mode) with rint. */
+static int g_rounding = 0;
+void orc_set_rounding(int32_t rule) { g_rounding = rule; }
+
 /* The child slopes of Algorithm 1 / Algorithm 2: t_P = [t (n_P - 1) / (n - 1)]. */
 static void child_slopes(int32_t n, const int32_t np[2], int32_t t, int32_t tp[2]) {
+  if (g_rounding == 1) {
+    for (int i = 0; i < 2; i++) {
+      double k = (double)(np[i] - 1) / (double)(n - 1);
+      tp[i] = (int32_t)rint((double)t * k);
+    }
+    return;
+  }
   tp[0] = (int32_t)orc_round_half_even((int64_t)t * (np[0] - 1), n - 1);
   tp[1] = (int32_t)orc_round_half_even((int64_t)t * (np[1] - 1), n - 1);
 }
@@ -76,6 +91,13 @@ static void child_slopes(int32_t n, const int32_t np[2], int32_t t, int32_t tp[2
 static int32_t imod(int64_t a, int64_t m) {
   int64_t r = a % m;
   return (int32_t)(r < 0 ? r + m : r);
+}
+
+/* One child slope under the current rounding rule (for tests). */
+int32_t orc_child_slope(int32_t n, int32_t ni, int32_t t) {
+  int32_t np[2] = {ni, ni}, tp[2];
+  child_slopes(n, np, t, tp);
+  return tp[0];
 }
 
 /* ---------------------------------------------------------------------- */

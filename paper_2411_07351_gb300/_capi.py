@@ -22,7 +22,8 @@ FHT_SPLIT_T, FHT_SPLIT_S = 0, 1
 
 class fht_tuning_t(ctypes.Structure):
     _fields_ = [("fused_rows", ctypes.c_int32), ("tile_cols", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("with_adjoint", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("threads", ctypes.c_int32), ("with_adjoint", ctypes.c_int32), ("rounding", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class fht_plan_info_t(ctypes.Structure):
@@ -58,6 +59,7 @@ SIGNATURES = {
     "fht_forward_timed": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp), _i32]),
     "fht_forward_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "fht_plan_destroy": (ctypes.c_int, [_vp]),
+    "fht_pattern_errors": (ctypes.c_int, [_i32, _i32, ctypes.c_int, _vp, _vp]),
     "fht_queue_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i32, _i64]),
     "fht_queue_set_wait_limit": (ctypes.c_int, [_vp, _i64]),
     "fht_submit": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(fht_job), _vp]),

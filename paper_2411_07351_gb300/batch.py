@@ -11,6 +11,12 @@ from . import _capi as C
 from .fht import Plan, PlanCache
 
 
+# Column tile of plans made for batched launches: 64-column tiles keep the
+# persistent kernel at 3 CTAs per SM (<= 64 KB of shared memory per CTA) and
+# fit the small images batches are for.
+BATCH_TILE_COLS = 64
+
+
 class BatchQueue:
     """One fht_queue_t: device tables for up to max_jobs jobs / max_units units per submit."""
 
@@ -28,7 +34,8 @@ class BatchQueue:
         C.check(self._lib.fht_queue_set_wait_limit(self._q, int(seconds * 1e9)), "fht_queue_set_wait_limit")
 
     def plan_for(self, x: torch.Tensor, quads: int, boundary: str, split: str) -> Plan:
-        return self.plans.get(x.shape[0], x.shape[1], x.dtype, quads, boundary, split, self.device_index)
+        return self.plans.get(x.shape[0], x.shape[1], x.dtype, quads, boundary, split, self.device_index,
+                              tile_cols=BATCH_TILE_COLS)
 
     def submit(self, images, quads: int = C.FHT_QALL, boundary: str = "cyclic", split: str = "T",
                outs=None, workspaces=None, stream=None, flags=None, tags=None):

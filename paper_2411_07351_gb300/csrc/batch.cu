@@ -50,6 +50,7 @@ struct BatchUnit {
 
 constexpr int kUpperRowsPerUnit = 8;
 constexpr int kTilesPerUnit = 4;
+constexpr int kBatchThreads = 256;
 
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
@@ -104,13 +105,13 @@ __device__ void batch_spine(const BatchJob& jb, int32_t r0, int32_t tile, SpineT
     if (c < sr[r].term_count) st[r][c] = jb.spine_terms[sr[r].term_begin + c];
   }
   __syncthreads();
-  // 512 threads x 2 columns: the same 1024-column tile as the plain spine kernel
-  spine_rows_tile<true, 512, 2, AccT, false>(sr, st, nr, jb.fp.quad, ws, out, u0);
+  // 256 threads x 4 columns: the same 1024-column tile as the plain spine kernel
+  spine_rows_tile<true, kBatchThreads, 4, AccT, false>(sr, st, nr, jb.fp.quad, ws, out, u0);
 }
 
 // counters[0]: next unit; counters[1 + j]: finished units of job j.
 template <typename InT, typename AccT>
-__global__ void __launch_bounds__(512, 2) batch_kernel(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchJob* __restrict__ jobs,
                                                       const BatchUnit* __restrict__ units, int32_t nunits,
                                                       const int64_t* __restrict__ spine_nrows, int32_t* counters,
                                                       int32_t* status, int64_t wait_ns) {
@@ -262,11 +263,12 @@ cudaError_t launch_batch(fht_queue_s* q, int32_t nunits, size_t smem, cudaStream
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0, sms = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 512, smem)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, fht::kBatchThreads, smem)) != cudaSuccess)
+    return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, q->device)) != cudaSuccess) return e;
   const int grid = std::max(1, std::min<int>(nunits, std::max(1, per_sm) * sms));
-  kfn<<<grid, 512, smem, st>>>(q->d_jobs, q->d_units, nunits, q->d_spine_nrows, q->d_counters, q->d_status,
-                               q->wait_ns);
+  kfn<<<grid, fht::kBatchThreads, smem, st>>>(q->d_jobs, q->d_units, nunits, q->d_spine_nrows, q->d_counters,
+                                              q->d_status, q->wait_ns);
   return cudaGetLastError();
 }
 

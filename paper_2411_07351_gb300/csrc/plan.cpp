@@ -11,6 +11,7 @@
 #include "plan.hpp"
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <set>
 
@@ -38,9 +39,27 @@ int64_t round_half_even(int64_t a, int64_t d) {
   return q + (q & 1);
 }
 
+static thread_local int32_t g_rounding = 0;
+
+void set_rounding_rule(int32_t rule) { g_rounding = rule; }
+
+// Algorithm 1 writes k_P = (w_P - 1)/(w - 1), then [t k_P].  Rule 1 reads it
+// literally in floating point: k in double, then round-to-nearest-even of the
+// product; it differs from the exact rule only where t (m_i - 1)/(m - 1) is a
+// tie that the double product misses.
+static inline int32_t float_k_round(int32_t t, int32_t mi, int32_t m) {
+  const double k = (double)(mi - 1) / (double)(m - 1);
+  return (int32_t)rint((double)t * k);
+}
+
 void merge_entry(int32_t m, int32_t m0, int32_t m1, int32_t t, int32_t& t1, int32_t& t2, int32_t& s) {
-  t1 = (int32_t)round_half_even((int64_t)t * (m0 - 1), m - 1);
-  t2 = (int32_t)round_half_even((int64_t)t * (m1 - 1), m - 1);
+  if (g_rounding == 1) {
+    t1 = float_k_round(t, m0, m);
+    t2 = float_k_round(t, m1, m);
+  } else {
+    t1 = (int32_t)round_half_even((int64_t)t * (m0 - 1), m - 1);
+    t2 = (int32_t)round_half_even((int64_t)t * (m1 - 1), m - 1);
+  }
   s = t - t2;
 }
 
@@ -53,6 +72,13 @@ static inline int32_t round_qr(int64_t q, int64_t r, int64_t d) {
 
 void merge_table(int32_t m, int32_t m0, int32_t m1, std::vector<MergeRow>& out) {
   out.resize(m);
+  if (g_rounding == 1) {
+    for (int32_t t = 0; t < m; t++) {
+      const int32_t t2 = float_k_round(t, m1, m);
+      out[t] = MergeRow{float_k_round(t, m0, m), t2, t - t2};
+    }
+    return;
+  }
   const int64_t d = m - 1;
   int64_t q0 = 0, r0 = 0, q1 = 0, r1 = 0;  // t (m0 - 1) = q0 d + r0, t (m1 - 1) = q1 d + r1
   for (int32_t t = 0; t < m; t++) {
@@ -174,6 +200,8 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
   if (cfg.F < 1 || cfg.F > 64 || (cfg.F & (cfg.F - 1))) return "fused_rows must be a power of two in [1, 64]";
   if (cfg.TW < 32 || cfg.TW % 32 || cfg.TW > 1024) return "tile_cols must be a multiple of 32 in [32, 1024]";
   if (cfg.threads < 32 || cfg.threads % 32 || cfg.threads > 1024) return "threads must be a multiple of 32";
+  if (cfg.rounding != 0 && cfg.rounding != 1) return "unknown rounding rule";
+  set_rounding_rule(cfg.rounding);
   P = HostPlan();
   P.cfg = cfg;
   P.in_size = dtype_in_size(cfg.dtype);
@@ -509,10 +537,11 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
       if (nd.m > 1) P.adds += (int64_t)nd.m * (cfg.ext ? Q.L + nd.m - 1 : Q.W);
     P.ideal_bytes += (int64_t)Q.n * Q.L * P.in_size + qsize * acc;
   }
-  // tiles: fast-path items use tile_cols; generic items use half of it when
-  // both kinds share the launch, so that their shared windows stay smaller
+  // tiles: fast-path items use tile_cols; generic items (two ping-pong
+  // buffers of up to 63 rows) use half of it, so their shared windows stay
+  // no larger than the fast path's
   for (const FusedItem& fi : P.fused) P.n_by64 += fi.kind == FUSED_BY64;
-  P.generic_tw = (P.n_by64 > 0) ? std::max(32, cfg.TW / 64 * 32) : cfg.TW;
+  P.generic_tw = std::max(32, cfg.TW / 64 * 32);
   for (FusedItem& fi : P.fused) {
     fi.tw = fi.kind == FUSED_BY64 ? cfg.TW : P.generic_tw;
     fi.ntiles = (fi.wn + fi.tw - 1) / fi.tw;

@@ -56,7 +56,12 @@ struct PlanConfig {
   int32_t TW = 128;        // fused column tile
   int32_t threads = 256;   // fused CTA size
   bool with_adjoint = false;  // also build the adjoint tables
+  int32_t rounding = 0;       // 0: exact half-to-even; 1: rint(t * k) with k = (m_i - 1)/(m - 1) in fp64
 };
+
+// The rounding rule for merge tables, set from PlanConfig::rounding while a
+// plan is built (plan building is single-threaded per call).
+void set_rounding_rule(int32_t rule);
 
 struct HostPlan {
   PlanConfig cfg;

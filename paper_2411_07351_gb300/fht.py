@@ -38,7 +38,7 @@ class Plan:
     def __init__(self, h: int, w: int, dtype=torch.float32, quads: int = C.FHT_QALL,
                  boundary: str = "cyclic", split: str = "T", device: int | None = None,
                  fused_rows: int = 0, tile_cols: int = 0, threads: int = 0, with_adjoint: bool = False,
-                 tuning: str | None = None):
+                 tuning: str | None = None, rounding: str = "exact"):
         self._lib = C.load()
         if tuning == "auto" and not (tile_cols or threads):
             from .tune import lookup
@@ -57,7 +57,9 @@ class Plan:
         if device is None:
             device = torch.cuda.current_device()
         self.device_index = int(device)
-        tun = C.fht_tuning_t(fused_rows, tile_cols, threads, int(with_adjoint))
+        if rounding not in ("exact", "float"):
+            raise ValueError("rounding is 'exact' or 'float'")
+        tun = C.fht_tuning_t(fused_rows, tile_cols, threads, int(with_adjoint), 1 if rounding == "float" else 0)
         handle = ctypes.c_void_p()
         args = (ctypes.byref(handle), self.h, self.w, self.fht_dtype, self.quads, BOUNDARY[boundary], SPLIT[split],
                 self.device_index, ctypes.byref(tun))
@@ -152,14 +154,14 @@ class PlanCache:
         self._d: OrderedDict = OrderedDict()
         self._lock = threading.Lock()
 
-    def get(self, h, w, dtype, quads, boundary, split, device) -> Plan:
-        key = (h, w, dtype, quads, boundary, split, device)
+    def get(self, h, w, dtype, quads, boundary, split, device, tile_cols: int = 0) -> Plan:
+        key = (h, w, dtype, quads, boundary, split, device, tile_cols)
         with self._lock:
             p = self._d.get(key)
             if p is not None:
                 self._d.move_to_end(key)
                 return p
-        p = Plan(h, w, dtype, quads, boundary, split, device)
+        p = Plan(h, w, dtype, quads, boundary, split, device, tile_cols=tile_cols)
         with self._lock:
             self._d[key] = p
             while len(self._d) > self.capacity:

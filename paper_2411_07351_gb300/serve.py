@@ -26,7 +26,7 @@ from dataclasses import dataclass, field
 import torch
 
 from . import _capi as C
-from .batch import BatchQueue
+from .batch import BATCH_TILE_COLS, BatchQueue
 from .fht import PlanCache
 
 
@@ -49,8 +49,10 @@ class PlanBuilder:
     future per distinct shape, so that the serving thread never waits for a
     plan it does not need yet."""
 
-    def __init__(self, device: int, quads: int, boundary: str, split: str, workers: int = 8):
+    def __init__(self, device: int, quads: int, boundary: str, split: str, workers: int = 8,
+                 batch_below: int = 0):
         self.device, self.quads, self.boundary, self.split = device, quads, boundary, split
+        self.batch_below = batch_below
         self.cache = PlanCache(capacity=8192)
         self.pool = cf.ThreadPoolExecutor(max_workers=workers)
         self.futures: dict = {}
@@ -58,7 +60,9 @@ class PlanBuilder:
 
     def _build(self, h, w, dtype):
         torch.cuda.set_device(self.device)
-        return self.cache.get(h, w, dtype, self.quads, self.boundary, self.split, self.device)
+        # requests that will be batched get the batch tile width
+        tc = BATCH_TILE_COLS if h * w < self.batch_below else 0
+        return self.cache.get(h, w, dtype, self.quads, self.boundary, self.split, self.device, tile_cols=tc)
 
     def request(self, req: "Request"):
         k = (req.image.shape[0], req.image.shape[1], req.image.dtype)
@@ -98,7 +102,7 @@ class Server:
         self.budget = budget_bytes
         self.quads, self.boundary, self.split = quads, boundary, split
         self.max_batch = max_batch
-        self.builder = PlanBuilder(device, quads, boundary, split)
+        self.builder = PlanBuilder(device, quads, boundary, split, batch_below=plain_pixels)
         self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
         self.queues = [BatchQueue(device=device, max_jobs=max_batch, max_units=1 << 22) for _ in range(streams)]
         self.free_slots = collections.deque(range(streams))

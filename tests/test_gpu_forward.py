@@ -172,3 +172,19 @@ def test_repeat_deterministic(F):
     a = _run(F, img, 15, "extended")
     b = _run(F, img, 15, "extended")
     assert np.array_equal(a, b)
+
+
+def test_float_k_rounding(F, orc):
+    """Plans with rounding='float' (Algorithm 1 read in floating point) match the
+    oracle under the same rule, bit-exactly, at sizes where the rules differ."""
+    orc.set_rounding(orc.ROUND_FLOAT)
+    try:
+        for h, w in [(23, 30), (45, 17), (181, 64), (725, 40)]:
+            img = inputs.uniform_u8(h * 3 + w, h, w)
+            x = torch.from_numpy(img).cuda()
+            p = F.Plan(h, w, torch.uint8, 15, "extended", rounding="float")
+            p.check()
+            got = p.forward(x).cpu().numpy().astype(np.int64)
+            assert np.array_equal(got, orc.fht(img.astype(np.int64), 15, orc.EXTENDED))
+    finally:
+        orc.set_rounding(orc.ROUND_EXACT)
