@@ -477,7 +477,11 @@ __device__ __forceinline__ void store_row(AccT* dst, const RowJob& J, bool fin, 
 // part reads hit L1; consecutive CTAs share rows through L2.
 constexpr int kMaxSpineTerms = 16;
 constexpr int kSpineRows = 16;
-constexpr int kSpineTile = 1024;
+constexpr int kSpineTile = 1024;  // batched kernel: 256 threads x 4 columns
+// plain spine kernel: 256 threads x kSpineQPT columns per row tile
+constexpr int kSpineQPT = 8;
+constexpr bool kSpinePipe = false;
+constexpr int kSpineTilePlain = 256 * kSpineQPT;
 
 // One output row x one column tile of BS * QPT columns: every thread owns QPT
 // columns spaced BS apart.
@@ -625,14 +629,22 @@ __device__ __forceinline__ void spine_rows_tile(const SpineRow* sr, SpineTerm (*
     }
   }
   }
+  // at most 64 loaded values live per thread: rows with more than 64 / QPT
+  // terms sweep the tile in two halves
+  constexpr int QH = QPT > 1 ? QPT / 2 : 1;
   for (int32_t r = 0; r < nr; r++) {
     const QuadDesc& Q = quads[sr[r].q];
     if (u0 >= Q.W) continue;
     AccT* dst = out + sr[r].dst;
     switch (sr[r].term_count) {
-#define FHT_SPINE_CASE(N)                                        \
-  case N:                                                        \
-    spine_tile<kC, N, BS, QPT, AccT>(st[r], Q, ws, dst, u0);     \
+#define FHT_SPINE_CASE(N)                                                   \
+  case N:                                                                   \
+    if constexpr (N * QPT <= 64) {                                          \
+      spine_tile<kC, N, BS, QPT, AccT>(st[r], Q, ws, dst, u0);              \
+    } else {                                                                \
+      spine_tile<kC, N, BS, QH, AccT>(st[r], Q, ws, dst, u0);               \
+      if (u0 + BS * QH < Q.W) spine_tile<kC, N, BS, QH, AccT>(st[r], Q, ws, dst, u0 + BS * QH); \
+    }                                                                       \
     break;
       FHT_SPINE_CASE(1) FHT_SPINE_CASE(2) FHT_SPINE_CASE(3) FHT_SPINE_CASE(4) FHT_SPINE_CASE(5) FHT_SPINE_CASE(6)
       FHT_SPINE_CASE(7) FHT_SPINE_CASE(8) FHT_SPINE_CASE(9) FHT_SPINE_CASE(10) FHT_SPINE_CASE(11)

@@ -77,13 +77,13 @@ __global__ void __launch_bounds__(256) upper_kernel(const RowJob* __restrict__ r
 }
 
 template <typename AccT>
-__global__ void __launch_bounds__(256) spine_kernel(const SpineRow* __restrict__ rows, int64_t nrows,
+__global__ void __launch_bounds__(256, 2) spine_kernel(const SpineRow* __restrict__ rows, int64_t nrows,
                                                    const SpineTerm* __restrict__ terms, const AccT* __restrict__ ws,
                                                    AccT* __restrict__ out, QuadDescs quads) {
   __shared__ SpineTerm st[kSpineRows][kMaxSpineTerms];
   __shared__ SpineRow sr[kSpineRows];
   const int64_t r0 = (int64_t)blockIdx.x * kSpineRows;
-  const int32_t u0 = blockIdx.y * kSpineTile;
+  const int32_t u0 = blockIdx.y * kSpineTilePlain;
   const int32_t nr = (int32_t)(nrows - r0 < kSpineRows ? nrows - r0 : kSpineRows);
   if (threadIdx.x < nr) sr[threadIdx.x] = rows[r0 + threadIdx.x];
   __syncthreads();
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) spine_kernel(const SpineRow* __restrict__
     if (c < sr[r].term_count) st[r][c] = terms[sr[r].term_begin + c];
   }
   __syncthreads();
-  spine_rows_tile<false, 256, 4, AccT>(sr, st, nr, quads.q, ws, out, u0);
+  spine_rows_tile<false, 256, kSpineQPT, AccT, kSpinePipe>(sr, st, nr, quads.q, ws, out, u0);
 }
 
 // ------------------------------------------------------------------------
@@ -183,7 +183,8 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
       int32_t maxW = 1;
       for (int q = 0; q < 4; q++)
         if (P.cfg.quads & (1u << q)) maxW = std::max(maxW, P.quad[q].W);
-      dim3 sgrid((unsigned)((n + kSpineRows - 1) / kSpineRows), (unsigned)((maxW + kSpineTile - 1) / kSpineTile));
+      dim3 sgrid((unsigned)((n + kSpineRows - 1) / kSpineRows),
+                 (unsigned)((maxW + kSpineTilePlain - 1) / kSpineTilePlain));
       mark(0);
       spine_kernel<AccT><<<sgrid, 256, 0, st>>>(D.spine_rows, n, D.spine_terms, wsa, static_cast<AccT*>(out), qd);
       mark(1);
