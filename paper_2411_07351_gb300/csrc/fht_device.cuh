@@ -479,8 +479,8 @@ constexpr int kMaxSpineTerms = 16;
 constexpr int kSpineRows = 16;
 constexpr int kSpineTile = 1024;  // batched kernel: 256 threads x 4 columns
 // plain spine kernel: 256 threads x kSpineQPT columns per row tile
-constexpr int kSpineQPT = 8;
-constexpr bool kSpinePipe = false;
+constexpr int kSpineQPT = 4;
+constexpr bool kSpinePipe = true;
 constexpr int kSpineTilePlain = 256 * kSpineQPT;
 
 // One output row x one column tile of BS * QPT columns: every thread owns QPT

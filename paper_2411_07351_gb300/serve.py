@@ -5,9 +5,9 @@ an LRU cache and buffers in PyTorch's caching allocator, admits a request
 only while the device-memory budget (output + workspace of every admitted,
 unfinished request) has room, and on every turn of its loop submits the
 admitted small requests that are not yet running as ONE persistent batched
-launch (fht_submit) on a stream whose previous launch has finished; a large
-request (at least ``plain_pixels``) fills the GPU by itself and runs the
-per-image kernels on a stream of its own.  Batches on
+launch (fht_submit) on the least busy of its streams (each stream holds up to
+``max_inflight`` launches); a large request (at least ``plain_pixels``)
+fills the GPU by itself and runs the per-image kernels instead.  Batches on
 different streams overlap on the device; a request that arrives while others
 run joins the next batch as soon as memory and a stream are free.  Latency is
 arrival -> the host seeing the batch's completion event.
@@ -87,14 +87,13 @@ class _Batch:
     reqs: list
     slot: int
     stream: torch.cuda.Stream = field(default=None)
-    by_rid: dict = field(default_factory=dict)
     plain: bool = False
 
 
 class Server:
     def __init__(self, device: int = 0, budget_bytes: int = 16 << 30, streams: int = 4, quads: int = C.FHT_QALL,
                  boundary: str = "cyclic", split: str = "T", max_batch: int = 1024, keep_outputs: bool = True,
-                 max_batch_pixels: int = 16 << 20, plain_pixels: int = 1 << 20):
+                 max_batch_pixels: int = 16 << 20, plain_pixels: int = 1 << 20, max_inflight: int = 4):
         self.device = device
         self.max_batch_pixels = max_batch_pixels
         self.plain_pixels = plain_pixels
@@ -105,7 +104,9 @@ class Server:
         self.builder = PlanBuilder(device, quads, boundary, split, batch_below=plain_pixels)
         self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
         self.queues = [BatchQueue(device=device, max_jobs=max_batch, max_units=1 << 22) for _ in range(streams)]
-        self.free_slots = collections.deque(range(streams))
+        self.inflight = [0] * streams        # launches in flight per stream
+        self.max_inflight = max_inflight
+        self.by_rid: dict = {}               # running batched requests by id
         self.waiting: collections.deque = collections.deque()   # arrived, not admitted
         self.admitted: collections.deque = collections.deque()  # admitted, not launched
         self.running: list[_Batch] = []
@@ -134,44 +135,50 @@ class Server:
             self.max_used = max(self.max_used, self.used)
             self.admitted.append(req)
 
+    def _finish(self, r, t):
+        r.done = t
+        self.used -= r.nbytes
+        if not self.keep_outputs:
+            r.out = None
+        self.finished.append(r)
+
     def _retire(self, now_fn):
+        # batched requests finish one by one (per-job completion flags)
+        for q in self.queues:
+            for rid in q.poll(cap=4096):
+                r = self.by_rid.pop(rid, None)
+                if r is not None:
+                    self._finish(r, now_fn())
         still = []
         for b in self.running:
             if b.plain:
                 if b.event.query():
                     r = b.reqs[0]
-                    r.done = now_fn()
-                    self.used -= r.nbytes
+                    self._finish(r, now_fn())
                     r.ws = None
-                    if not self.keep_outputs:
-                        r.out = None
-                    self.finished.append(r)
-                    self.free_slots.append(b.slot)
+                    self.inflight[b.slot] -= 1
                 else:
                     still.append(b)
                 continue
-            # requests finish one by one (per-job completion flags) ...
-            for rid in self.queues[b.slot].poll(cap=len(b.reqs)):
-                r = b.by_rid.pop(rid, None)
-                if r is None:
-                    continue
-                r.done = now_fn()
-                self.used -= r.nbytes
-                if not self.keep_outputs:
-                    r.out = None
-                self.finished.append(r)
-            # ... and the stream slot frees up when the whole launch has ended
-            if not b.by_rid and b.event.query():
+            # a launch's workspaces are released, and its stream slot counted
+            # free, once every request is done and the launch has ended
+            if all(r.done is not None for r in b.reqs) and b.event.query():
                 for r in b.reqs:
-                    r.ws = None  # workspaces go back once the launch has ended
-                self.free_slots.append(b.slot)
+                    r.ws = None
+                self.inflight[b.slot] -= 1
             else:
                 still.append(b)
         self.running = still
 
+    def _pick_stream(self):
+        k = min(range(len(self.streams)), key=lambda i: self.inflight[i])
+        return k if self.inflight[k] < self.max_inflight else None
+
     def _launch(self):
-        while self.admitted and self.free_slots:
-            slot = self.free_slots.popleft()
+        while self.admitted:
+            slot = self._pick_stream()
+            if slot is None:
+                return
             s = self.streams[slot]
             head = self.admitted[0]
             if head.image.numel() >= self.plain_pixels:
@@ -185,7 +192,8 @@ class Server:
                     ev = torch.cuda.Event()
                     ev.record(s)
                 r.batch_size = 1
-                self.running.append(_Batch(ev, [r], slot, s, {r.rid: r}, plain=True))
+                self.running.append(_Batch(ev, [r], slot, s, plain=True))
+                self.inflight[slot] += 1
                 self.batches += 1
                 continue
             reqs, pix = [], 0
@@ -199,12 +207,14 @@ class Server:
                     r.out = r.plan.new_output()
                     r.ws = r.plan.new_workspace()
                     r.batch_size = len(reqs)
+                    self.by_rid[r.rid] = r
                 self.queues[slot].submit([r.image for r in reqs], self.quads, self.boundary, self.split,
                                          outs=[r.out for r in reqs], workspaces=[r.ws for r in reqs], stream=s,
                                          tags=[r.rid for r in reqs])
                 ev = torch.cuda.Event()
                 ev.record(s)
-            self.running.append(_Batch(ev, reqs, slot, s, {r.rid: r for r in reqs}))
+            self.running.append(_Batch(ev, reqs, slot, s))
+            self.inflight[slot] += 1
             self.batches += 1
 
     def step(self, now_fn):

@@ -61,6 +61,7 @@ def test_admission_budget_smaller_than_a_request(F):
     done, _ = run_stream(srv, reqs)
     assert len(done) == 20
     assert max(r.batch_size for r in done) == 1  # admitted one at a time
+    assert srv.max_used <= max(r.nbytes for r in done)
     for r in done:
         assert torch.equal(r.out, r.plan.forward(r.image))
     srv.close()
