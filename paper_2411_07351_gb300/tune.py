@@ -55,9 +55,41 @@ def save_cache(d: dict):
     os.replace(tmp, path)
 
 
+PACKAGED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_table.json")
+
+
 def lookup(h, w, dtype, quads, boundary, split):
+    """The user's cache first, then the table shipped with the package (measured
+    on GB300 by ``python -m paper_2411_07351_gb300.tune``)."""
+    k = key(h, w, dtype, quads, boundary, split)
     with _lock:
-        return load_cache().get(key(h, w, dtype, quads, boundary, split))
+        hit = load_cache().get(k)
+    if hit is None and os.path.exists(PACKAGED):
+        with open(PACKAGED) as f:
+            hit = json.load(f).get(k)
+    return hit
+
+
+def sweep(sizes=(64, 128, 256, 512, 1024, 2048, 4096), dtypes=(torch.uint8, torch.float32),
+          boundaries=("cyclic", "extended"), quads: int = C.FHT_QALL, reps: int = 8, out: str | None = None) -> dict:
+    """Tune square sizes of a grid and write the winners to `out` (default: the packaged table)."""
+    table = {}
+    for n in sizes:
+        for dt in dtypes:
+            for b in boundaries:
+                e = tune(n, n, dt, quads, b, "T", reps=reps, save=False)
+                table[key(n, n, dt, quads, b, "T")] = e
+                print(key(n, n, dt, quads, b, "T"), e["tile_cols"], e["threads"], f"{e['ms']:.4f} ms", flush=True)
+    path = out or PACKAGED
+    with open(path, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    return table
+
+
+if __name__ == "__main__":
+    import sys
+
+    sweep(out=sys.argv[1] if len(sys.argv) > 1 else None)
 
 
 def _time_plan(plan, x, reps: int) -> float:
