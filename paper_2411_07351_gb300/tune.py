@@ -86,11 +86,6 @@ def sweep(sizes=(64, 128, 256, 512, 1024, 2048, 4096), dtypes=(torch.uint8, torc
     return table
 
 
-if __name__ == "__main__":
-    import sys
-
-    sweep(out=sys.argv[1] if len(sys.argv) > 1 else None)
-
 
 def _time_plan(plan, x, reps: int) -> float:
     out, ws = plan.new_output(), plan.new_workspace()
@@ -138,3 +133,9 @@ def tune(h: int, w: int, dtype=torch.float32, quads: int = C.FHT_QALL, boundary:
             d[key(h, w, dtype, quads, boundary, split)] = entry
             save_cache(d)
     return entry
+
+
+if __name__ == "__main__":
+    import sys
+
+    sweep(out=sys.argv[1] if len(sys.argv) > 1 else None)
