@@ -78,7 +78,10 @@ typedef struct {
   int32_t with_adjoint;/* 1: build the adjoint tables now (otherwise on the first fht_adjoint) */
   int32_t rounding;    /* child slopes [t k_P]: 0 = exact, ties to even (default);
                           1 = k_P = (m_P - 1)/(m - 1) in double, then rint(t k_P) (Algorithm 1 read literally) */
-  int32_t reserved[3];
+  int32_t spine_chunk; /* Split_T roots taller than 64 rows: spine nodes summed per spine launch (default 3);
+                          the lower chunks' top nodes are summed first and become single parts of the
+                          chunk above.  A value >= the spine length gives one spine launch. */
+  int32_t reserved[2];
 } fht_tuning_t;
 
 typedef struct {

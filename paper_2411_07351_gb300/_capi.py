@@ -23,7 +23,7 @@ FHT_SPLIT_T, FHT_SPLIT_S = 0, 1
 class fht_tuning_t(ctypes.Structure):
     _fields_ = [("fused_rows", ctypes.c_int32), ("tile_cols", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("with_adjoint", ctypes.c_int32), ("rounding", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("spine_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class fht_plan_info_t(ctypes.Structure):

@@ -45,7 +45,7 @@ struct BatchUnit {
   int32_t index;  // fused / band item, first spine row, or first row job
   int32_t tile;   // first column tile (fused, band), column tile (spine) or row count (upper)
   int32_t need;   // units of this job that must be finished first
-  int32_t ntiles; // fused / band: column tiles handled by this unit
+  int32_t ntiles; // fused / band: column tiles handled by this unit; spine: rows
 };
 
 constexpr int kUpperRowsPerUnit = 8;
@@ -92,12 +92,11 @@ __device__ void batch_upper_rows(const RowJob* __restrict__ rows, int32_t first,
 }
 
 template <typename AccT>
-__device__ void batch_spine(const BatchJob& jb, int32_t r0, int32_t tile, SpineTerm (*st)[kMaxSpineTerms],
-                            SpineRow* sr, int64_t nrows) {
-  const AccT* ws = static_cast<const AccT*>(jb.fp.ws);
+__device__ void batch_spine(const BatchJob& jb, int32_t r0, int32_t nr, int32_t tile,
+                            SpineTerm (*st)[kMaxSpineTerms], SpineRow* sr) {
+  AccT* ws = static_cast<AccT*>(jb.fp.ws);
   AccT* out = static_cast<AccT*>(jb.fp.out);
   const int32_t u0 = tile * kSpineTile;
-  const int32_t nr = (int32_t)(nrows - r0 < kSpineRows ? nrows - r0 : kSpineRows);
   if ((int32_t)threadIdx.x < nr) sr[threadIdx.x] = jb.spine_rows[r0 + threadIdx.x];
   __syncthreads();
   for (int32_t idx = threadIdx.x; idx < nr * kMaxSpineTerms; idx += blockDim.x) {
@@ -106,14 +105,14 @@ __device__ void batch_spine(const BatchJob& jb, int32_t r0, int32_t tile, SpineT
   }
   __syncthreads();
   // 256 threads x 4 columns: the same 1024-column tile as the plain spine kernel
-  spine_rows_tile<true, kBatchThreads, 4, AccT, false>(sr, st, nr, jb.fp.quad, ws, out, u0);
+  spine_rows_tile<true, kBatchThreads, 4, AccT, false>(sr, st, nr, jb.fp.quad, ws, out, ws, u0);
 }
 
 // counters[0]: next unit; counters[1 + j]: finished units of job j.
 template <typename InT, typename AccT>
 __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchJob* __restrict__ jobs,
                                                       const BatchUnit* __restrict__ units, int32_t nunits,
-                                                      const int64_t* __restrict__ spine_nrows, int32_t* counters,
+                                                      int32_t* counters,
                                                       int32_t* status, int64_t wait_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int32_t s_unit;
@@ -167,7 +166,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchJob*
           break;
         }
         case UNIT_SPINE:
-          batch_spine<AccT>(jb, U.index, U.tile, st, sr, spine_nrows[U.job]);
+          batch_spine<AccT>(jb, U.index, U.ntiles, U.tile, st, sr);
           break;
         default:
           batch_upper_rows<AccT>(jb.rows, U.index, U.tile, static_cast<AccT*>(jb.fp.ws),
@@ -207,12 +206,10 @@ struct fht_queue_s {
   int64_t wait_ns = 2000000000;  // 2 s
   fht::BatchJob* d_jobs = nullptr;
   fht::BatchUnit* d_units = nullptr;
-  int64_t* d_spine_nrows = nullptr;
   int32_t* d_counters = nullptr;  // [1 + max_jobs]
   int32_t* d_status = nullptr;
   fht::BatchJob* h_jobs = nullptr;  // pinned staging
   fht::BatchUnit* h_units = nullptr;
-  int64_t* h_spine_nrows = nullptr;
   cudaEvent_t staged = nullptr;     // staging buffers free again after this event
   bool staged_pending = false;
   int32_t last_units = 0;
@@ -246,12 +243,10 @@ struct QueueDeviceGuard {
 void queue_free(fht_queue_s* q) {
   if (q->d_jobs) cudaFree(q->d_jobs);
   if (q->d_units) cudaFree(q->d_units);
-  if (q->d_spine_nrows) cudaFree(q->d_spine_nrows);
   if (q->d_counters) cudaFree(q->d_counters);
   if (q->d_status) cudaFree(q->d_status);
   if (q->h_jobs) cudaFreeHost(q->h_jobs);
   if (q->h_units) cudaFreeHost(q->h_units);
-  if (q->h_spine_nrows) cudaFreeHost(q->h_spine_nrows);
   if (q->staged) cudaEventDestroy(q->staged);
   if (q->done_evt) cudaEventDestroy(q->done_evt);
   if (q->h_flags) cudaFreeHost(q->h_flags);
@@ -267,8 +262,8 @@ cudaError_t launch_batch(fht_queue_s* q, int32_t nunits, size_t smem, cudaStream
     return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, q->device)) != cudaSuccess) return e;
   const int grid = std::max(1, std::min<int>(nunits, std::max(1, per_sm) * sms));
-  kfn<<<grid, fht::kBatchThreads, smem, st>>>(q->d_jobs, q->d_units, nunits, q->d_spine_nrows, q->d_counters,
-                                              q->d_status, q->wait_ns);
+  kfn<<<grid, fht::kBatchThreads, smem, st>>>(q->d_jobs, q->d_units, nunits, q->d_counters, q->d_status,
+                                              q->wait_ns);
   return cudaGetLastError();
 }
 
@@ -294,12 +289,10 @@ fht_status fht_queue_create(fht_queue_t* out, int device, int32_t max_jobs, int6
   cudaError_t e;
   if ((e = cudaMalloc(&q->d_jobs, sizeof(fht::BatchJob) * max_jobs)) != cudaSuccess ||
       (e = cudaMalloc(&q->d_units, sizeof(fht::BatchUnit) * max_units)) != cudaSuccess ||
-      (e = cudaMalloc(&q->d_spine_nrows, sizeof(int64_t) * max_jobs)) != cudaSuccess ||
       (e = cudaMalloc(&q->d_counters, sizeof(int32_t) * (1 + (size_t)max_jobs))) != cudaSuccess ||
       (e = cudaMalloc(&q->d_status, 256)) != cudaSuccess ||
       (e = cudaMallocHost(&q->h_jobs, sizeof(fht::BatchJob) * max_jobs)) != cudaSuccess ||
       (e = cudaMallocHost(&q->h_units, sizeof(fht::BatchUnit) * max_units)) != cudaSuccess ||
-      (e = cudaMallocHost(&q->h_spine_nrows, sizeof(int64_t) * max_jobs)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&q->staged, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&q->done_evt, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaMemset(q->d_status, 0, 256)) != cudaSuccess ||
@@ -373,7 +366,6 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
     B.spine_rows = D->spine_rows;
     B.spine_terms = D->spine_terms;
     B.rows = D->rows;
-    q->h_spine_nrows[j] = (int64_t)P.spine_rows.size();
     smem = std::max(smem, D->geo.smem);
   }
   // pass 2: units, phase by phase across all jobs
@@ -386,7 +378,9 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
   int32_t max_phase = 0;
   for (int32_t j = 0; j < njobs; j++) {
     const fht::HostPlan& P = *fht_capi_device_plan(jobs[j].plan)->host;
-    max_phase = std::max<int32_t>(max_phase, P.bands ? 2 : (int32_t)P.pass_begin.size() - 1);
+    // bands: fused, band, then one phase per spine chunk (bottom-up)
+    max_phase = std::max<int32_t>(max_phase, P.bands ? 1 + (int32_t)P.spine_pass_bytes.size()
+                                                     : (int32_t)P.pass_begin.size() - 1);
   }
   std::vector<int32_t> phase_units(njobs, 0);
   for (int32_t phase = 0; phase <= max_phase; phase++) {
@@ -407,14 +401,15 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
           for (size_t i = 0; i < P.band_items.size() && ok; i++)
             for (int32_t t = 0; t < P.band_items[i].ntiles && ok; t += tpu, count++)
               ok = push(j, fht::UNIT_BAND, (int32_t)i, t, n, tpu);
-        } else if (phase == 2 && !P.spine_rows.empty()) {
+        } else if (phase >= 2 && phase - 2 < (int32_t)P.spine_pass_bytes.size()) {
           int32_t maxW = 1;
           for (int k = 0; k < 4; k++)
             if (P.cfg.quads & (1u << k)) maxW = std::max(maxW, P.quad[k].W);
           const int32_t tiles = (maxW + fht::kSpineTile - 1) / fht::kSpineTile;
+          const int64_t b = P.spine_pass_begin[phase - 2], e = P.spine_pass_begin[phase - 1];
           for (int32_t t = 0; t < tiles && ok; t++)
-            for (size_t r = 0; r < P.spine_rows.size() && ok; r += fht::kSpineRows, count++)
-              ok = push(j, fht::UNIT_SPINE, (int32_t)r, t, n);
+            for (int64_t r = b; r < e && ok; r += fht::kSpineRows, count++)
+              ok = push(j, fht::UNIT_SPINE, (int32_t)r, t, n, (int32_t)std::min<int64_t>(fht::kSpineRows, e - r));
         }
       } else if (phase < (int32_t)P.pass_begin.size()) {
         const int64_t b = P.pass_begin[phase - 1], e = P.pass_begin[phase];
@@ -437,8 +432,6 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
           cudaSuccess ||
       (e = cudaMemcpyAsync(q->d_units, q->h_units, sizeof(fht::BatchUnit) * nunits, cudaMemcpyHostToDevice, st)) !=
           cudaSuccess ||
-      (e = cudaMemcpyAsync(q->d_spine_nrows, q->h_spine_nrows, sizeof(int64_t) * njobs, cudaMemcpyHostToDevice,
-                           st)) != cudaSuccess ||
       (e = cudaMemsetAsync(q->d_counters, 0, sizeof(int32_t) * (1 + (size_t)njobs), st)) != cudaSuccess ||
       (!capturing && (e = cudaEventRecord(q->staged, st)) != cudaSuccess))
     return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_submit: ") + cudaGetErrorString(e));

@@ -141,6 +141,8 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
     if (tuning->threads) cfg.threads = tuning->threads;
     cfg.with_adjoint = tuning->with_adjoint != 0;
     cfg.rounding = tuning->rounding;
+    if (tuning->spine_chunk) cfg.spine_chunk = tuning->spine_chunk;
+    if (cfg.spine_chunk < 1) return fail(FHT_ERR_INVALID, "fht_plan: spine_chunk must be >= 1");
     if (cfg.threads > 512) return fail(FHT_ERR_INVALID, "fht_plan: threads must be <= 512");
   }
   fht_plan_s* p = new (std::nothrow) fht_plan_s();

@@ -89,14 +89,23 @@ enum : int32_t { LAUNCH_FUSED = 0, LAUNCH_UPPER = 1, LAUNCH_BAND = 2, LAUNCH_SPI
 // One output row of a root whose tree is a Split_T spine over "parts"
 // (perfect bands of 2^k rows, 64-row blocks and one remainder subtree):
 //   H[t][u] = sum_p part_p[r_p(t)][u + off_p(t)]
-// cyclic: part index mod W; extended: zero outside [0, wpart).  The sum is
-// stored through the quadrant's column map.
+// cyclic: part index mod W; extended: zero outside [0, wpart).  A row of the
+// root is stored through the quadrant's column map; a row of an inner spine
+// node (the top of a lower spine chunk, itself a part of the chunk above) is
+// stored in its own node-local columns in the workspace.
 struct SpineRow {
-  int64_t dst;        // output offset of the row
+  int64_t dst;        // offset of the row: the output (final) or the workspace (an inner spine node)
   int32_t q;          // quadrant
   int32_t term_begin, term_count;
+  int32_t flags;      // SPINE_INNER: an inner spine node, stored in its own columns (no output map)
+  int32_t w;          // columns of the row
   int32_t pad;
 };
+
+enum : int32_t { SPINE_INNER = 1 };
+
+// Tallest perfect band the band pass builds: 64 blocks of 64 rows.
+constexpr int32_t kMaxBandRows = 4096;
 
 struct SpineTerm {
   int64_t row;        // workspace offset of the part's row r_p(t)

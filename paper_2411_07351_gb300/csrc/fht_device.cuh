@@ -604,22 +604,37 @@ __device__ __forceinline__ void spine_group_pipelined(const SpineRow* sr, SpineT
   }
 }
 
+// The row geometry of a spine row: the quadrant's, or for an inner spine node
+// its own width and the identity column map.
+__device__ __forceinline__ QuadDesc spine_row_desc(const QuadDesc* quads, const SpineRow& r) {
+  QuadDesc Q = quads[r.q];
+  if (r.flags & SPINE_INNER) {
+    Q.W = r.w;
+    Q.sigma = 1;
+    Q.kappa = 0;
+  }
+  return Q;
+}
+
 // Rows [r0, r0 + nr) of a spine (terms staged in shared memory by the caller)
-// for the column tile starting at u0.
+// for the column tile starting at u0.  Root rows go to `out`, inner-node rows
+// to `inner` (the workspace base; never a region this launch reads).
 template <bool kC, int BS, int QPT, typename AccT, bool kPipe = true>
 __device__ __forceinline__ void spine_rows_tile(const SpineRow* sr, SpineTerm (*st)[kMaxSpineTerms], int32_t nr,
-                                                const QuadDesc* quads, const AccT* ws, AccT* out, int32_t u0) {
+                                                const QuadDesc* quads, const AccT* ws, AccT* out, AccT* inner,
+                                                int32_t u0) {
   bool uniform = kPipe && nr > 0;
   for (int32_t r = 1; r < nr; r++)
-    uniform = uniform && sr[r].q == sr[0].q && sr[r].term_count == sr[0].term_count;
+    uniform = uniform && sr[r].q == sr[0].q && sr[r].term_count == sr[0].term_count && sr[r].flags == sr[0].flags;
   if constexpr (kPipe) {
   if (uniform) {
-    const QuadDesc& Q = quads[sr[0].q];
+    const QuadDesc Q = spine_row_desc(quads, sr[0]);
     if (u0 >= Q.W) return;
+    AccT* base = (sr[0].flags & SPINE_INNER) ? inner : out;
     switch (sr[0].term_count) {
 #define FHT_SPINE_PIPE(N)                                                                 \
   case N:                                                                                 \
-    spine_group_pipelined<kC, N, BS, QPT, AccT>(sr, st, nr, Q, ws, out, u0);              \
+    spine_group_pipelined<kC, N, BS, QPT, AccT>(sr, st, nr, Q, ws, base, u0);             \
     return;
       FHT_SPINE_PIPE(1) FHT_SPINE_PIPE(2) FHT_SPINE_PIPE(3) FHT_SPINE_PIPE(4) FHT_SPINE_PIPE(5)
       FHT_SPINE_PIPE(6) FHT_SPINE_PIPE(7) FHT_SPINE_PIPE(8)
@@ -633,9 +648,9 @@ __device__ __forceinline__ void spine_rows_tile(const SpineRow* sr, SpineTerm (*
   // terms sweep the tile in two halves
   constexpr int QH = QPT > 1 ? QPT / 2 : 1;
   for (int32_t r = 0; r < nr; r++) {
-    const QuadDesc& Q = quads[sr[r].q];
+    const QuadDesc Q = spine_row_desc(quads, sr[r]);
     if (u0 >= Q.W) continue;
-    AccT* dst = out + sr[r].dst;
+    AccT* dst = ((sr[r].flags & SPINE_INNER) ? inner : out) + sr[r].dst;
     switch (sr[r].term_count) {
 #define FHT_SPINE_CASE(N)                                                   \
   case N:                                                                   \

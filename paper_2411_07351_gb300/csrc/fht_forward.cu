@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) upper_kernel(const RowJob* __restrict__ r
 template <typename AccT>
 __global__ void __launch_bounds__(256) spine_kernel(const SpineRow* __restrict__ rows, int64_t nrows,
                                                    const SpineTerm* __restrict__ terms, const AccT* __restrict__ ws,
-                                                   AccT* __restrict__ out, QuadDescs quads) {
+                                                   AccT* __restrict__ out, AccT* inner, QuadDescs quads) {
   __shared__ SpineTerm st[kSpineRows][kMaxSpineTerms];
   __shared__ SpineRow sr[kSpineRows];
   const int64_t r0 = (int64_t)blockIdx.x * kSpineRows;
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) spine_kernel(const SpineRow* __restrict__
     if (c < sr[r].term_count) st[r][c] = terms[sr[r].term_begin + c];
   }
   __syncthreads();
-  spine_rows_tile<false, 256, kSpineQPT, AccT, kSpinePipe>(sr, st, nr, quads.q, ws, out, u0);
+  spine_rows_tile<false, 256, kSpineQPT, AccT, kSpinePipe>(sr, st, nr, quads.q, ws, out, inner, u0);
 }
 
 // ------------------------------------------------------------------------
@@ -113,8 +113,14 @@ void fused_geometry(const HostPlan& P, FusedGeometry& g) {
   g.smem = std::max(generic, by64);
 }
 
+static int32_t spine_passes(const HostPlan& P) {
+  int32_t n = 0;
+  for (size_t k = 0; k + 1 < P.spine_pass_begin.size(); k++) n += P.spine_pass_begin[k + 1] > P.spine_pass_begin[k];
+  return n;
+}
+
 int32_t forward_launches(const HostPlan& P) {
-  if (P.bands) return 1 + (P.band_items.empty() ? 0 : 1) + (P.spine_rows.empty() ? 0 : 1);
+  if (P.bands) return 1 + (P.band_items.empty() ? 0 : 1) + spine_passes(P);
   return 1 + (int32_t)P.pass_bytes.size();
 }
 
@@ -130,7 +136,16 @@ void forward_launch_info(const HostPlan& P, int32_t k, int32_t& kind, int64_t& b
     bytes = P.band_bytes;
   } else {
     kind = LAUNCH_SPINE;
-    bytes = P.spine_bytes;
+    // the k-th spine launch (empty passes launch nothing)
+    int32_t s = k - 1 - (P.band_items.empty() ? 0 : 1);
+    bytes = 0;
+    for (size_t p = 0; p + 1 < P.spine_pass_begin.size(); p++) {
+      if (P.spine_pass_begin[p + 1] == P.spine_pass_begin[p]) continue;
+      if (s-- == 0) {
+        bytes = P.spine_pass_bytes[p];
+        break;
+      }
+    }
   }
 }
 
@@ -176,17 +191,20 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
       launch++;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (!P.spine_rows.empty()) {
-      QuadDescs qd;
-      for (int q = 0; q < 4; q++) qd.q[q] = P.quad[q];
-      const int64_t n = (int64_t)P.spine_rows.size();
-      int32_t maxW = 1;
-      for (int q = 0; q < 4; q++)
-        if (P.cfg.quads & (1u << q)) maxW = std::max(maxW, P.quad[q].W);
+    QuadDescs qd;
+    for (int q = 0; q < 4; q++) qd.q[q] = P.quad[q];
+    int32_t maxW = 1;
+    for (int q = 0; q < 4; q++)
+      if (P.cfg.quads & (1u << q)) maxW = std::max(maxW, P.quad[q].W);
+    // spine chunks bottom-up: every launch reads the inner nodes the one before wrote
+    for (size_t p = 0; p + 1 < P.spine_pass_begin.size(); p++) {
+      const int64_t b = P.spine_pass_begin[p], n = P.spine_pass_begin[p + 1] - b;
+      if (n <= 0) continue;
       dim3 sgrid((unsigned)((n + kSpineRows - 1) / kSpineRows),
                  (unsigned)((maxW + kSpineTilePlain - 1) / kSpineTilePlain));
       mark(0);
-      spine_kernel<AccT><<<sgrid, 256, 0, st>>>(D.spine_rows, n, D.spine_terms, wsa, static_cast<AccT*>(out), qd);
+      spine_kernel<AccT><<<sgrid, 256, 0, st>>>(D.spine_rows + b, n, D.spine_terms, wsa, static_cast<AccT*>(out),
+                                                wsa, qd);
       mark(1);
       launch++;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -227,6 +227,12 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
   int64_t ws_off = 0;  // elements of the accumulator type after the header
   std::vector<std::vector<RowJob>> passes;
   std::vector<int64_t> bytes_by_height;
+  std::vector<SpineRow> pre_rows;                          // big parts (n > 8192), before the spine
+  std::vector<SpineTerm> pre_terms;
+  int64_t pre_bytes = 0;
+  std::vector<std::vector<SpineRow>> spine_levels_rows;    // by chunk level from the bottom
+  std::vector<std::vector<SpineTerm>> spine_levels_terms;
+  std::vector<int64_t> spine_levels_bytes;
   std::set<int32_t> heights_seen;
 
   for (int q = 0; q < 4; q++) {
@@ -297,14 +303,22 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
     const bool root_fused = !is_upper[rootidx];
     if (root_fused) nbuf = 0;  // the single fused subtree writes the output directly
     // band schedule: walk the Split_T spine from the root; every left child is
-    // a power of two (a perfect band, or a 64-row block), the walk ends at a
-    // power of two or at the remainder subtree of at most 64 rows
+    // a power of two, the walk ends at a power of two or at the remainder
+    // subtree of at most 64 rows.  A power of two of at most 4096 rows is a
+    // part (a perfect band of 64-row blocks, or one block); a larger one (n >
+    // 8192) is a "big" part, summed in a pre-pass from its 4096-row bands.
     const bool use_bands = cfg.split == Split::T && cfg.F == 64 && !root_fused;
-    std::vector<int32_t> spine, parts;
-    auto is_part = [&](int32_t i) {
-      const int32_t m = tr.nodes[i].m;
-      return m <= 64 || (m & (m - 1)) == 0;
-    };
+    std::vector<int32_t> spine, parts, bands, big;
+    // spine chunks of spine_chunk consecutive spine nodes, from the bottom:
+    // [k_top, k_bottom] indices into `spine`.  The top node of every chunk but
+    // the highest is an inner node, summed first into its own compact rows
+    // after the buffers, and a single part of the chunk above.  Big parts
+    // live in the same compact region.
+    std::vector<std::pair<int32_t, int32_t>> chunks;
+    std::vector<int64_t> inner_row0_of(tr.nodes.size(), -1);  // first compact row of an inner or big node
+    int64_t inner_rows = 0;
+    auto is_pow2 = [&](int32_t i) { return (tr.nodes[i].m & (tr.nodes[i].m - 1)) == 0; };
+    auto is_part = [&](int32_t i) { return tr.nodes[i].m <= 64 || (is_pow2(i) && tr.nodes[i].m <= kMaxBandRows); };
     if (use_bands) {
       int32_t i = rootidx;
       while (!is_part(i)) {
@@ -313,15 +327,45 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
         i = tr.nodes[i].child[1];
       }
       parts.push_back(i);
-      for (int32_t pi : parts)
-        if (tr.nodes[pi].m > 64 && pi != rootidx) nbuf = std::max(nbuf, 2);
+      // the bands: parts of 128..4096 rows, and the 4096-row bands under big parts
+      for (int32_t pi : parts) {
+        if (is_part(pi)) {
+          if (tr.nodes[pi].m > 64) bands.push_back(pi);
+          continue;
+        }
+        big.push_back(pi);
+        std::vector<int32_t> stack{pi};
+        while (!stack.empty()) {
+          const int32_t v = stack.back();
+          stack.pop_back();
+          if (tr.nodes[v].m <= kMaxBandRows) {
+            bands.push_back(v);
+          } else {
+            stack.push_back(tr.nodes[v].child[1]);
+            stack.push_back(tr.nodes[v].child[0]);
+          }
+        }
+      }
+      for (int32_t bi : bands)
+        if (bi != rootidx) nbuf = std::max(nbuf, 2);
+      for (int32_t bi : big) {
+        inner_row0_of[bi] = inner_rows;
+        inner_rows += tr.nodes[bi].m;
+      }
+      const int32_t C = std::max(1, cfg.spine_chunk);
+      for (int32_t kb = (int32_t)spine.size() - 1; kb >= 0; kb -= C) chunks.emplace_back(std::max(0, kb - C + 1), kb);
+      for (size_t c = 0; c + 1 < chunks.size(); c++) {
+        inner_row0_of[spine[chunks[c].first]] = inner_rows;
+        inner_rows += tr.nodes[spine[chunks[c].first]].m;
+      }
       P.bands = true;
     }
     P.ws_quad_off[q] = ws_off;
     P.ws_pitch[q] = pitch;
     P.nbuf[q] = nbuf;
     const int64_t bufsize = (int64_t)tr.n * pitch;
-    ws_off += nbuf * bufsize;
+    ws_off += nbuf * bufsize + inner_rows * pitch;
+    const int64_t inner_base = P.ws_quad_off[q] + nbuf * bufsize;
     auto buf_row = [&](int32_t b, int32_t row) -> int64_t {
       return P.ws_quad_off[q] + (int64_t)b * bufsize + (int64_t)row * pitch;
     };
@@ -379,9 +423,8 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
       // pass) or buffer 1 (a band: written by the band pass), or is the root
       auto part_buf = [&](int32_t pi) { return tr.nodes[pi].m <= 64 ? 0 : 1; };
       auto part_w = [&](int32_t pi) { return cfg.ext ? Q.L + tr.nodes[pi].m - 1 : Q.W; };
-      for (int32_t pi : parts) {
+      for (int32_t pi : bands) {
         const TreeNode& band = tr.nodes[pi];
-        if (band.m <= 64) continue;
         const bool fin = pi == rootidx;
         const int32_t B = band.m / 64, G = 64 / B;
         int32_t L = 0;
@@ -418,41 +461,106 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
           const TreeNode& nd = tr.nodes[spine[k]];
           merge_table(nd.m, tr.nodes[nd.child[0]].m, tr.nodes[nd.child[1]].m, stab[k]);
         }
-        P.spine_terms.reserve(P.spine_terms.size() + (size_t)tr.n * (spine.size() + 1));
-        // every output slope t: follow the spine, collecting (part, row, offset)
-        for (int32_t t = 0; t < tr.n; t++) {
-          SpineRow sr;
-          sr.dst = Q.out_off + (int64_t)t * Q.W;
-          sr.q = q;
-          sr.term_begin = (int32_t)P.spine_terms.size();
-          sr.pad = 0;
-          int32_t tn = t;
-          int64_t off = 0;  // accumulated shift in window (x) coordinates
-          auto add_term = [&](int32_t pi, int32_t row) {
-            const TreeNode& pt = tr.nodes[pi];
-            SpineTerm st;
-            st.row = buf_row(part_buf(pi), pt.a + row);
-            st.wpart = part_w(pi);
-            st.off = cfg.ext ? (int32_t)(off + pt.m - tr.n) : (int32_t)off;  // off kept reduced mod W
-            P.spine_terms.push_back(st);
-          };
-          for (size_t k = 0; k < spine.size(); k++) {
-            const TreeNode& nd = tr.nodes[spine[k]];
-            const MergeRow& mr = stab[k][tn];
-            const int32_t t1 = mr.t1, t2 = mr.t2, sh = mr.s;
-            add_term(nd.child[0], t1);
-            off += sh;
-            if (!cfg.ext && off >= Q.W) off = off < 2 * (int64_t)Q.W ? off - Q.W : off % Q.W;
-            tn = t2;
-            if (k + 1 == spine.size()) add_term(nd.child[1], t2);
+        auto node_row = [&](int32_t pi, int32_t row) -> int64_t {
+          if (inner_row0_of[pi] >= 0) return inner_base + (inner_row0_of[pi] + row) * pitch;
+          return buf_row(part_buf(pi), tr.nodes[pi].a + row);
+        };
+        auto node_w = [&](int32_t pi) { return cfg.ext ? Q.L + tr.nodes[pi].m - 1 : Q.W; };
+        // pre-pass: every big part, as the sum over its 4096-row bands; the
+        // terms follow the merges of its subtree, t -> (t1, t2, s), down to
+        // the bands, accumulating the shifts
+        for (int32_t bi : big) {
+          const TreeNode& N = tr.nodes[bi];
+          for (int32_t t = 0; t < N.m; t++) {
+            SpineRow sr{};
+            sr.dst = node_row(bi, t);
+            sr.q = q;
+            sr.flags = SPINE_INNER;
+            sr.w = node_w(bi);
+            sr.term_begin = (int32_t)pre_terms.size();
+            struct Visit {
+              int32_t v, t;
+              int64_t off;
+            };
+            std::vector<Visit> stack{{bi, t, 0}};
+            while (!stack.empty()) {
+              const Visit z = stack.back();
+              stack.pop_back();
+              const TreeNode& nd = tr.nodes[z.v];
+              if (nd.m <= kMaxBandRows) {
+                SpineTerm st;
+                st.row = node_row(z.v, z.t);
+                st.wpart = node_w(z.v);
+                st.off = cfg.ext ? (int32_t)(z.off + nd.m - N.m) : (int32_t)z.off;
+                pre_terms.push_back(st);
+                continue;
+              }
+              int32_t t1, t2, sh;
+              merge_entry(nd.m, tr.nodes[nd.child[0]].m, tr.nodes[nd.child[1]].m, z.t, t1, t2, sh);
+              int64_t off2 = z.off + sh;
+              if (!cfg.ext && off2 >= Q.W) off2 %= Q.W;
+              stack.push_back({nd.child[1], t2, off2});
+              stack.push_back({nd.child[0], t1, z.off});
+            }
+            sr.term_count = (int32_t)pre_terms.size() - sr.term_begin;
+            P.max_spine_terms = std::max(P.max_spine_terms, sr.term_count);
+            pre_rows.push_back(sr);
           }
-          sr.term_count = (int32_t)P.spine_terms.size() - sr.term_begin;
-          P.max_spine_terms = std::max(P.max_spine_terms, sr.term_count);
-          P.spine_rows.push_back(sr);
+          // compulsory bytes: the bands once, the big part written once
+          pre_bytes += 2 * (int64_t)N.m * node_w(bi) * acc;
         }
-        int64_t parts_bytes = 0;
-        for (int32_t pi : parts) parts_bytes += (int64_t)tr.nodes[pi].m * part_w(pi);
-        P.spine_bytes += (parts_bytes + qsize) * acc;
+        if ((int32_t)spine_levels_rows.size() < (int32_t)chunks.size()) spine_levels_rows.resize(chunks.size());
+        if ((int32_t)spine_levels_terms.size() < (int32_t)chunks.size()) spine_levels_terms.resize(chunks.size());
+        if ((int32_t)spine_levels_bytes.size() < (int32_t)chunks.size()) spine_levels_bytes.resize(chunks.size(), 0);
+        for (size_t c = 0; c < chunks.size(); c++) {
+          const int32_t ktop = chunks[c].first, kbot = chunks[c].second;
+          const int32_t top = spine[ktop];
+          const TreeNode& N = tr.nodes[top];
+          const bool fin = top == rootidx;
+          std::vector<SpineRow>& rows_out = spine_levels_rows[c];
+          std::vector<SpineTerm>& terms_out = spine_levels_terms[c];
+          // every slope t of the chunk's top node: follow the spine down to the
+          // chunk's lower boundary, collecting (part, row, offset)
+          for (int32_t t = 0; t < N.m; t++) {
+            SpineRow sr{};
+            sr.dst = fin ? Q.out_off + (int64_t)t * Q.W : node_row(top, t);
+            sr.q = q;
+            sr.flags = fin ? 0 : SPINE_INNER;
+            sr.w = fin ? Q.W : node_w(top);
+            sr.term_begin = (int32_t)terms_out.size();  // rebased when the launches are flattened
+            int32_t tn = t;
+            int64_t off = 0;  // accumulated shift in window (x) coordinates
+            auto add_term = [&](int32_t pi, int32_t row) {
+              const TreeNode& pt = tr.nodes[pi];
+              SpineTerm st;
+              st.row = node_row(pi, row);
+              st.wpart = node_w(pi);
+              st.off = cfg.ext ? (int32_t)(off + pt.m - N.m) : (int32_t)off;  // off kept reduced mod W
+              terms_out.push_back(st);
+            };
+            for (int32_t k = ktop; k <= kbot; k++) {
+              const TreeNode& nd = tr.nodes[spine[k]];
+              const MergeRow& mr = stab[k][tn];
+              add_term(nd.child[0], mr.t1);
+              off += mr.s;
+              if (!cfg.ext && off >= Q.W) off = off < 2 * (int64_t)Q.W ? off - Q.W : off % Q.W;
+              tn = mr.t2;
+              if (k == kbot) add_term(nd.child[1], mr.t2);
+            }
+            sr.term_count = (int32_t)terms_out.size() - sr.term_begin;
+            P.max_spine_terms = std::max(P.max_spine_terms, sr.term_count);
+            rows_out.push_back(sr);
+          }
+          // compulsory bytes of this launch: its parts once, its node written once
+          int64_t by = (int64_t)N.m * (fin ? Q.W : node_w(top));
+          for (int32_t k = ktop; k <= kbot; k++) {
+            const int32_t pi = tr.nodes[spine[k]].child[0];
+            by += (int64_t)tr.nodes[pi].m * node_w(pi);
+          }
+          const int32_t low = tr.nodes[spine[kbot]].child[1];
+          by += (int64_t)tr.nodes[low].m * node_w(low);
+          spine_levels_bytes[c] += by * acc;
+        }
       }
     }
 
@@ -536,6 +644,24 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
     for (const TreeNode& nd : tr.nodes)
       if (nd.m > 1) P.adds += (int64_t)nd.m * (cfg.ext ? Q.L + nd.m - 1 : Q.W);
     P.ideal_bytes += (int64_t)Q.n * Q.L * P.in_size + qsize * acc;
+  }
+  // spine launches: the big parts, then the lowest chunk level of every quadrant first
+  P.spine_pass_begin.push_back(0);
+  if (!pre_rows.empty()) {
+    spine_levels_rows.insert(spine_levels_rows.begin(), pre_rows);
+    spine_levels_terms.insert(spine_levels_terms.begin(), pre_terms);
+    spine_levels_bytes.insert(spine_levels_bytes.begin(), pre_bytes);
+  }
+  for (size_t c = 0; c < spine_levels_rows.size(); c++) {
+    const int32_t base = (int32_t)P.spine_terms.size();
+    for (SpineRow sr : spine_levels_rows[c]) {
+      sr.term_begin += base;
+      P.spine_rows.push_back(sr);
+    }
+    P.spine_terms.insert(P.spine_terms.end(), spine_levels_terms[c].begin(), spine_levels_terms[c].end());
+    P.spine_pass_begin.push_back((int64_t)P.spine_rows.size());
+    P.spine_pass_bytes.push_back(spine_levels_bytes[c]);
+    P.spine_bytes += spine_levels_bytes[c];
   }
   // tiles: fast-path items use tile_cols; generic items (two ping-pong
   // buffers of up to 63 rows) use half of it, so their shared windows stay

@@ -55,6 +55,7 @@ struct PlanConfig {
   int32_t F = 64;          // fused rows
   int32_t TW = 128;        // fused column tile
   int32_t threads = 256;   // fused CTA size
+  int32_t spine_chunk = 3; // spine nodes merged per spine-sum launch (the lower chunks first)
   bool with_adjoint = false;  // also build the adjoint tables
   int32_t rounding = 0;       // 0: exact half-to-even; 1: rint(t * k) with k = (m_i - 1)/(m - 1) in fp64
 };
@@ -103,8 +104,10 @@ struct HostPlan {
   // spine-sum pass, replacing the per-height passes
   bool bands = false;
   std::vector<FusedItem> band_items;
-  std::vector<SpineRow> spine_rows;
+  std::vector<SpineRow> spine_rows;       // all spine launches, lowest chunk level first
   std::vector<SpineTerm> spine_terms;
+  std::vector<int64_t> spine_pass_begin;  // spine_rows[spine_pass_begin[k] .. spine_pass_begin[k+1])
+  std::vector<int64_t> spine_pass_bytes;
   int32_t max_band_ntiles = 0;
   int64_t band_bytes = 0, spine_bytes = 0;
   int32_t max_spine_terms = 0;

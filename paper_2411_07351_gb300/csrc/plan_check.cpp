@@ -3,8 +3,11 @@
 // fht_forward.cu; a plan that passes cannot make them touch memory outside
 // the input, the workspace, the output or the shared window.
 #include <algorithm>
+#include <cstdint>
+#include <iterator>
 #include <set>
 #include <string>
+#include <vector>
 
 #include "fht_launch.hpp"
 #include "plan.hpp"
@@ -140,27 +143,62 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
       }
     }
   }
-  for (size_t k = 0; k < P.spine_rows.size(); k++) {
-    const SpineRow& R = P.spine_rows[k];
-    if (R.q < 0 || R.q > 3 || !(P.cfg.quads & (1u << R.q))) return at("spine", k) + "bad quadrant";
-    const QuadDesc& Q = P.quad[R.q];
-    if (R.term_count < 1 || R.term_count > 16 || R.term_begin < 0 ||
-        (size_t)R.term_begin + R.term_count > P.spine_terms.size())
-      return at("spine", k) + "terms";
-    if (R.dst < 0 || R.dst + Q.W > out_elems) return at("spine", k) + "row outside the output";
-    for (int32_t u : {0, Q.W - 1}) {
-      const int64_t X = (int64_t)Q.sigma * u + Q.kappa;
-      if (X < -Q.W || X >= 2 * (int64_t)Q.W) return at("spine", k) + "column map needs more than one wrap";
-    }
-    for (int32_t c = 0; c < R.term_count; c++) {
-      const SpineTerm& T = P.spine_terms[R.term_begin + c];
-      if (Q.ext) {
-        if (T.row < 0 || T.row + T.wpart > ws_elems) return at("spine", k) + "part row outside the workspace";
+  if (!P.spine_rows.empty() &&
+      (P.spine_pass_begin.size() != P.spine_pass_bytes.size() + 1 || P.spine_pass_begin.front() != 0 ||
+       P.spine_pass_begin.back() != (int64_t)P.spine_rows.size()))
+    return "spine passes do not cover the spine rows";
+  // inner spine rows: written by one pass, read only by later passes
+  std::set<int64_t> inner_all, inner_written;  // inner row starts: of every pass, of earlier passes
+  for (const SpineRow& R : P.spine_rows)
+    if (R.flags & SPINE_INNER) inner_all.insert(R.dst);
+  for (size_t p = 0; p + 1 < P.spine_pass_begin.size(); p++) {
+    if (P.spine_pass_begin[p + 1] < P.spine_pass_begin[p]) return "spine passes out of order";
+    std::vector<std::pair<int64_t, int64_t>> wr;  // [begin, end) written by this pass
+    for (int64_t k = P.spine_pass_begin[p]; k < P.spine_pass_begin[p + 1]; k++) {
+      const SpineRow& R = P.spine_rows[k];
+      if (R.q < 0 || R.q > 3 || !(P.cfg.quads & (1u << R.q))) return at("spine", k) + "bad quadrant";
+      const QuadDesc& Q = P.quad[R.q];
+      if (R.term_count < 1 || R.term_count > 16 || R.term_begin < 0 ||
+          (size_t)R.term_begin + R.term_count > P.spine_terms.size())
+        return at("spine", k) + "terms";
+      if (R.flags & SPINE_INNER) {
+        if (R.w < 1 || R.w > Q.W || (!Q.ext && R.w != Q.W)) return at("spine", k) + "inner row width";
+        if (R.dst < 0 || R.dst + R.w > ws_elems) return at("spine", k) + "inner row outside the workspace";
+        wr.emplace_back(R.dst, R.dst + R.w);
       } else {
-        if (T.wpart != Q.W || T.off < 0 || T.off >= Q.W || T.row < 0 || T.row + Q.W > ws_elems)
-          return at("spine", k) + "cyclic part row";
+        if (R.dst < 0 || R.dst + Q.W > out_elems) return at("spine", k) + "row outside the output";
+        for (int32_t u : {0, Q.W - 1}) {
+          const int64_t X = (int64_t)Q.sigma * u + Q.kappa;
+          if (X < -Q.W || X >= 2 * (int64_t)Q.W) return at("spine", k) + "column map needs more than one wrap";
+        }
+      }
+      for (int32_t c = 0; c < R.term_count; c++) {
+        const SpineTerm& T = P.spine_terms[R.term_begin + c];
+        if (Q.ext) {
+          if (T.row < 0 || T.row + T.wpart > ws_elems) return at("spine", k) + "part row outside the workspace";
+        } else {
+          if (T.wpart != Q.W || T.off < 0 || T.off >= Q.W || T.row < 0 || T.row + Q.W > ws_elems)
+            return at("spine", k) + "cyclic part row";
+        }
       }
     }
+    std::sort(wr.begin(), wr.end());
+    for (size_t i = 1; i < wr.size(); i++)
+      if (wr[i].first < wr[i - 1].second) return "spine pass " + std::to_string(p) + ": inner rows overlap";
+    // no term of this pass reads a row this pass writes; a term that reads an
+    // inner row reads one an earlier pass wrote
+    for (int64_t k = P.spine_pass_begin[p]; k < P.spine_pass_begin[p + 1]; k++) {
+      const SpineRow& R = P.spine_rows[k];
+      for (int32_t c = 0; c < R.term_count; c++) {
+        const SpineTerm& T = P.spine_terms[R.term_begin + c];
+        const int64_t lo = T.row, hi = T.row + T.wpart;
+        auto it = std::upper_bound(wr.begin(), wr.end(), std::make_pair(lo, INT64_MAX));
+        if (it != wr.begin() && std::prev(it)->second > lo) return at("spine", k) + "reads a row its pass writes";
+        if (it != wr.end() && it->first < hi) return at("spine", k) + "reads a row its pass writes";
+        if (inner_all.count(lo) && !inner_written.count(lo)) return at("spine", k) + "reads an inner row not yet written";
+      }
+    }
+    for (const auto& w : wr) inner_written.insert(w.first);
   }
 
   // ---- adjoint ----

@@ -38,7 +38,7 @@ class Plan:
     def __init__(self, h: int, w: int, dtype=torch.float32, quads: int = C.FHT_QALL,
                  boundary: str = "cyclic", split: str = "T", device: int | None = None,
                  fused_rows: int = 0, tile_cols: int = 0, threads: int = 0, with_adjoint: bool = False,
-                 tuning: str | None = None, rounding: str = "exact"):
+                 tuning: str | None = None, rounding: str = "exact", spine_chunk: int = 0):
         self._lib = C.load()
         if tuning == "auto" and not (tile_cols or threads):
             from .tune import lookup
@@ -59,7 +59,8 @@ class Plan:
         self.device_index = int(device)
         if rounding not in ("exact", "float"):
             raise ValueError("rounding is 'exact' or 'float'")
-        tun = C.fht_tuning_t(fused_rows, tile_cols, threads, int(with_adjoint), 1 if rounding == "float" else 0)
+        tun = C.fht_tuning_t(fused_rows, tile_cols, threads, int(with_adjoint), 1 if rounding == "float" else 0,
+                             int(spine_chunk))
         handle = ctypes.c_void_p()
         args = (ctypes.byref(handle), self.h, self.w, self.fht_dtype, self.quads, BOUNDARY[boundary], SPLIT[split],
                 self.device_index, ctypes.byref(tun))

@@ -79,6 +79,17 @@ def test_plan_verifier_over_many_shapes(F):
                    with_adjoint=True).check()
 
 
+def test_plan_verifier_spine_chunks_and_tall_roots(F):
+    # spine chunk sizes, and roots taller than 8192 rows (their power-of-two
+    # part is summed from 4096-row bands before the spine)
+    for h in (2047, 4095, 8191, 8193, 9000, 16384, 20000, 40000):
+        for ch in (1, 2, 3, 100):
+            for b in ("cyclic", "extended"):
+                F.Plan(h, 3, torch.float32, 15, b, device=-1, spine_chunk=ch).check()
+    with pytest.raises(F.FHTError):
+        F.Plan(100, 100, torch.float32, 15, device=-1, spine_chunk=-1)
+
+
 def test_invalid_arguments(F):
     with pytest.raises(F.FHTError):
         F.Plan(0, 5, torch.float32, 1, device=-1)
@@ -103,11 +114,17 @@ def test_host_only_plan_cannot_run(F):
 def test_byte_model_c2(F):
     # 4095^2 float32, four quadrants, extended; ideal = input once + output once.
     # Band schedule (Split_T, 64-row blocks): fused pass + band pass + spine sum,
-    # 2.05 GB.  The per-height schedule (here forced by 32-row fused subtrees)
-    # moves one read + write of every node per tree height: 5.1 GB.
+    # 2.05 GB in one spine launch; summing the spine in chunks of three nodes
+    # (the default) writes and reads the 511-row inner node once more: + 75 MB.
+    # The per-height schedule (here forced by 32-row fused subtrees) moves one
+    # read + write of every node per tree height: 5.1 GB.
     p = F.Plan(4095, 4095, torch.float32, 15, "extended", device=-1)
     assert abs(p.info.ideal_bytes - (4 * 4095 * 4095 * 4 + 4 * 4095 * 8189 * 4)) == 0
-    assert 2.0e9 < p.info.model_bytes < 2.1e9
+    assert 2.1e9 < p.info.model_bytes < 2.15e9
+    p1 = F.Plan(4095, 4095, torch.float32, 15, "extended", device=-1, spine_chunk=100)
+    assert 2.0e9 < p1.info.model_bytes < 2.1e9
+    inner = 4 * 2 * 511 * (4095 + 510) * 4
+    assert abs(p.info.model_bytes - p1.info.model_bytes - inner) < 1e6
     assert p.info.upper_passes == 6
     p32 = F.Plan(4095, 4095, torch.float32, 15, "extended", device=-1, fused_rows=32)
     assert 5.0e9 < p32.info.model_bytes < 5.2e9

@@ -188,3 +188,45 @@ def test_float_k_rounding(F, orc):
             assert np.array_equal(got, orc.fht(img.astype(np.int64), 15, orc.EXTENDED))
     finally:
         orc.set_rounding(orc.ROUND_EXACT)
+
+
+@pytest.mark.parametrize("spine_chunk", [1, 2, 3, 100])
+def test_spine_chunks_same_result(F, orc, spine_chunk):
+    """The spine of a Split_T root summed in chunks (lower chunk tops first, as
+    single parts of the chunk above) gives the same transform for every chunk size."""
+    img = inputs.uniform_u8(2047 + spine_chunk, 2047, 300)
+    check_exact(F, orc, img, 15, "cyclic", spine_chunk=spine_chunk)
+    check_exact(F, orc, img, 15, "extended", spine_chunk=spine_chunk)
+    imf = inputs.normal_f32(1500 + spine_chunk, 1500, 777)
+    check_float(F, orc, imf, 15, "extended", spine_chunk=spine_chunk)
+
+
+@pytest.mark.parametrize("h,w", [(9000, 37), (12289, 5), (16500, 9)])
+def test_taller_than_8192(F, orc, h, w):
+    """Split_T roots whose power-of-two part is taller than the largest band
+    (4096 rows): that part is summed from its bands first.  Cyclic: the whole
+    output against the oracle; extended: sampled outputs against the definition."""
+    img = inputs.uniform_u8(h * 31 + w, h, w)
+    check_exact(F, orc, img, 15, "cyclic")
+    x = torch.from_numpy(img).cuda()
+    p = F.Plan(h, w, torch.uint8, 15, "extended")
+    p.check()
+    blocks = p.unpack(p.forward(x))
+    rng = np.random.default_rng(h)
+    k = 4000
+    qs = rng.integers(0, 4, k)
+    ts = np.array([rng.integers(0, blocks[q].shape[0]) for q in qs])
+    xs = np.array([rng.integers(0, blocks[q].shape[1]) for q in qs])
+    val, _ = orc.brute_at(img, qs, ts, xs, orc.EXTENDED)
+    got = np.zeros(k, dtype=np.int64)
+    for q in range(4):
+        sel = np.nonzero(qs == q)[0]
+        ti, xi = torch.from_numpy(ts[sel]).cuda(), torch.from_numpy(xs[sel]).cuda()
+        got[sel] = blocks[q][ti, xi].cpu().numpy()
+    assert np.array_equal(got, val.astype(np.int64))
+    # every row of every quadrant sums to the image total
+    total = int(img.astype(np.int64).sum())
+    for b in blocks:
+        assert (b.long().sum(1) == total).all()
+    del blocks, x, p
+    torch.cuda.empty_cache()
