@@ -532,75 +532,80 @@ __device__ __forceinline__ void spine_tile(const SpineTerm* st, const QuadDesc& 
 }
 
 // Loads of one spine row's terms for this thread's QPT columns
-// u = u0 + tid + q BS.  Branch-free: for each term the columns that read
-// inside the part row (extended) or that wrap (cyclic) form one contiguous
-// range of q BS, found from two thresholds; every load uses the term's
-// hoisted pointer with a compile-time offset.
+// u = u0 + tid + q BS of a row of W columns.  Branch-free: for each term the
+// columns that read inside the part row (extended) or that wrap (cyclic) form
+// one contiguous range of q BS, found from two thresholds; every load uses the
+// term's hoisted pointer with a compile-time offset.
 template <bool kC, int NT, int BS, int QPT, typename AccT>
-__device__ __forceinline__ void spine_load(const SpineTerm* st, const QuadDesc& Q, const AccT* __restrict__ ws,
+__device__ __forceinline__ void spine_load(const SpineTerm* st, int32_t W, bool ext, const AccT* __restrict__ ws,
                                            int32_t u0, AccT (&v)[NT][QPT]) {
   const int32_t base_u = u0 + (int32_t)threadIdx.x;
-  const int32_t live = Q.W - base_u;  // column q is inside the output row iff q BS < live
-  const bool full = u0 + BS * QPT <= Q.W;
+  const int32_t live = W - base_u;  // column q is inside the row iff q BS < live
+  const bool full = u0 + BS * QPT <= W;
 #pragma unroll
   for (int c = 0; c < NT; c++) {
     const int32_t off = st[c].off;
     const AccT* __restrict__ src = ws + st[c].row + (base_u + off);
     // CTA-uniform test: the whole tile reads one in-bounds stretch of the part row
-    const bool clean = full && (Q.ext ? (u0 + off >= 0 && u0 + BS * QPT + off <= st[c].wpart)
-                                      : (u0 + BS * QPT + off <= Q.W));
+    const bool clean = full && (ext ? (u0 + off >= 0 && u0 + BS * QPT + off <= st[c].wpart)
+                                    : (u0 + BS * QPT + off <= W));
     if (clean) {
 #pragma unroll
       for (int q = 0; q < QPT; q++) v[c][q] = ld_ws<kC>(src + q * BS);
-    } else if (Q.ext) {
+    } else if (ext) {
       const int32_t lo = -(base_u + off), hi = st[c].wpart - (base_u + off);  // valid iff lo <= q BS < hi
 #pragma unroll
       for (int q = 0; q < QPT; q++)
         v[c][q] = (q * BS >= lo && q * BS < hi && q * BS < live) ? ld_ws<kC>(src + q * BS) : AccT(0);
     } else {
-      const int32_t wrap = Q.W - (base_u + off);  // q BS >= wrap reads W columns back
+      const int32_t wrap = W - (base_u + off);  // q BS >= wrap reads W columns back
 #pragma unroll
       for (int q = 0; q < QPT; q++) {
-        const AccT* p = (q * BS >= wrap) ? src - Q.W : src;
+        const AccT* p = (q * BS >= wrap) ? src - W : src;
         v[c][q] = (q * BS < live) ? ld_ws<kC>(p + q * BS) : AccT(0);
       }
     }
   }
 }
 
-template <int NT, int BS, int QPT, typename AccT>
-__device__ __forceinline__ void spine_store(const QuadDesc& Q, AccT* __restrict__ dst, int32_t u0,
-                                            const AccT (&v)[NT][QPT]) {
+// Sum and store: through the quadrant's column map X = (sigma u + kappa) mod W
+// (root rows, kMap) or at u itself (inner spine nodes).
+template <bool kMap, int NT, int BS, int QPT, typename AccT>
+__device__ __forceinline__ void spine_store(int32_t W, int32_t sigma, int32_t kappa, AccT* __restrict__ dst,
+                                            int32_t u0, const AccT (&v)[NT][QPT]) {
 #pragma unroll
   for (int q = 0; q < QPT; q++) {
     AccT acc = v[0][q];
 #pragma unroll
     for (int c = 1; c < NT; c++) acc += v[c][q];
     const int32_t u = u0 + q * BS + (int32_t)threadIdx.x;
-    if (u < Q.W) {
-      int32_t X = Q.sigma * u + Q.kappa;
-      if (X < 0) X += Q.W;
-      if (X >= Q.W) X -= Q.W;
+    if (u < W) {
+      int32_t X = u;
+      if constexpr (kMap) {
+        X = sigma * u + kappa;
+        if (X < 0) X += W;
+        if (X >= W) X -= W;
+      }
       dst[X] = acc;
     }
   }
 }
 
-// All nr rows share one quadrant and one term count: the loads of row r + 1
-// are issued before row r is summed and stored, so two rows of loads are in
-// flight per thread.
-template <bool kC, int NT, int BS, int QPT, typename AccT>
+// All nr rows share one quadrant, one kind and one term count: the loads of
+// row r + 1 are issued before row r is summed and stored, so two rows of
+// loads are in flight per thread.
+template <bool kC, bool kMap, int NT, int BS, int QPT, typename AccT>
 __device__ __forceinline__ void spine_group_pipelined(const SpineRow* sr, SpineTerm (*st)[kMaxSpineTerms],
-                                                      int32_t nr, const QuadDesc& Q, const AccT* ws, AccT* out,
-                                                      int32_t u0) {
+                                                      int32_t nr, int32_t W, bool ext, int32_t sigma, int32_t kappa,
+                                                      const AccT* ws, AccT* out, int32_t u0) {
   AccT a[NT][QPT], b[NT][QPT];
-  spine_load<kC, NT, BS, QPT, AccT>(st[0], Q, ws, u0, a);
+  spine_load<kC, NT, BS, QPT, AccT>(st[0], W, ext, ws, u0, a);
   for (int32_t r = 0; r < nr; r += 2) {
-    if (r + 1 < nr) spine_load<kC, NT, BS, QPT, AccT>(st[r + 1], Q, ws, u0, b);
-    spine_store<NT, BS, QPT, AccT>(Q, out + sr[r].dst, u0, a);
+    if (r + 1 < nr) spine_load<kC, NT, BS, QPT, AccT>(st[r + 1], W, ext, ws, u0, b);
+    spine_store<kMap, NT, BS, QPT, AccT>(W, sigma, kappa, out + sr[r].dst, u0, a);
     if (r + 1 >= nr) break;
-    if (r + 2 < nr) spine_load<kC, NT, BS, QPT, AccT>(st[r + 2], Q, ws, u0, a);
-    spine_store<NT, BS, QPT, AccT>(Q, out + sr[r + 1].dst, u0, b);
+    if (r + 2 < nr) spine_load<kC, NT, BS, QPT, AccT>(st[r + 2], W, ext, ws, u0, a);
+    spine_store<kMap, NT, BS, QPT, AccT>(W, sigma, kappa, out + sr[r + 1].dst, u0, b);
   }
 }
 
@@ -628,19 +633,34 @@ __device__ __forceinline__ void spine_rows_tile(const SpineRow* sr, SpineTerm (*
     uniform = uniform && sr[r].q == sr[0].q && sr[r].term_count == sr[0].term_count && sr[r].flags == sr[0].flags;
   if constexpr (kPipe) {
   if (uniform) {
-    const QuadDesc Q = spine_row_desc(quads, sr[0]);
-    if (u0 >= Q.W) return;
-    AccT* base = (sr[0].flags & SPINE_INNER) ? inner : out;
-    switch (sr[0].term_count) {
-#define FHT_SPINE_PIPE(N)                                                                 \
-  case N:                                                                                 \
-    spine_group_pipelined<kC, N, BS, QPT, AccT>(sr, st, nr, Q, ws, base, u0);             \
+    const QuadDesc& Q = quads[sr[0].q];
+    if (sr[0].flags & SPINE_INNER) {
+      const int32_t W = sr[0].w;
+      if (u0 >= W) return;
+      switch (sr[0].term_count) {
+#define FHT_SPINE_PIPE(N)                                                                             \
+  case N:                                                                                             \
+    spine_group_pipelined<kC, false, N, BS, QPT, AccT>(sr, st, nr, W, Q.ext, 1, 0, ws, inner, u0);    \
     return;
-      FHT_SPINE_PIPE(1) FHT_SPINE_PIPE(2) FHT_SPINE_PIPE(3) FHT_SPINE_PIPE(4) FHT_SPINE_PIPE(5)
-      FHT_SPINE_PIPE(6) FHT_SPINE_PIPE(7) FHT_SPINE_PIPE(8)
+        FHT_SPINE_PIPE(1) FHT_SPINE_PIPE(2) FHT_SPINE_PIPE(3) FHT_SPINE_PIPE(4) FHT_SPINE_PIPE(5)
+        FHT_SPINE_PIPE(6) FHT_SPINE_PIPE(7) FHT_SPINE_PIPE(8)
 #undef FHT_SPINE_PIPE
-      default:
-        break;  // more terms: the row-by-row path below
+        default:
+          break;  // more terms: the row-by-row path below
+      }
+    } else {
+      if (u0 >= Q.W) return;
+      switch (sr[0].term_count) {
+#define FHT_SPINE_PIPE(N)                                                                                     \
+  case N:                                                                                                     \
+    spine_group_pipelined<kC, true, N, BS, QPT, AccT>(sr, st, nr, Q.W, Q.ext, Q.sigma, Q.kappa, ws, out, u0); \
+    return;
+        FHT_SPINE_PIPE(1) FHT_SPINE_PIPE(2) FHT_SPINE_PIPE(3) FHT_SPINE_PIPE(4) FHT_SPINE_PIPE(5)
+        FHT_SPINE_PIPE(6) FHT_SPINE_PIPE(7) FHT_SPINE_PIPE(8)
+#undef FHT_SPINE_PIPE
+        default:
+          break;
+      }
     }
   }
   }

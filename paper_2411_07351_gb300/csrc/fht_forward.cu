@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) upper_kernel(const RowJob* __restrict__ r
 }
 
 template <typename AccT>
-__global__ void __launch_bounds__(256) spine_kernel(const SpineRow* __restrict__ rows, int64_t nrows,
+__global__ void __launch_bounds__(256, sizeof(AccT) > 4 ? 1 : 3) spine_kernel(const SpineRow* __restrict__ rows, int64_t nrows,
                                                    const SpineTerm* __restrict__ terms, const AccT* __restrict__ ws,
                                                    AccT* __restrict__ out, AccT* inner, QuadDescs quads) {
   __shared__ SpineTerm st[kSpineRows][kMaxSpineTerms];

@@ -2,10 +2,12 @@
 
     python -m paper_2411_07351_gb300.profile_forward --h 2048 --w 2048 --reps 3
 
-Each rep launches the plan's kernels once (fused pass, then one pass per upper
-tree height).  Nothing is timed here; use it under ncu.
+Each rep launches the plan's kernels once (fused pass, then the band pass and
+the spine launches, or one pass per upper tree height).  Nothing is timed
+here; use it under ncu.
 """
 import argparse
+import ctypes
 
 import torch
 
@@ -30,7 +32,11 @@ def main():
     for _ in range(a.reps):
         p.forward(x, out, ws)
     torch.cuda.synchronize()
-    print(f"ok {a.h}x{a.w} {a.dtype} {a.boundary}: launches per forward = {1 + p.info.upper_passes}, "
+    from paper_2411_07351_gb300 import _capi
+
+    n = ctypes.c_int32()
+    _capi.check(_capi.load().fht_plan_launches(p._h, ctypes.byref(n)), "fht_plan_launches")
+    print(f"ok {a.h}x{a.w} {a.dtype} {a.boundary}: launches per forward = {n.value}, "
           f"model bytes = {p.info.model_bytes}")
 
 
