@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchJob*
           for (int32_t tile = U.tile; tile < U.tile + U.ntiles && tile < it.ntiles; tile++) {
             if (tile > U.tile) __syncthreads();  // the previous tile's shared reads are done
             if (it.kind != FUSED_GENERIC) {
-              fused_block<true, InT, AccT>(jb.fp, it, Q, tile, sm, sm + (size_t)64 * jb.fp.RS);
+              fused_block_any<true, InT, AccT>(jb.fp, it, Q, tile, sm, sm + (size_t)64 * jb.fp.RS);
             } else {
               fused_generic<InT, AccT>(jb.fp, it, Q, tile, sm, sm + (size_t)jb.fp.Fm * jb.fp.RP);
             }

@@ -458,6 +458,203 @@ __device__ __forceinline__ void fused_block(const FusedParams& p, const FusedIte
   }
 }
 
+// ---- compile-time tile width: the same block paths with every pitch and
+// width a constant, so that shared addresses are base + immediate and the
+// column loops unroll without per-iteration bounds or pointer arithmetic ----
+
+template <int M, int RSRC, int RDST, int WIDTH, typename AccT>
+__device__ __forceinline__ void merge4_pass_c(const AccT* src, AccT* dst) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  for (int32_t rq = warp; rq < 16; rq += nwarps) {
+    const AccT *q0, *q1, *q2, *q3;
+    int32_t r0;
+    merge4_ptrs<M, AccT>(src, RSRC, rq, q0, q1, q2, q3, r0);
+    q0 += lane;
+    q1 += lane;
+    q2 += lane;
+    q3 += lane;
+    AccT* d = dst + r0 * RDST + lane;
+#pragma unroll
+    for (int c = 0; c < (WIDTH + 31) / 32; c++) {
+      if (32 * c + 32 <= WIDTH || 32 * c + lane < WIDTH) {
+        AccT o[4];
+        merge4_at<AccT>(q0, q1, q2, q3, 32 * c, o);
+        d[32 * c] = o[0];
+        d[RDST + 32 * c] = o[1];
+        d[2 * RDST + 32 * c] = o[2];
+        d[3 * RDST + 32 * c] = o[3];
+      }
+    }
+  }
+}
+
+template <int RSRC, int RDST, int WIDTH, typename AccT>
+__device__ __forceinline__ void merge2_pass1_c(const AccT* src, AccT* dst) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  for (int32_t rp = warp; rp < 32; rp += nwarps) {
+    const AccT *q0, *q1;
+    int32_t r0;
+    merge2_ptrs<1, AccT>(src, RSRC, rp, q0, q1, r0);
+    q0 += lane;
+    q1 += lane;
+    AccT* d = dst + r0 * RDST + lane;
+#pragma unroll
+    for (int c = 0; c < (WIDTH + 31) / 32; c++) {
+      if (32 * c + 32 <= WIDTH || 32 * c + lane < WIDTH) {
+        const AccT a = q0[32 * c];
+        d[32 * c] = a + q1[32 * c];
+        d[RDST + 32 * c] = a + q1[32 * c + 1];
+      }
+    }
+  }
+}
+
+template <int M, int RSRC, int TW, typename AccT>
+__device__ __forceinline__ void final_merge4_c(const FusedItem& it, const QuadDesc& Q, const AccT* src, AccT* base,
+                                               int32_t u0, int32_t ncols) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  const int64_t pitch = it.dst_pitch;
+  for (int32_t rq = warp; rq < 16; rq += nwarps) {
+    const AccT *q0, *q1, *q2, *q3;
+    int32_t r0;
+    merge4_ptrs<M, AccT>(src, RSRC, rq, q0, q1, q2, q3, r0);
+    q0 += lane;
+    q1 += lane;
+    q2 += lane;
+    q3 += lane;
+    AccT* o = base + (int64_t)r0 * pitch;
+#pragma unroll
+    for (int c = 0; c < TW / 32; c++) {
+      const int32_t j = 32 * c + lane;
+      if (j < ncols) {
+        AccT v[4];
+        merge4_at<AccT>(q0, q1, q2, q3, 32 * c, v);
+        int32_t X = u0 + j;
+        if (it.final_) {
+          X = Q.sigma * X + Q.kappa;
+          if (X < 0) X += Q.W;
+          if (X >= Q.W) X -= Q.W;
+        }
+        AccT* oo = o + X;
+        oo[0] = v[0];
+        oo[pitch] = v[1];
+        oo[2 * pitch] = v[2];
+        oo[3 * pitch] = v[3];
+      }
+    }
+  }
+}
+
+template <int RSRC, int TW, typename AccT>
+__device__ __forceinline__ void final_merge2_1_c(const FusedItem& it, const QuadDesc& Q, const AccT* src, AccT* base,
+                                                 int32_t u0, int32_t ncols) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  const int64_t pitch = it.dst_pitch;
+  for (int32_t rp = warp; rp < 32; rp += nwarps) {
+    const AccT *q0, *q1;
+    int32_t r0;
+    merge2_ptrs<1, AccT>(src, RSRC, rp, q0, q1, r0);
+    q0 += lane;
+    q1 += lane;
+    AccT* o = base + (int64_t)r0 * pitch;
+#pragma unroll
+    for (int c = 0; c < TW / 32; c++) {
+      const int32_t j = 32 * c + lane;
+      if (j < ncols) {
+        const AccT a = q0[32 * c];
+        int32_t X = u0 + j;
+        if (it.final_) {
+          X = Q.sigma * X + Q.kappa;
+          if (X < 0) X += Q.W;
+          if (X >= Q.W) X -= Q.W;
+        }
+        o[X] = a + q1[32 * c];
+        o[pitch + X] = a + q1[32 * c + 1];
+      }
+    }
+  }
+}
+
+// Shared pitches of the block paths for a tile of TW columns (TW a multiple
+// of 32): staged / level-4 rows TW + 63, level-2 rows TW + 61 (both odd).
+template <int TW>
+struct BlockPitch {
+  static constexpr int RS = TW + 63;
+  static constexpr int RA = TW + 61;
+};
+
+template <bool kC, int TW, typename InT, typename AccT>
+__device__ __forceinline__ void fused_block_c(const FusedParams& p, const FusedItem& it, const QuadDesc& Q,
+                                              int32_t tile, AccT* S, AccT* A) {
+  constexpr int RS = BlockPitch<TW>::RS, RA = BlockPitch<TW>::RA;
+  const int32_t u0 = tile * TW;
+  const int32_t span = (1 << it.L) - 1;
+  if (it.kind == FUSED_BY64) {
+    stage_rows<InT, AccT>(p, Q, it.a, 64, u0 - it.c, TW + span, S, RS);
+  } else {
+    stage_gathered<kC, AccT>(p, it, Q, u0 - it.c, TW + span, S, RS);
+  }
+  __syncthreads();
+  const int32_t ncols = min(TW, it.wn - u0);
+  AccT* __restrict__ base = (it.final_ ? static_cast<AccT*>(p.out) : static_cast<AccT*>(p.ws)) + it.dst;
+  switch (it.L) {
+    case 6:
+      merge4_pass_c<1, RS, RA, TW + 60, AccT>(S, A);
+      __syncthreads();
+      merge4_pass_c<4, RA, RS, TW + 48, AccT>(A, S);
+      __syncthreads();
+      final_merge4_c<16, RS, TW, AccT>(it, Q, S, base, u0, ncols);
+      break;
+    case 5:
+      merge2_pass1_c<RS, RA, TW + 30, AccT>(S, A);
+      __syncthreads();
+      merge4_pass_c<2, RA, RS, TW + 24, AccT>(A, S);
+      __syncthreads();
+      final_merge4_c<8, RS, TW, AccT>(it, Q, S, base, u0, ncols);
+      break;
+    case 4:
+      merge4_pass_c<1, RS, RA, TW + 12, AccT>(S, A);
+      __syncthreads();
+      final_merge4_c<4, RA, TW, AccT>(it, Q, A, base, u0, ncols);
+      break;
+    case 3:
+      merge2_pass1_c<RS, RA, TW + 6, AccT>(S, A);
+      __syncthreads();
+      final_merge4_c<2, RA, TW, AccT>(it, Q, A, base, u0, ncols);
+      break;
+    case 2:
+      final_merge4_c<1, RS, TW, AccT>(it, Q, S, base, u0, ncols);
+      break;
+    default:
+      final_merge2_1_c<RS, TW, AccT>(it, Q, S, base, u0, ncols);
+      break;
+  }
+}
+
+// Block path dispatch: the common tile widths run the compile-time variant.
+template <bool kC, typename InT, typename AccT>
+__device__ __forceinline__ void fused_block_any(const FusedParams& p, const FusedItem& it, const QuadDesc& Q,
+                                                int32_t tile, AccT* S, AccT* A) {
+  switch (it.tw) {
+    case 64:
+      fused_block_c<kC, 64, InT, AccT>(p, it, Q, tile, S, A);
+      break;
+    case 128:
+      fused_block_c<kC, 128, InT, AccT>(p, it, Q, tile, S, A);
+      break;
+    case 256:
+      fused_block_c<kC, 256, InT, AccT>(p, it, Q, tile, S, A);
+      break;
+    default:
+      fused_block<kC, InT, AccT>(p, it, Q, tile, S, A);
+      break;
+  }
+}
+
 template <typename AccT>
 __device__ __forceinline__ void store_row(AccT* dst, const RowJob& J, bool fin, int32_t u, AccT v) {
   if (fin) {

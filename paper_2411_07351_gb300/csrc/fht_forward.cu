@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(512, 2) fused_kernel(FusedParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AccT* sm = reinterpret_cast<AccT*>(smem_raw);
   if (it.kind != FUSED_GENERIC) {
-    fused_block<false, InT, AccT>(p, it, Q, tile, sm, sm + (size_t)64 * p.RS);
+    fused_block_any<false, InT, AccT>(p, it, Q, tile, sm, sm + (size_t)64 * p.RS);
   } else {
     fused_generic<InT, AccT>(p, it, Q, tile, sm, sm + (size_t)p.Fm * p.RP);
   }

@@ -42,6 +42,8 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
       // fast path: staged window TW + 63 in S, level-2 rows TW + 60 in A,
       // level-4 rows TW + 48 back in S; reads reach +3, +12 and +48 beyond
       if (it.m != 64 || it.nlev != 6 || it.L != 6) return at("fused", k) + "fast path needs a 64-row block";
+      // the compile-time variants (tile 64, 128, 256) fix the pitches at TW + 63 and TW + 61
+      if (tw != TW || g.RS != TW + 63 || g.RA != TW + 61) return at("fused", k) + "fast-path pitches";
       if (tw + 63 > g.RS || tw + 60 > g.RA || (size_t)64 * (g.RS + g.RA) * P.acc_size > g.smem)
         return at("fused", k) + "fast-path buffers too small";
       if ((tw + 60 - 1) + 3 >= g.RS || (tw + 48 - 1) + 12 >= g.RA || (tw - 1) + 48 >= g.RS)
@@ -118,6 +120,7 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
   for (size_t k = 0; k < P.band_items.size(); k++) {
     const FusedItem& it = P.band_items[k];
     if (!P.bands || it.kind != FUSED_BAND) return at("band", k) + "not a band item";
+    if (it.tw != TW || g.RS != TW + 63 || g.RA != TW + 61) return at("band", k) + "block-path pitches";
     if (it.q < 0 || it.q > 3 || !(P.cfg.quads & (1u << it.q))) return at("band", k) + "bad quadrant";
     const QuadDesc& Q = P.quad[it.q];
     if (it.B < 2 || it.B > 64 || (it.B & (it.B - 1)) || (1 << it.L) != it.B || it.m != 64)
