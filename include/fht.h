@@ -156,6 +156,31 @@ fht_status fht_forward_timed(fht_plan_t plan, const void* d_in, int64_t in_pitch
  *  - Arguments, output and errors as for fht_forward. */
 fht_status fht_forward_noalloc(fht_plan_t plan, const void* d_in, int64_t in_pitch, void* d_out, void* stream);
 
+/* ---- host-memory pipeline ----
+ * Forward transforms of images held in host memory, the copies included:
+ * for callers whose images arrive in, and whose results go back to, host
+ * memory.  The paper has no counterpart (an interface of this library).
+ * fht_pipe_create allocates `depth` device sets (input, output, workspace of
+ * the plan) and 2 + copy_streams blocking streams on the plan's device.
+ * Each fht_pipe_submit takes the next set in turn and enqueues, without
+ * blocking the host: the copy of h_in (h x w elements of the plan's input
+ * type, row pitch in_pitch elements) to the device once the set's previous
+ * output copies have finished; fht_forward; the copy of the packed output
+ * (out_elems elements) to h_out, split over the copy streams.  Consecutive
+ * submits overlap (output copy of image i, transform of i + 1, input copy of
+ * i + 2).  h_in and h_out must stay valid and unchanged (h_in) or unread
+ * (h_out) until fht_pipe_sync returns; page-locked host memory gives
+ * asynchronous copies, pageable memory still works but copies synchronously.
+ * Work recorded on the legacy default stream before (after) a submit runs
+ * before (after) it.  Errors: FHT_ERR_INVALID for bad arguments, FHT_ERR_NOMEM
+ * or FHT_ERR_CUDA from the runtime; fht_pipe_sync waits for every submit. */
+typedef struct fht_pipe_s* fht_pipe_t;
+fht_status fht_pipe_create(fht_pipe_t* pipe, fht_plan_t plan, int32_t depth, int32_t copy_streams);
+fht_status fht_pipe_submit(fht_pipe_t pipe, const void* h_in, int64_t in_pitch, void* h_out);
+fht_status fht_pipe_sync(fht_pipe_t pipe);
+/* Waits for outstanding work, then frees the sets and streams.  NULL is accepted. */
+fht_status fht_pipe_destroy(fht_pipe_t pipe);
+
 /* Adjoint (back-projection): the exact transpose of fht_forward, i.e.
  * d_gin = sum over quadrants of Q^T(d_gout_q), the transpose of Algorithm 1's
  * merge applied level by level in reverse, as gathers (deterministic).

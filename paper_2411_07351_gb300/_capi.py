@@ -67,6 +67,10 @@ SIGNATURES = {
     "fht_queue_status": (ctypes.c_int, [_vp, _vp]),
     "fht_queue_reset_status": (ctypes.c_int, [_vp, _vp]),
     "fht_queue_destroy": (ctypes.c_int, [_vp]),
+    "fht_pipe_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, _i32, _i32]),
+    "fht_pipe_submit": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
+    "fht_pipe_sync": (ctypes.c_int, [_vp]),
+    "fht_pipe_destroy": (ctypes.c_int, [_vp]),
     "fht_ws_status": (ctypes.c_int, [_vp, _vp]),
     "fht_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fht_last_error": (ctypes.c_char_p, []),

@@ -147,6 +147,54 @@ class Plan:
             pass
 
 
+class HostPipeline:
+    """Transforms of images held in host memory (fht_pipe_*): every submit
+    copies the image in, transforms it and copies the packed output back,
+    overlapping with the neighbouring submits.  Host tensors should be
+    pinned (``tensor.pin_memory()``) for the copies to run asynchronously;
+    they must stay alive and unchanged until ``synchronize`` returns."""
+
+    def __init__(self, plan: Plan, depth: int = 2, copy_streams: int = 2):
+        self.plan = plan
+        self._lib = plan._lib
+        h = ctypes.c_void_p()
+        st = self._lib.fht_pipe_create(ctypes.byref(h), plan._h, depth, copy_streams)
+        if st == C.FHT_ERR_NOMEM:
+            torch.cuda.empty_cache()  # the pipe allocates outside PyTorch
+            st = self._lib.fht_pipe_create(ctypes.byref(h), plan._h, depth, copy_streams)
+        C.check(st, "fht_pipe_create")
+        self._h = h
+        self._keep: list = []
+
+    def submit(self, host_in: torch.Tensor, host_out: torch.Tensor):
+        p = self.plan
+        if host_in.is_cuda or host_out.is_cuda:
+            raise ValueError("HostPipeline takes host tensors")
+        if host_in.dtype != p.in_dtype or tuple(host_in.shape) != (p.h, p.w) or host_in.stride(1) != 1:
+            raise ValueError(f"expected a {p.h}x{p.w} {p.in_dtype} host tensor with unit column stride")
+        if host_out.dtype != p.out_dtype or host_out.numel() < p.out_elems or not host_out.is_contiguous():
+            raise ValueError("host output has the wrong size, dtype or layout")
+        C.check(self._lib.fht_pipe_submit(self._h, host_in.data_ptr(), host_in.stride(0), host_out.data_ptr()),
+                "fht_pipe_submit")
+        self._keep.append((host_in, host_out))
+
+    def synchronize(self):
+        C.check(self._lib.fht_pipe_sync(self._h), "fht_pipe_sync")
+        self._keep.clear()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fht_pipe_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class PlanCache:
     """Least-recently-used cache of plans keyed by their full configuration."""
 
