@@ -165,6 +165,76 @@ def oracle_sample_seconds(img, wl, rows: int):
     return time.perf_counter() - t
 
 
+def _oracle_full_image(job):
+    """Worker of the all-core oracle baseline: the full 4-quadrant transform of
+    the seeded workload image, once (a spawned process: no CUDA state)."""
+    h, w, boundary = job
+    import oracle
+    from paper_2411_07351_gb300 import inputs
+
+    img = inputs.c2_image(h=h, w=w)
+    t = time.perf_counter()
+    oracle.fht(img, 15, oracle.EXTENDED if boundary == "extended" else oracle.CYCLIC)
+    return time.perf_counter() - t
+
+
+def cpu_baselines(img, wl, min_seconds: float = 10.0):
+    """The oracle as it stands on the host cores: (1) one core, the full
+    4-quadrant transform of the workload image repeated for >= min_seconds;
+    (2) all cores, one independent full transform per core in spawned
+    processes (the oracle itself is single-threaded)."""
+    import multiprocessing as mp
+
+    import oracle
+
+    h, w = img.shape
+    b = oracle.EXTENDED if wl["boundary"] == "extended" else oracle.CYCLIC
+    runs, t0 = 0, time.perf_counter()
+    while runs == 0 or time.perf_counter() - t0 < min_seconds:
+        oracle.fht(img, 15, b)
+        runs += 1
+    sec1 = time.perf_counter() - t0
+    one = {"value": runs * h * w / sec1 / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"the full {h}x{w} image, 4 quadrants, {runs} runs in {sec1:.1f} s",
+           "cpu": _cpu_model(), "nproc": os.cpu_count()}
+    n = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(n) as pool:
+        pool.map(_oracle_full_image, [(h, w, wl["boundary"])] * n)
+    secn = time.perf_counter() - t0
+    alln = {"value": n * h * w / secn / 1e6, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{n} independent full 4-quadrant transforms of the {h}x{w} image, one per core, "
+                      f"{secn:.1f} s wall including process start", "cpu": _cpu_model(), "nproc": n}
+    return one, alln
+
+
+def per_height_model_bytes(h: int, w: int, ext: bool, in_size: int = 4, acc: int = 4, F: int = 64) -> int:
+    """HBM bytes of the per-height schedule of the Split_T recursion, four
+    quadrants: the image read once per quadrant, every subtree of at most F
+    rows written once, and every node above them reading its two children and
+    writing its own rows (row width L + m - 1 extended, L cyclic)."""
+
+    def split_t(m):
+        p = 1
+        while 2 * p < m:
+            p *= 2
+        return p, m - p
+
+    total = 0
+    for n, L in ((h, w), (h, w), (w, h), (w, h)):
+        def width(m, L=L):
+            return L + m - 1 if ext else L
+
+        def rec(m):
+            if m <= F:
+                return m * width(m) * acc
+            a, b = split_t(m)
+            return rec(a) + rec(b) + (a * width(a) + b * width(b) + m * width(m)) * acc
+
+        total += n * L * in_size + rec(n)
+    return total
+
+
 def _band_rows(per_step_budget_s: float, w: int, h: int) -> int:
     # cost model of one quadrant of a band of r rows: r (w + r) log2 r, 3 s at r = 4095 (measured)
     def est(r):
@@ -328,13 +398,10 @@ def run_fht(args, wl):
     clocks = clocks_stop(clk)
     e2e_value = world * h * w / (e2e_ms * 1e-3) / 1e6
 
-    cpu = None
+    ph_bytes = per_height_model_bytes(h, w, wl["boundary"] == "extended")
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rows = h
-        sec = oracle_sample_seconds(img, wl, rows)
-        cpu = {"value": rows * w / 4.0 / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"quadrant Q0 of the full {h}x{w} image, one run ({sec:.1f} s); "
-                         "value scaled to 4 quadrants", "cpu": _cpu_model(), "nproc": os.cpu_count()}
+        cpu, cpu_all = cpu_baselines(img, wl)
 
     if rank == 0:
         line = {
@@ -351,7 +418,14 @@ def run_fht(args, wl):
                          "algorithmic_bytes_per_launch": dk["model_bytes"] / dk["launches"]},
             "kernels": kernels,
             "model_bytes_per_step": int(plan.info.model_bytes), "ideal_bytes_per_step": int(plan.info.ideal_bytes),
+            "step_roofline": {
+                "per_height_model_bytes": ph_bytes, "achieved": ph_bytes / (ms * 1e-3) / 1e9, "peak": peak,
+                "unit": "GB/s", "frac": ph_bytes / (ms * 1e-3) / 1e9 / peak,
+                "note": "bytes the per-height schedule (64-row fused subtrees, one pass per upper tree height) "
+                        "moves per step, over the measured step time; this build's own schedule moves "
+                        "model_bytes_per_step"},
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
             "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
                     "api": "fht_pipe_submit, 2 device sets, copies on their own streams",
                     "h2d_bytes_per_step": int(host_in.numel() * host_in.element_size()),

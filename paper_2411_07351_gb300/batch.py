@@ -38,12 +38,15 @@ class BatchQueue:
                               tile_cols=BATCH_TILE_COLS)
 
     def submit(self, images, quads: int = C.FHT_QALL, boundary: str = "cyclic", split: str = "T",
-               outs=None, workspaces=None, stream=None, flags=None, tags=None):
+               outs=None, workspaces=None, stream=None, flags=None, tags=None, plans=None):
         """Enqueue one persistent launch over `images` (2-D CUDA tensors of one dtype).
 
+        `plans` may give each image's plan (made by the caller for that shape,
+        quadrants, boundary and split); otherwise they come from this queue's cache.
         Returns (outputs, plans, workspaces); outputs are the packed quadrants of each image."""
         n = len(images)
-        plans = [self.plan_for(x, quads, boundary, split) for x in images]
+        if plans is None:
+            plans = [self.plan_for(x, quads, boundary, split) for x in images]
         if outs is None:
             outs = [p.new_output() for p in plans]
         if workspaces is None:

@@ -76,22 +76,114 @@ __global__ void __launch_bounds__(256) upper_kernel(const RowJob* __restrict__ r
   }
 }
 
+// Zeros that stand in for a part row wherever a spine term lies wholly
+// outside its part for a column tile (zero-initialised static storage).
+__device__ __align__(16) unsigned char g_spine_zero[kSpineTilePlain * sizeof(double)];
+
+// Fast tile of a spine row group: every term of every row is, over this
+// column tile, either wholly inside its part row (one contiguous stretch) or
+// wholly outside it (zeros), so each load is a plain pointer + constant.
+template <bool kMap, int NT, int QPT, typename AccT>
+__device__ __forceinline__ void spine_fast_load(const AccT* const* tp, AccT (&v)[NT][QPT]) {
+#pragma unroll
+  for (int c = 0; c < NT; c++) {
+    const AccT* __restrict__ p = tp[c] + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < QPT; q++) v[c][q] = __ldg(p + q * 256);
+  }
+}
+
+template <bool kMap, int NT, int QPT, typename AccT>
+__device__ __forceinline__ void spine_fast_group(const SpineRow* sr, const AccT* const (*tp)[kMaxSpineTerms],
+                                                 int32_t nr, int32_t W, int32_t sigma, int32_t kappa, AccT* out,
+                                                 int32_t u0) {
+  AccT a[NT][QPT], b[NT][QPT];
+  spine_fast_load<kMap, NT, QPT, AccT>(tp[0], a);
+  for (int32_t r = 0; r < nr; r += 2) {
+    if (r + 1 < nr) spine_fast_load<kMap, NT, QPT, AccT>(tp[r + 1], b);
+    spine_store<kMap, NT, 256, QPT, AccT>(W, sigma, kappa, out + sr[r].dst, u0, a);
+    if (r + 1 >= nr) break;
+    if (r + 2 < nr) spine_fast_load<kMap, NT, QPT, AccT>(tp[r + 2], a);
+    spine_store<kMap, NT, 256, QPT, AccT>(W, sigma, kappa, out + sr[r + 1].dst, u0, b);
+  }
+}
+
 template <typename AccT>
-__global__ void __launch_bounds__(256, sizeof(AccT) > 4 ? 1 : 3) spine_kernel(const SpineRow* __restrict__ rows, int64_t nrows,
-                                                   const SpineTerm* __restrict__ terms, const AccT* __restrict__ ws,
-                                                   AccT* __restrict__ out, AccT* inner, QuadDescs quads) {
+__global__ void __launch_bounds__(256, sizeof(AccT) > 4 ? 1 : 3) spine_kernel(const SpineRow* __restrict__ rows,
+                                                   int64_t nrows, const SpineTerm* __restrict__ terms,
+                                                   const AccT* __restrict__ ws, AccT* __restrict__ out, AccT* inner,
+                                                   QuadDescs quads) {
   __shared__ SpineTerm st[kSpineRows][kMaxSpineTerms];
   __shared__ SpineRow sr[kSpineRows];
+  __shared__ const AccT* tp[kSpineRows][kMaxSpineTerms];
+  __shared__ int32_t s_straddle;
   const int64_t r0 = (int64_t)blockIdx.x * kSpineRows;
   const int32_t u0 = blockIdx.y * kSpineTilePlain;
   const int32_t nr = (int32_t)(nrows - r0 < kSpineRows ? nrows - r0 : kSpineRows);
   if (threadIdx.x < nr) sr[threadIdx.x] = rows[r0 + threadIdx.x];
+  if (threadIdx.x == 0) s_straddle = 0;
   __syncthreads();
   for (int32_t idx = threadIdx.x; idx < nr * kMaxSpineTerms; idx += blockDim.x) {
     const int32_t r = idx / kMaxSpineTerms, c = idx % kMaxSpineTerms;
     if (c < sr[r].term_count) st[r][c] = terms[sr[r].term_begin + c];
   }
+  // one row geometry for the whole group (same quadrant, kind and term count)
+  bool uniform = nr > 0 && sr[0].term_count <= 8;
+  for (int32_t r = 1; r < nr; r++)
+    uniform = uniform && sr[r].q == sr[0].q && sr[r].term_count == sr[0].term_count && sr[r].flags == sr[0].flags;
+  const QuadDesc& Q = quads.q[sr[0].q];
+  const bool is_inner = sr[0].flags & SPINE_INNER;
+  const int32_t W = is_inner ? sr[0].w : Q.W;
+  const bool fast_tile = uniform && u0 + kSpineTilePlain <= W;
   __syncthreads();
+  if (fast_tile) {
+    // classify every term over this tile: inside its part row, outside it, or across an edge
+    const AccT* zero = reinterpret_cast<const AccT*>(g_spine_zero);
+    for (int32_t idx = threadIdx.x; idx < nr * kMaxSpineTerms; idx += blockDim.x) {
+      const int32_t r = idx / kMaxSpineTerms, c = idx % kMaxSpineTerms;
+      if (c >= sr[r].term_count) continue;
+      const SpineTerm T = st[r][c];
+      const int32_t lo = u0 + T.off, hi = lo + kSpineTilePlain;
+      const AccT* p = nullptr;
+      if (Q.ext) {
+        if (lo >= 0 && hi <= T.wpart) p = ws + T.row + lo;
+        else if (hi <= 0 || lo >= T.wpart) p = zero;
+      } else {
+        if (hi <= W) p = ws + T.row + lo;          // no wrap inside the tile
+        else if (lo >= W) p = ws + T.row + lo - W; // the whole tile wraps
+      }
+      tp[r][c] = p;
+      if (!p) s_straddle = 1;
+    }
+    __syncthreads();
+  }
+  if (fast_tile && !s_straddle) {
+    if (is_inner) {
+      switch (sr[0].term_count) {
+#define FHT_SPINE_FAST(N)                                                                               \
+  case N:                                                                                               \
+    spine_fast_group<false, N, kSpineQPT, AccT>(sr, tp, nr, W, 1, 0, inner, u0);                        \
+    return;
+        FHT_SPINE_FAST(1) FHT_SPINE_FAST(2) FHT_SPINE_FAST(3) FHT_SPINE_FAST(4) FHT_SPINE_FAST(5)
+        FHT_SPINE_FAST(6) FHT_SPINE_FAST(7) FHT_SPINE_FAST(8)
+#undef FHT_SPINE_FAST
+        default:
+          break;
+      }
+    } else {
+      switch (sr[0].term_count) {
+#define FHT_SPINE_FAST(N)                                                                               \
+  case N:                                                                                               \
+    spine_fast_group<true, N, kSpineQPT, AccT>(sr, tp, nr, W, Q.sigma, Q.kappa, out, u0);               \
+    return;
+        FHT_SPINE_FAST(1) FHT_SPINE_FAST(2) FHT_SPINE_FAST(3) FHT_SPINE_FAST(4) FHT_SPINE_FAST(5)
+        FHT_SPINE_FAST(6) FHT_SPINE_FAST(7) FHT_SPINE_FAST(8)
+#undef FHT_SPINE_FAST
+        default:
+          break;
+      }
+    }
+  }
   spine_rows_tile<false, 256, kSpineQPT, AccT, kSpinePipe>(sr, st, nr, quads.q, ws, out, inner, u0);
 }
 

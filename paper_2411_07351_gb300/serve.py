@@ -210,7 +210,7 @@ class Server:
                     self.by_rid[r.rid] = r
                 self.queues[slot].submit([r.image for r in reqs], self.quads, self.boundary, self.split,
                                          outs=[r.out for r in reqs], workspaces=[r.ws for r in reqs], stream=s,
-                                         tags=[r.rid for r in reqs])
+                                         tags=[r.rid for r in reqs], plans=[r.plan for r in reqs])
                 ev = torch.cuda.Event()
                 ev.record(s)
             self.running.append(_Batch(ev, reqs, slot, s))

@@ -67,6 +67,24 @@ def test_batch_mixed_sizes_and_order(F, queue, boundary):
         assert torch.equal(outs2[k], ref[i])
 
 
+@pytest.mark.parametrize("boundary", ["cyclic", "extended"])
+def test_batch_chunked_spines_and_tall_roots(F, orc, queue, boundary):
+    # spines of several chunks (one phase per chunk in the persistent launch)
+    # and a root taller than 8192 rows (its big part summed first)
+    g = np.random.default_rng(11)
+    sizes = [(2047, 50), (50, 2047), (1500, 33), (9000, 3), (3, 9000), (700, 700)]
+    xs = [torch.from_numpy(g.integers(0, 256, s, dtype=np.uint8)).cuda() for s in sizes]
+    outs, plans, _ = queue.submit(xs, 15, boundary)
+    torch.cuda.synchronize()
+    assert queue.status() == 0
+    for x, o, p in zip(xs, outs, plans):
+        assert torch.equal(o, p.forward(x))
+    b = orc.EXTENDED if boundary == "extended" else orc.CYCLIC
+    for k in (0, 3):
+        im = xs[k].cpu().numpy().astype(np.int64)
+        assert np.array_equal(outs[k].cpu().numpy(), orc.fht(im, 15, b))
+
+
 def test_batch_float_and_split_s(F, queue):
     g = np.random.default_rng(8)
     xs = [torch.from_numpy(g.standard_normal(s).astype(np.float32)).cuda() for s in [(70, 90), (300, 129), (33, 500)]]
