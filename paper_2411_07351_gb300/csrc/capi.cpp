@@ -72,6 +72,8 @@ cudaError_t upload_tables(fht_plan_s* p) {
   tp.add(&d.band_items, h.band_items);
   tp.add(&d.spine_rows, h.spine_rows);
   tp.add(&d.spine_terms, h.spine_terms);
+  tp.add(&d.spine_segs, h.spine_segs);
+  tp.add(&d.spine_grps, h.spine_grps);
   if (h.has_adjoint) {
     tp.add(&d.arows, h.arows);
     tp.add(&d.aterms, h.aterms);
@@ -110,6 +112,8 @@ void free_dev(fht_plan_s* p) {
   d.band_items = nullptr;
   d.spine_rows = nullptr;
   d.spine_terms = nullptr;
+  d.spine_segs = nullptr;
+  d.spine_grps = nullptr;
 }
 
 }  // namespace

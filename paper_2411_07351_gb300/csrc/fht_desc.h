@@ -111,6 +111,31 @@ struct SpineTerm {
   int64_t row;        // workspace offset of the part's row r_p(t)
   int32_t wpart;      // part row width
   int32_t off;        // column offset (reduced to [0, W) in the cyclic case)
+  int32_t sofs;       // staged spine kernel: shared-memory element of this term's column u0
+  int32_t pad;
+};
+
+// Staged spine kernel: the rows of one 16-row group read a handful of part
+// rows (consecutive slopes share them), each over a window a few columns
+// wider than the column tile.  The group's distinct (part row, offset range)
+// pairs are its segments; a CTA copies each segment's window into shared
+// memory once, then sums every term from there.
+constexpr int kMaxSpineTerms = 16;      // terms of one spine row
+constexpr int kSpineRows = 16;          // spine rows per CTA (a 16-row group)
+constexpr int32_t kStageTile = 512;     // columns per CTA
+constexpr int32_t kStageMaxSegs = 64;   // segments per 16-row group
+constexpr int32_t kStageMaxSpan = 64;   // offsets merged into one segment differ by at most this
+
+struct SpineSeg {
+  int64_t row;        // workspace offset of the part row
+  int32_t wpart;      // part row width (the row length W in the cyclic case)
+  int32_t a_off;      // the window starts at part column u0 + a_off (a multiple of 16 bytes)
+  int32_t len;        // window length (elements, a multiple of 16 bytes)
+  int32_t smem;       // first shared-memory element of the window (16-byte aligned)
+};
+
+struct SpineGrp {
+  int32_t seg_begin, seg_count;
 };
 
 // One row of one level of a fused program: dst row <- src[top] + src[bot] shifted by s.

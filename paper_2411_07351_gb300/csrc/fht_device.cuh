@@ -142,6 +142,66 @@ __device__ __forceinline__ void stage_rows(const FusedParams& p, const QuadDesc&
   }
 }
 
+// Asynchronous copies into shared memory (cp.async): the copy engine of the
+// SM writes shared memory directly, so a thread can have all of its staging
+// copies in flight at once without holding them in registers.  With
+// src_bytes = 0 nothing is read and the destination is zero-filled.
+__device__ __forceinline__ void cp_async_4(void* smem_dst, const void* gmem_src, int32_t src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gmem_src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_8(void* smem_dst, const void* gmem_src, int32_t src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gmem_src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem_z(T* smem_dst, const T* gmem_src, bool valid) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  if constexpr (sizeof(T) == 8) {
+    cp_async_8(smem_dst, gmem_src, valid ? 8 : 0);
+  } else {
+    cp_async_4(smem_dst, gmem_src, valid ? 4 : 0);
+  }
+}
+
+// stage_gathered with cp.async (plain kernels only: the copies go through L1,
+// which the persistent batch kernel must not use for data written in the
+// same launch).  Same layout as stage_gathered.
+template <typename AccT>
+__device__ __forceinline__ void stage_gathered_async(const FusedParams& p, const FusedItem& it, const QuadDesc& Q,
+                                                     int32_t x0, int32_t width, AccT* buf, int32_t rp) {
+  const AccT* __restrict__ ws = static_cast<const AccT*>(p.ws);
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t nwarps = blockDim.x >> 5;
+  const int32_t lim = Q.ext ? it.wsrc : Q.W;
+  for (int32_t r = warp; r < 64; r += nwarps) {
+    const int32_t g = r / it.B, b = r - g * it.B;
+    const int32_t K = it.K0 + g;
+    const AccT* __restrict__ row = ws + it.src + (int64_t)(64 * b + K) * it.src_pitch;
+    const int32_t base = x0 + K * b + it.c_src;  // >= 0 in the cyclic case
+    AccT* dst = buf + (size_t)r * rp;
+    if (base >= 0 && base + width <= lim) {
+      for (int32_t j = lane; j < width; j += 32) cp_async_elem_z<AccT>(dst + j, row + base + j, true);
+    } else {
+      for (int32_t j = lane; j < width; j += 32) {
+        int32_t z = base + j;
+        bool ok = true;
+        if (Q.ext) {
+          ok = z >= 0 && z < it.wsrc;
+        } else {
+          z = z % Q.W;
+        }
+        cp_async_elem_z<AccT>(dst + j, ok ? row + z : row, ok);
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
 // Store rows [0, m) x columns [0, ncols) of a shared buffer as the node's
 // Hough rows starting at node column u0.
 template <typename AccT>
@@ -594,7 +654,10 @@ __device__ __forceinline__ void fused_block_c(const FusedParams& p, const FusedI
   const int32_t u0 = tile * TW;
   const int32_t span = (1 << it.L) - 1;
   if (it.kind == FUSED_BY64) {
+    // register staging: measured faster than cp.async for the input window
     stage_rows<InT, AccT>(p, Q, it.a, 64, u0 - it.c, TW + span, S, RS);
+  } else if constexpr (!kC) {
+    stage_gathered_async<AccT>(p, it, Q, u0 - it.c, TW + span, S, RS);
   } else {
     stage_gathered<kC, AccT>(p, it, Q, u0 - it.c, TW + span, S, RS);
   }
@@ -672,8 +735,6 @@ __device__ __forceinline__ void store_row(AccT* dst, const RowJob& J, bool fin, 
 // row before adding (term count fixed at compile time per row).  The rows of
 // a CTA read neighbouring rows of the same parts at nearby offsets, so most
 // part reads hit L1; consecutive CTAs share rows through L2.
-constexpr int kMaxSpineTerms = 16;
-constexpr int kSpineRows = 16;
 constexpr int kSpineTile = 1024;  // batched kernel: 256 threads x 4 columns
 // plain spine kernel: 256 threads x kSpineQPT columns per row tile
 constexpr int kSpineQPT = 4;

@@ -187,6 +187,177 @@ __global__ void __launch_bounds__(256, sizeof(AccT) > 4 ? 1 : 3) spine_kernel(co
   spine_rows_tile<false, 256, kSpineQPT, AccT, kSpinePipe>(sr, st, nr, quads.q, ws, out, inner, u0);
 }
 
+// ---- staged spine kernel ----
+// One CTA = one 16-row group x one tile of kStageTile columns.  The group's
+// segments (distinct part-row windows) are copied into shared memory with
+// cp.async: 16-byte chunks whose bytes beyond the part row are zero-filled by
+// the copy itself (extended), or element by element with the cyclic wrap;
+// then every output element is the sum of its terms read from shared memory.
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gmem_src, int32_t src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem_src), "r"(src_bytes) : "memory");
+}
+
+template <typename AccT>
+__device__ __forceinline__ void cp_async_elem(AccT* smem_dst, const AccT* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  if constexpr (sizeof(AccT) == 8) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+  }
+}
+
+constexpr int kStageThreads = 128;
+constexpr int kStageQPT = kStageTile / kStageThreads;
+
+// Per-row constants of a staged CTA, set once by the prologue.
+template <typename AccT>
+struct StagedRow {
+  AccT* dst;      // output row (root) or inner-node row (workspace)
+  int32_t W;      // row length
+  int32_t sigma;  // column map X = (sigma u + kappa) mod W; sigma = 0: X = u
+  int32_t kappa;
+  int32_t pad;
+};
+
+template <int NT, typename AccT>
+__device__ __forceinline__ void staged_rows(const AccT* S, const int32_t (*so)[kMaxSpineTerms],
+                                            const StagedRow<AccT>* ri, int32_t nr, int32_t u0) {
+  for (int32_t r = 0; r < nr; r++) {
+    const StagedRow<AccT> R = ri[r];
+    if (u0 >= R.W) continue;
+    int32_t o[NT];
+#pragma unroll
+    for (int c = 0; c < NT; c++) o[c] = so[r][c] + (int32_t)threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < kStageQPT; q++) {
+      const int32_t u = u0 + q * kStageThreads + (int32_t)threadIdx.x;
+      AccT acc = S[o[0] + q * kStageThreads];
+#pragma unroll
+      for (int c = 1; c < NT; c++) acc += S[o[c] + q * kStageThreads];
+      if (u < R.W) {
+        int32_t X = u;
+        if (R.sigma != 0) {
+          X = R.sigma * u + R.kappa;
+          if (X < 0) X += R.W;
+          if (X >= R.W) X -= R.W;
+        }
+        R.dst[X] = acc;
+      }
+    }
+  }
+}
+
+template <typename AccT>
+__global__ void __launch_bounds__(kStageThreads) spine_staged_kernel(const SpineRow* __restrict__ rows, int64_t nrows,
+                                                           const SpineTerm* __restrict__ terms,
+                                                           const SpineGrp* __restrict__ grps,
+                                                           const SpineSeg* __restrict__ segs,
+                                                           const AccT* __restrict__ ws, AccT* __restrict__ out,
+                                                           AccT* inner, QuadDescs quads) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AccT* S = reinterpret_cast<AccT*>(smem_raw);
+  __shared__ StagedRow<AccT> ri[kSpineRows];
+  __shared__ int32_t tc[kSpineRows];
+  __shared__ __align__(16) int32_t so[kSpineRows][kMaxSpineTerms];
+  __shared__ SpineSeg sg[kStageMaxSegs];
+  constexpr int32_t EPC = 16 / (int32_t)sizeof(AccT);
+  const int64_t r0 = (int64_t)blockIdx.x * kSpineRows;
+  const int32_t u0 = blockIdx.y * kStageTile;
+  const int32_t nr = (int32_t)(nrows - r0 < kSpineRows ? nrows - r0 : kSpineRows);
+  const SpineGrp G = grps[blockIdx.x];
+  if ((int32_t)threadIdx.x < nr) {
+    const SpineRow R = rows[r0 + threadIdx.x];
+    const QuadDesc& Q = quads.q[R.q];
+    const bool is_inner = R.flags & SPINE_INNER;
+    StagedRow<AccT> o;
+    o.dst = (is_inner ? inner : out) + R.dst;
+    o.W = is_inner ? R.w : Q.W;
+    o.sigma = is_inner ? 0 : Q.sigma;
+    o.kappa = Q.kappa;
+    o.pad = 0;
+    ri[threadIdx.x] = o;
+    tc[threadIdx.x] = R.term_count;
+    for (int32_t c = 0; c < R.term_count; c++) so[threadIdx.x][c] = terms[R.term_begin + c].sofs;
+  }
+  for (int32_t s = threadIdx.x; s < G.seg_count; s += blockDim.x) sg[s] = segs[G.seg_begin + s];
+  __syncthreads();
+  // nothing to do for a tile right of every row of the group
+  int32_t wmax = 0;
+  bool uniform = true;
+  for (int32_t r = 0; r < nr; r++) {
+    wmax = ri[r].W > wmax ? ri[r].W : wmax;
+    uniform = uniform && tc[r] == tc[0];
+  }
+  if (u0 >= wmax) return;
+  const bool ext = quads.q[0].ext | quads.q[1].ext | quads.q[2].ext | quads.q[3].ext;
+  // stage the windows
+  for (int32_t s = 0; s < G.seg_count; s++) {
+    const SpineSeg g = sg[s];
+    const AccT* __restrict__ rowp = ws + g.row;
+    const int32_t A = u0 + g.a_off;
+    AccT* dst = S + g.smem;
+    if (ext) {
+      // chunks start at multiples of 16 bytes of the part row (rows are 128-byte aligned)
+      for (int32_t k = threadIdx.x; k < g.len / EPC; k += blockDim.x) {
+        const int32_t i0 = A + k * EPC;
+        int32_t bytes = 0;
+        const AccT* src = rowp;
+        if (i0 >= 0 && i0 < g.wpart) {
+          bytes = (g.wpart - i0 < EPC ? g.wpart - i0 : EPC) * (int32_t)sizeof(AccT);
+          src = rowp + i0;
+        }
+        cp_async_16(dst + k * EPC, src, bytes);
+      }
+    } else if (g.wpart % EPC == 0) {
+      for (int32_t k = threadIdx.x; k < g.len / EPC; k += blockDim.x) {
+        int32_t i0 = A + k * EPC;
+        if (i0 >= g.wpart) i0 -= g.wpart;
+        if (i0 >= g.wpart) i0 %= g.wpart;  // a tile past this quadrant's rows (mixed groups)
+        cp_async_16(dst + k * EPC, rowp + i0, 16);
+      }
+    } else {
+      for (int32_t k = threadIdx.x; k < g.len; k += blockDim.x) {
+        int32_t i = A + k;
+        if (i >= g.wpart) i -= g.wpart;
+        if (i >= g.wpart) i %= g.wpart;
+        cp_async_elem<AccT>(dst + k, rowp + i);
+      }
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (uniform) {
+    switch (tc[0]) {
+#define FHT_STAGED(N)                                        \
+  case N:                                                    \
+    staged_rows<N, AccT>(S, so, ri, nr, u0);                 \
+    return;
+      FHT_STAGED(1) FHT_STAGED(2) FHT_STAGED(3) FHT_STAGED(4) FHT_STAGED(5) FHT_STAGED(6) FHT_STAGED(7)
+      FHT_STAGED(8)
+#undef FHT_STAGED
+      default:
+        break;
+    }
+  }
+  // mixed or long rows: one row at a time
+  for (int32_t r = 0; r < nr; r++) {
+    switch (tc[r]) {
+#define FHT_STAGED1(N)                                                       \
+  case N:                                                                    \
+    staged_rows<N, AccT>(S, so + r, ri + r, 1, u0);                          \
+    break;
+      FHT_STAGED1(1) FHT_STAGED1(2) FHT_STAGED1(3) FHT_STAGED1(4) FHT_STAGED1(5) FHT_STAGED1(6)
+      FHT_STAGED1(7) FHT_STAGED1(8) FHT_STAGED1(9) FHT_STAGED1(10) FHT_STAGED1(11) FHT_STAGED1(12)
+      FHT_STAGED1(13) FHT_STAGED1(14) FHT_STAGED1(15) FHT_STAGED1(16)
+#undef FHT_STAGED1
+      default:
+        break;
+    }
+  }
+}
+
 // ------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------
@@ -292,11 +463,21 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
     for (size_t p = 0; p + 1 < P.spine_pass_begin.size(); p++) {
       const int64_t b = P.spine_pass_begin[p], n = P.spine_pass_begin[p + 1] - b;
       if (n <= 0) continue;
-      dim3 sgrid((unsigned)((n + kSpineRows - 1) / kSpineRows),
-                 (unsigned)((maxW + kSpineTilePlain - 1) / kSpineTilePlain));
+      const unsigned groups = (unsigned)((n + kSpineRows - 1) / kSpineRows);
       mark(0);
-      spine_kernel<AccT><<<sgrid, 256, 0, st>>>(D.spine_rows + b, n, D.spine_terms, wsa, static_cast<AccT*>(out),
-                                                wsa, qd);
+      if (P.spine_pass_smem[p] > 0) {
+        const size_t smem = (size_t)P.spine_pass_smem[p] * sizeof(AccT);
+        auto kst = spine_staged_kernel<AccT>;
+        if ((e = cudaFuncSetAttribute(kst, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+          return e;
+        dim3 sgrid(groups, (unsigned)((maxW + kStageTile - 1) / kStageTile));
+        kst<<<sgrid, kStageThreads, smem, st>>>(D.spine_rows + b, n, D.spine_terms, D.spine_grps + P.spine_grp_begin[p],
+                                      D.spine_segs, wsa, static_cast<AccT*>(out), wsa, qd);
+      } else {
+        dim3 sgrid(groups, (unsigned)((maxW + kSpineTilePlain - 1) / kSpineTilePlain));
+        spine_kernel<AccT><<<sgrid, 256, 0, st>>>(D.spine_rows + b, n, D.spine_terms, wsa,
+                                                  static_cast<AccT*>(out), wsa, qd);
+      }
       mark(1);
       launch++;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;

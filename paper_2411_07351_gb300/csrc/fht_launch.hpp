@@ -24,6 +24,8 @@ struct DevicePlan {
   FusedItem* band_items = nullptr;
   SpineRow* spine_rows = nullptr;
   SpineTerm* spine_terms = nullptr;
+  SpineSeg* spine_segs = nullptr;
+  SpineGrp* spine_grps = nullptr;
   AdjRow* arows = nullptr;
   AdjTerm* aterms = nullptr;
   int32_t* aptr = nullptr;

@@ -192,6 +192,81 @@ static int32_t bi_width(const PlanConfig& cfg, const QuadDesc& Q, int32_t m) {
 static int32_t dtype_in_size(int32_t dt) { return dt == 0 ? 1 : dt == 3 ? 8 : 4; }
 static int32_t dtype_acc_size(int32_t dt) { return dt == 3 ? 8 : 4; }
 
+// Segments of the staged spine kernel, pass by pass and 16-row group by
+// group (the grouping of the kernel's CTAs).  Terms of one group that read
+// the same part row at offsets within kStageMaxSpan of each other share one
+// window [u0 + a_off, u0 + a_off + len) of that row; every term records where
+// its column u0 lands in the group's shared buffer (sofs).  A pass whose
+// largest group needs more than kStageSmemMax bytes, or whose cyclic rows are
+// too short for the window arithmetic, keeps the unstaged kernel.
+static constexpr size_t kStageSmemMax = 96 << 10;
+
+static void build_spine_staging(HostPlan& P) {
+  const int32_t acc = P.acc_size;
+  const int32_t epc = 16 / acc;  // elements per 16-byte chunk
+  auto floor_to = [](int64_t a, int64_t m) { return a >= 0 ? a / m * m : -((-a + m - 1) / m) * m; };
+  auto ceil_to = [](int64_t a, int64_t m) { return (a + m - 1) / m * m; };
+  P.spine_grp_begin.push_back(0);
+  for (size_t p = 0; p + 1 < P.spine_pass_begin.size(); p++) {
+    const int64_t b = P.spine_pass_begin[p], e = P.spine_pass_begin[p + 1];
+    int64_t need = 0;
+    bool ok = true;
+    for (int64_t g0 = b; g0 < e; g0 += kSpineRows) {
+      const int64_t g1 = std::min<int64_t>(e, g0 + kSpineRows);
+      struct Seg {
+        int64_t row;
+        int32_t wpart, lo, hi;
+      };
+      std::vector<Seg> segs;
+      std::vector<std::pair<int64_t, int32_t>> member;  // term index -> segment
+      for (int64_t r = g0; r < g1; r++) {
+        const SpineRow& R = P.spine_rows[r];
+        const QuadDesc& Q = P.quad[R.q];
+        if (!Q.ext && Q.W < kStageTile + 4 * kStageMaxSpan) ok = false;
+        for (int32_t c = 0; c < R.term_count; c++) {
+          const int64_t ti = R.term_begin + c;
+          const SpineTerm& T = P.spine_terms[ti];
+          int32_t k = 0;
+          for (; k < (int32_t)segs.size(); k++) {
+            Seg& S = segs[k];
+            if (S.row == T.row && T.off >= S.hi - kStageMaxSpan && T.off <= S.lo + kStageMaxSpan) {
+              S.lo = std::min(S.lo, T.off);
+              S.hi = std::max(S.hi, T.off);
+              break;
+            }
+          }
+          if (k == (int32_t)segs.size()) segs.push_back({T.row, T.wpart, T.off, T.off});
+          member.emplace_back(ti, k);
+        }
+      }
+      if ((int32_t)segs.size() > kStageMaxSegs) ok = false;
+      SpineGrp G;
+      G.seg_begin = (int32_t)P.spine_segs.size();
+      G.seg_count = (int32_t)segs.size();
+      int64_t smem = 0;
+      for (const Seg& S : segs) {
+        SpineSeg o;
+        o.row = S.row;
+        o.wpart = S.wpart;
+        o.a_off = (int32_t)floor_to(S.lo, epc);
+        o.len = (int32_t)ceil_to((int64_t)S.hi + kStageTile - o.a_off, epc);
+        o.smem = (int32_t)smem;
+        smem += o.len;
+        P.spine_segs.push_back(o);
+      }
+      for (const auto& m : member) {
+        SpineTerm& T = P.spine_terms[m.first];
+        const SpineSeg& o = P.spine_segs[G.seg_begin + m.second];
+        T.sofs = o.smem + (T.off - o.a_off);
+      }
+      P.spine_grps.push_back(G);
+      need = std::max(need, smem);
+    }
+    P.spine_grp_begin.push_back((int64_t)P.spine_grps.size());
+    P.spine_pass_smem.push_back(ok && (size_t)need * acc <= kStageSmemMax ? (int32_t)need : 0);
+  }
+}
+
 std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
   if (cfg.h < 1 || cfg.w < 1 || cfg.h > 65535 || cfg.w > 65535) return "h and w must be in [1, 65535]";
   if (cfg.dtype < 0 || cfg.dtype > 3) return "unknown dtype";
@@ -663,6 +738,7 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
     P.spine_pass_bytes.push_back(spine_levels_bytes[c]);
     P.spine_bytes += spine_levels_bytes[c];
   }
+  build_spine_staging(P);
   // tiles: fast-path items use tile_cols; generic items (two ping-pong
   // buffers of up to 63 rows) use half of it, so their shared windows stay
   // no larger than the fast path's

@@ -108,6 +108,12 @@ struct HostPlan {
   std::vector<SpineTerm> spine_terms;
   std::vector<int64_t> spine_pass_begin;  // spine_rows[spine_pass_begin[k] .. spine_pass_begin[k+1])
   std::vector<int64_t> spine_pass_bytes;
+  // staged spine kernel: per pass, its 16-row groups (spine_grps[spine_grp_begin[k] ..]) and the
+  // shared-memory elements the largest group needs (0: the pass runs the unstaged kernel)
+  std::vector<SpineSeg> spine_segs;
+  std::vector<SpineGrp> spine_grps;
+  std::vector<int64_t> spine_grp_begin;
+  std::vector<int32_t> spine_pass_smem;
   int32_t max_band_ntiles = 0;
   int64_t band_bytes = 0, spine_bytes = 0;
   int32_t max_spine_terms = 0;

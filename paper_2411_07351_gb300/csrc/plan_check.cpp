@@ -203,6 +203,47 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
     }
     for (const auto& w : wr) inner_written.insert(w.first);
   }
+  // staged spine kernel: windows inside the workspace and the shared buffer,
+  // every term's tile inside a window of its own part row
+  if (!P.spine_rows.empty() && (P.spine_pass_smem.size() + 1 != P.spine_pass_begin.size() ||
+                                P.spine_grp_begin.size() != P.spine_pass_begin.size()))
+    return "staged spine tables do not match the passes";
+  const int32_t epc = 16 / P.acc_size;
+  for (size_t p = 0; p + 1 < P.spine_pass_begin.size(); p++) {
+    if (P.spine_pass_smem[p] <= 0) continue;
+    const int64_t b = P.spine_pass_begin[p], e = P.spine_pass_begin[p + 1];
+    const int64_t ng = (e - b + kSpineRows - 1) / kSpineRows;
+    if (P.spine_grp_begin[p + 1] - P.spine_grp_begin[p] != ng) return "staged spine: group count";
+    for (int64_t g = 0; g < ng; g++) {
+      const SpineGrp& G = P.spine_grps[P.spine_grp_begin[p] + g];
+      if (G.seg_count < 1 || G.seg_count > kStageMaxSegs || G.seg_begin < 0 ||
+          (size_t)G.seg_begin + G.seg_count > P.spine_segs.size())
+        return "staged spine: segments of group " + std::to_string(g);
+      for (int32_t s = 0; s < G.seg_count; s++) {
+        const SpineSeg& S = P.spine_segs[G.seg_begin + s];
+        if (S.smem % epc || S.len % epc || S.a_off % epc || S.row % epc || S.smem < 0 || S.len < kStageTile ||
+            (int64_t)S.smem + S.len > P.spine_pass_smem[p])
+          return "staged spine: window layout";
+        if (S.row < 0 || S.wpart < 1 || S.row + S.wpart > ws_elems) return "staged spine: window row";
+      }
+      const int64_t r1 = std::min<int64_t>(e, b + (g + 1) * kSpineRows);
+      for (int64_t r = b + g * kSpineRows; r < r1; r++) {
+        const SpineRow& R = P.spine_rows[r];
+        const QuadDesc& Q = P.quad[R.q];
+        for (int32_t c = 0; c < R.term_count; c++) {
+          const SpineTerm& T = P.spine_terms[R.term_begin + c];
+          bool found = false;
+          for (int32_t s = 0; s < G.seg_count && !found; s++) {
+            const SpineSeg& S = P.spine_segs[G.seg_begin + s];
+            found = S.row == T.row && S.wpart == T.wpart && T.sofs - S.smem == T.off - S.a_off &&
+                    T.sofs >= S.smem && T.sofs + kStageTile <= S.smem + S.len;
+          }
+          if (!found) return at("staged spine", r) + "term outside its window";
+          if (!Q.ext && Q.W < kStageTile + 4 * kStageMaxSpan) return at("staged spine", r) + "cyclic row too short";
+        }
+      }
+    }
+  }
 
   // ---- adjoint ----
   if (!P.has_adjoint) return "";

@@ -90,7 +90,7 @@ def test_awkward_sizes_u8(F, orc, boundary):
             check_exact(F, orc, img, 15, boundary)
 
 
-@pytest.mark.parametrize("h,w", [(511, 300), (4095, 33), (4097, 17), (33, 4097), (1000, 1000)])
+@pytest.mark.parametrize("h,w", [(511, 300), (4095, 33), (4097, 17), (33, 4097), (1000, 1000), (1500, 2600)])
 def test_larger_u8(F, orc, h, w):
     img = inputs.uniform_u8(h + w, h, w)
     check_exact(F, orc, img, 15, "cyclic")
