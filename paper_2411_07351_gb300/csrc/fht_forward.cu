@@ -221,6 +221,7 @@ struct StagedRow {
   int32_t pad;
 };
 
+// General rows: each row its own geometry and column map.
 template <int NT, typename AccT>
 __device__ __forceinline__ void staged_rows(const AccT* S, const int32_t (*so)[kMaxSpineTerms],
                                             const StagedRow<AccT>* ri, int32_t nr, int32_t u0) {
@@ -237,14 +238,53 @@ __device__ __forceinline__ void staged_rows(const AccT* S, const int32_t (*so)[k
 #pragma unroll
       for (int c = 1; c < NT; c++) acc += S[o[c] + q * kStageThreads];
       if (u < R.W) {
-        int32_t X = u;
-        if (R.sigma != 0) {
-          X = R.sigma * u + R.kappa;
-          if (X < 0) X += R.W;
-          if (X >= R.W) X -= R.W;
-        }
+        int32_t X = R.sigma * u + R.kappa;
+        if (X < 0) X += R.W;
+        if (X >= R.W) X -= R.W;
         R.dst[X] = acc;
       }
+    }
+  }
+}
+
+// Uniform rows (one quadrant, one kind, one term count): the output columns
+// X_q of this thread's kStageQPT columns are the same for every row, so they
+// are computed once; a row is then NT shared loads and one store per column.
+template <int NT, typename AccT>
+__device__ __forceinline__ void staged_rows_uniform(const AccT* S, const int32_t (*so)[kMaxSpineTerms],
+                                                    const StagedRow<AccT>* ri, int32_t nr, int32_t u0) {
+  const StagedRow<AccT> R0 = ri[0];
+  int32_t X[kStageQPT];
+  bool live[kStageQPT];
+#pragma unroll
+  for (int q = 0; q < kStageQPT; q++) {
+    const int32_t u = u0 + q * kStageThreads + (int32_t)threadIdx.x;
+    int32_t x = R0.sigma * u + R0.kappa;
+    if (x < 0) x += R0.W;
+    if (x >= R0.W) x -= R0.W;
+    X[q] = x;
+    live[q] = u < R0.W;
+  }
+  const bool full = u0 + kStageTile <= R0.W;
+  for (int32_t r = 0; r < nr; r++) {
+    AccT* __restrict__ d = ri[r].dst;
+    int32_t o[NT];
+#pragma unroll
+    for (int c = 0; c < NT; c++) o[c] = so[r][c] + (int32_t)threadIdx.x;
+    AccT acc[kStageQPT];
+#pragma unroll
+    for (int q = 0; q < kStageQPT; q++) {
+      acc[q] = S[o[0] + q * kStageThreads];
+#pragma unroll
+      for (int c = 1; c < NT; c++) acc[q] += S[o[c] + q * kStageThreads];
+    }
+    if (full) {
+#pragma unroll
+      for (int q = 0; q < kStageQPT; q++) d[X[q]] = acc[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < kStageQPT; q++)
+        if (live[q]) d[X[q]] = acc[q];
     }
   }
 }
@@ -259,7 +299,7 @@ __global__ void __launch_bounds__(kStageThreads) spine_staged_kernel(const Spine
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AccT* S = reinterpret_cast<AccT*>(smem_raw);
   __shared__ StagedRow<AccT> ri[kSpineRows];
-  __shared__ int32_t tc[kSpineRows];
+  __shared__ int32_t tc[kSpineRows], rq[kSpineRows];
   __shared__ __align__(16) int32_t so[kSpineRows][kMaxSpineTerms];
   __shared__ SpineSeg sg[kStageMaxSegs];
   constexpr int32_t EPC = 16 / (int32_t)sizeof(AccT);
@@ -274,11 +314,12 @@ __global__ void __launch_bounds__(kStageThreads) spine_staged_kernel(const Spine
     StagedRow<AccT> o;
     o.dst = (is_inner ? inner : out) + R.dst;
     o.W = is_inner ? R.w : Q.W;
-    o.sigma = is_inner ? 0 : Q.sigma;
-    o.kappa = Q.kappa;
+    o.sigma = is_inner ? 1 : Q.sigma;  // inner rows: X = u
+    o.kappa = is_inner ? 0 : Q.kappa;
     o.pad = 0;
     ri[threadIdx.x] = o;
     tc[threadIdx.x] = R.term_count;
+    rq[threadIdx.x] = R.q * 2 + (is_inner ? 1 : 0);
     for (int32_t c = 0; c < R.term_count; c++) so[threadIdx.x][c] = terms[R.term_begin + c].sofs;
   }
   for (int32_t s = threadIdx.x; s < G.seg_count; s += blockDim.x) sg[s] = segs[G.seg_begin + s];
@@ -288,19 +329,20 @@ __global__ void __launch_bounds__(kStageThreads) spine_staged_kernel(const Spine
   bool uniform = true;
   for (int32_t r = 0; r < nr; r++) {
     wmax = ri[r].W > wmax ? ri[r].W : wmax;
-    uniform = uniform && tc[r] == tc[0];
+    uniform = uniform && tc[r] == tc[0] && rq[r] == rq[0] && ri[r].W == ri[0].W;
   }
   if (u0 >= wmax) return;
   const bool ext = quads.q[0].ext | quads.q[1].ext | quads.q[2].ext | quads.q[3].ext;
-  // stage the windows
-  for (int32_t s = 0; s < G.seg_count; s++) {
+  // stage the windows: one warp per segment, lanes over its 16-byte chunks
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int32_t s = warp; s < G.seg_count; s += nwarps) {
     const SpineSeg g = sg[s];
     const AccT* __restrict__ rowp = ws + g.row;
     const int32_t A = u0 + g.a_off;
     AccT* dst = S + g.smem;
     if (ext) {
       // chunks start at multiples of 16 bytes of the part row (rows are 128-byte aligned)
-      for (int32_t k = threadIdx.x; k < g.len / EPC; k += blockDim.x) {
+      for (int32_t k = lane; k < g.len / EPC; k += 32) {
         const int32_t i0 = A + k * EPC;
         int32_t bytes = 0;
         const AccT* src = rowp;
@@ -311,14 +353,14 @@ __global__ void __launch_bounds__(kStageThreads) spine_staged_kernel(const Spine
         cp_async_16(dst + k * EPC, src, bytes);
       }
     } else if (g.wpart % EPC == 0) {
-      for (int32_t k = threadIdx.x; k < g.len / EPC; k += blockDim.x) {
+      for (int32_t k = lane; k < g.len / EPC; k += 32) {
         int32_t i0 = A + k * EPC;
         if (i0 >= g.wpart) i0 -= g.wpart;
         if (i0 >= g.wpart) i0 %= g.wpart;  // a tile past this quadrant's rows (mixed groups)
         cp_async_16(dst + k * EPC, rowp + i0, 16);
       }
     } else {
-      for (int32_t k = threadIdx.x; k < g.len; k += blockDim.x) {
+      for (int32_t k = lane; k < g.len; k += 32) {
         int32_t i = A + k;
         if (i >= g.wpart) i -= g.wpart;
         if (i >= g.wpart) i %= g.wpart;
@@ -332,7 +374,7 @@ __global__ void __launch_bounds__(kStageThreads) spine_staged_kernel(const Spine
     switch (tc[0]) {
 #define FHT_STAGED(N)                                        \
   case N:                                                    \
-    staged_rows<N, AccT>(S, so, ri, nr, u0);                 \
+    staged_rows_uniform<N, AccT>(S, so, ri, nr, u0);         \
     return;
       FHT_STAGED(1) FHT_STAGED(2) FHT_STAGED(3) FHT_STAGED(4) FHT_STAGED(5) FHT_STAGED(6) FHT_STAGED(7)
       FHT_STAGED(8)
