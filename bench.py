@@ -572,11 +572,24 @@ def run_c4(args):
     xs = [torch.from_numpy(im).cuda().requires_grad_(True) for im in imgs]
     mpix = sum(im.size for im in imgs) / 1e6
 
+    # the 64 images are independent: their forward and backward chains run on
+    # 8 side streams (autograd replays each op's backward on the op's stream)
+    side = [torch.cuda.Stream() for _ in range(8)]
+
     def step():
-        loss = 0
-        for x, y in zip(xs, ys):
-            loss = loss + 0.5 * ((fht(x, 15, "cyclic") - y) ** 2).sum()
+        main = torch.cuda.current_stream()
+        parts = []
+        for k, (x, y) in enumerate(zip(xs, ys)):
+            s = side[k % len(side)]
+            s.wait_stream(main)
+            with torch.cuda.stream(s):
+                parts.append(0.5 * ((fht(x, 15, "cyclic") - y) ** 2).sum())
+        for s in side:
+            main.wait_stream(s)
+        loss = torch.stack(parts).sum()
         loss.backward()
+        for s in side:
+            main.wait_stream(s)
         return loss
 
     for _ in range(3):
