@@ -127,6 +127,17 @@ def test_tuning_knobs_same_result(F, orc, fused_rows, tile_cols):
     check_exact(F, orc, img, 15, "cyclic", fused_rows=fused_rows, tile_cols=tile_cols)
 
 
+@pytest.mark.parametrize("tile_cols,threads", [(64, 512), (128, 512), (128, 256), (96, 512)])
+def test_float_launch_shapes(F, orc, tile_cols, threads):
+    # float inputs take the pipelined block pass at 512 threads and 64- or
+    # 128-column tiles, the per-tile block pass otherwise: same result
+    img = inputs.normal_f32(31, 700, 515)
+    check_float(F, orc, img, 15, "extended", tile_cols=tile_cols, threads=threads)
+    check_float(F, orc, img, 15, "cyclic", tile_cols=tile_cols, threads=threads)
+    imi = inputs.uniform_u8(32, 300, 200).astype(np.int32) - 128
+    check_exact(F, orc, imi, 15, "extended", tile_cols=tile_cols, threads=threads)
+
+
 def test_pitched_input(F, orc):
     img = inputs.uniform_u8(9, 100, 70)
     big = torch.zeros((100, 96), dtype=torch.uint8)
