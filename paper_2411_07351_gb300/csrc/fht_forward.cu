@@ -208,7 +208,7 @@ __device__ __forceinline__ void cp_async_elem(AccT* smem_dst, const AccT* gmem_s
   }
 }
 
-constexpr int kStageThreads = 128;
+constexpr int kStageThreads = 256;
 constexpr int kStageQPT = kStageTile / kStageThreads;
 
 // Per-row constants of a staged CTA, set once by the prologue.
