@@ -465,11 +465,29 @@ def run_c1(args):
     torch.cuda.set_device(0)
     img = inputs.c1_image()
     x = torch.from_numpy(img).cuda()
-    plan = F.Plan(257, 257, torch.uint8, F.FHT_Q0, "cyclic")
+    plan = F.Plan(257, 257, torch.uint8, F.FHT_Q0, "cyclic", tuning="auto")
     out, ws = plan.new_output(), plan.new_workspace()
     for _ in range(50):
         plan.forward(x, out, ws)
     torch.cuda.synchronize()
+    # the same call captured once in a CUDA graph (the three launches without host gaps)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.forward(x, out, ws)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.forward(x, out, ws)
+    gdev = []
+    for i in range(max(args.steps, 1000) + 50):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        graph.replay()
+        b.record()
+        b.synchronize()
+        if i >= 50:
+            gdev.append(a.elapsed_time(b) * 1e3)
     n = max(args.steps, 1000)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
     host = []
@@ -486,7 +504,9 @@ def run_c1(args):
             "higher_is_better": True, "dtype": "u8->i32", "data": "synthetic",
             "config": {"workload": "c1: 257x257 uint8 U{0..255} seed 1, quadrant Q0, cyclic"},
             "latency_us": {"device_p50": _pct(dev, 0.5), "device_p99": _pct(dev, 0.99),
-                           "host_p50": _pct(host, 0.5), "host_p99": _pct(host, 0.99)},
+                           "host_p50": _pct(host, 0.5), "host_p99": _pct(host, 0.99),
+                           "graph_device_p50": _pct(gdev, 0.5), "graph_device_p99": _pct(gdev, 0.99)},
+            "tile_cols": int(plan.info.tile_cols),
             "gpu_launches_per_call": _launches(plan)}
     print(json.dumps(line), flush=True)
 

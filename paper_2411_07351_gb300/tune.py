@@ -71,15 +71,18 @@ def lookup(h, w, dtype, quads, boundary, split):
 
 
 def sweep(sizes=(64, 128, 256, 512, 1024, 2048, 4096), dtypes=(torch.uint8, torch.float32),
-          boundaries=("cyclic", "extended"), quads: int = C.FHT_QALL, reps: int = 8, out: str | None = None) -> dict:
-    """Tune square sizes of a grid and write the winners to `out` (default: the packaged table)."""
+          boundaries=("cyclic", "extended"), quads: int = C.FHT_QALL, reps: int = 8, out: str | None = None,
+          single_quadrant_sizes=(64, 128, 256, 512)) -> dict:
+    """Tune square sizes of a grid and write the winners to `out` (default: the packaged table).
+    Small single-quadrant (Q0) transforms, which are latency-bound, get entries of their own."""
     table = {}
-    for n in sizes:
+    grid = [(n, q) for n in sizes for q in (quads,)] + [(n, C.FHT_Q0) for n in single_quadrant_sizes]
+    for n, q in grid:
         for dt in dtypes:
             for b in boundaries:
-                e = tune(n, n, dt, quads, b, "T", reps=reps, save=False)
-                table[key(n, n, dt, quads, b, "T")] = e
-                print(key(n, n, dt, quads, b, "T"), e["tile_cols"], e["threads"], f"{e['ms']:.4f} ms", flush=True)
+                e = tune(n, n, dt, q, b, "T", reps=reps, save=False)
+                table[key(n, n, dt, q, b, "T")] = e
+                print(key(n, n, dt, q, b, "T"), e["tile_cols"], e["threads"], f"{e['ms']:.4f} ms", flush=True)
     path = out or PACKAGED
     with open(path, "w") as f:
         json.dump(table, f, indent=1, sort_keys=True)
