@@ -46,6 +46,7 @@ struct BatchUnit {
   int32_t tile;   // first column tile (fused, band), column tile (spine) or row count (upper)
   int32_t need;   // units of this job that must be finished first
   int32_t ntiles; // fused / band: column tiles handled by this unit; spine: rows
+  int32_t aux;    // spine: columns per thread (1, 2 or 4)
 };
 
 constexpr int kUpperRowsPerUnit = 8;
@@ -92,11 +93,11 @@ __device__ void batch_upper_rows(const RowJob* __restrict__ rows, int32_t first,
 }
 
 template <typename AccT>
-__device__ void batch_spine(const BatchJob& jb, int32_t r0, int32_t nr, int32_t tile,
+__device__ void batch_spine(const BatchJob& jb, int32_t r0, int32_t nr, int32_t tile, int32_t qpt,
                             SpineTerm (*st)[kMaxSpineTerms], SpineRow* sr) {
   AccT* ws = static_cast<AccT*>(jb.fp.ws);
   AccT* out = static_cast<AccT*>(jb.fp.out);
-  const int32_t u0 = tile * kSpineTile;
+  const int32_t u0 = tile * kBatchThreads * qpt;
   if ((int32_t)threadIdx.x < nr) sr[threadIdx.x] = jb.spine_rows[r0 + threadIdx.x];
   __syncthreads();
   for (int32_t idx = threadIdx.x; idx < nr * kMaxSpineTerms; idx += blockDim.x) {
@@ -104,8 +105,15 @@ __device__ void batch_spine(const BatchJob& jb, int32_t r0, int32_t nr, int32_t 
     if (c < sr[r].term_count) st[r][c] = jb.spine_terms[sr[r].term_begin + c];
   }
   __syncthreads();
-  // 256 threads x 4 columns: the same 1024-column tile as the plain spine kernel
-  spine_rows_tile<true, kBatchThreads, 4, AccT, false>(sr, st, nr, jb.fp.quad, ws, out, ws, u0);
+  // 256 threads x qpt columns: tiles of 256, 512 or 1024 columns, the narrowest
+  // that covers the job's rows in one tile where it can (small images)
+  if (qpt == 1) {
+    spine_rows_tile<true, kBatchThreads, 1, AccT, false>(sr, st, nr, jb.fp.quad, ws, out, ws, u0);
+  } else if (qpt == 2) {
+    spine_rows_tile<true, kBatchThreads, 2, AccT, false>(sr, st, nr, jb.fp.quad, ws, out, ws, u0);
+  } else {
+    spine_rows_tile<true, kBatchThreads, 4, AccT, false>(sr, st, nr, jb.fp.quad, ws, out, ws, u0);
+  }
 }
 
 // counters[0]: next unit; counters[1 + j]: finished units of job j.
@@ -166,7 +174,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchJob*
           break;
         }
         case UNIT_SPINE:
-          batch_spine<AccT>(jb, U.index, U.ntiles, U.tile, st, sr);
+          batch_spine<AccT>(jb, U.index, U.ntiles, U.tile, U.aux, st, sr);
           break;
         default:
           batch_upper_rows<AccT>(jb.rows, U.index, U.tile, static_cast<AccT*>(jb.fp.ws),
@@ -370,9 +378,10 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
   }
   // pass 2: units, phase by phase across all jobs
   std::vector<int32_t> done_before(njobs, 0);
-  auto push = [&](int32_t job, int32_t kind, int32_t index, int32_t tile, int32_t need, int32_t ntiles = 1) -> bool {
+  auto push = [&](int32_t job, int32_t kind, int32_t index, int32_t tile, int32_t need, int32_t ntiles = 1,
+                  int32_t aux = 0) -> bool {
     if (nunits >= q->max_units) return false;
-    q->h_units[nunits++] = fht::BatchUnit{job, kind, index, tile, need, ntiles};
+    q->h_units[nunits++] = fht::BatchUnit{job, kind, index, tile, need, ntiles, aux};
     return true;
   };
   int32_t max_phase = 0;
@@ -405,11 +414,14 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
           int32_t maxW = 1;
           for (int k = 0; k < 4; k++)
             if (P.cfg.quads & (1u << k)) maxW = std::max(maxW, P.quad[k].W);
-          const int32_t tiles = (maxW + fht::kSpineTile - 1) / fht::kSpineTile;
+          const int32_t qpt = maxW <= fht::kBatchThreads ? 1 : maxW <= 2 * fht::kBatchThreads ? 2 : 4;
+          const int32_t width = fht::kBatchThreads * qpt;
+          const int32_t tiles = (maxW + width - 1) / width;
           const int64_t b = P.spine_pass_begin[phase - 2], e = P.spine_pass_begin[phase - 1];
           for (int32_t t = 0; t < tiles && ok; t++)
             for (int64_t r = b; r < e && ok; r += fht::kSpineRows, count++)
-              ok = push(j, fht::UNIT_SPINE, (int32_t)r, t, n, (int32_t)std::min<int64_t>(fht::kSpineRows, e - r));
+              ok = push(j, fht::UNIT_SPINE, (int32_t)r, t, n, (int32_t)std::min<int64_t>(fht::kSpineRows, e - r),
+                        qpt);
         }
       } else if (phase < (int32_t)P.pass_begin.size()) {
         const int64_t b = P.pass_begin[phase - 1], e = P.pass_begin[phase];
