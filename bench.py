@@ -549,7 +549,7 @@ def run_c3(args):
             p.forward(x, o, w)
 
     def batched():
-        q.submit(xs, F.FHT_QALL, "cyclic", "T", outs=outs, workspaces=wss)
+        q.submit(xs, F.FHT_QALL, "cyclic", "T", outs=outs, workspaces=wss, plans=plans)
 
     plain()
     batched()
@@ -563,7 +563,7 @@ def run_c3(args):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.stream(s):
         with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
-            q.submit(xs, F.FHT_QALL, "cyclic", "T", outs=outs, workspaces=wss, stream=s)
+            q.submit(xs, F.FHT_QALL, "cyclic", "T", outs=outs, workspaces=wss, stream=s, plans=plans)
     torch.cuda.synchronize()
     t_graph = timed(g.replay, reps)
     line = {"metric": METRIC, "value": mpix / (t_batch * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": reps,

@@ -5,6 +5,7 @@ from __future__ import annotations
 
 import ctypes
 
+import numpy as np
 import torch
 
 from . import _capi as C
@@ -15,6 +16,12 @@ from .fht import Plan, PlanCache
 # persistent kernel at 3 CTAs per SM (<= 64 KB of shared memory per CTA) and
 # fit the small images batches are for.
 BATCH_TILE_COLS = 64
+
+# numpy layout of fht_job (include/fht.h): 64 bytes, naturally aligned fields
+_JOB_DTYPE = np.dtype([("plan", np.uint64), ("d_in", np.uint64), ("in_pitch", np.int64), ("d_out", np.uint64),
+                       ("d_ws", np.uint64), ("ws_bytes", np.uint64), ("tag", np.uint64), ("flags", np.uint32),
+                       ("reserved", np.uint32)])
+assert _JOB_DTYPE.itemsize == ctypes.sizeof(C.fht_job)
 
 
 class BatchQueue:
@@ -51,20 +58,22 @@ class BatchQueue:
             outs = [p.new_output() for p in plans]
         if workspaces is None:
             workspaces = [p.new_workspace() for p in plans]
-        jobs = (C.fht_job * n)()
-        for k, (x, p, o, w) in enumerate(zip(images, plans, outs, workspaces)):
-            if x.stride(1) != 1:
-                raise ValueError("images must have unit column stride")
-            jobs[k].plan = p._h
-            jobs[k].d_in = x.data_ptr()
-            jobs[k].in_pitch = x.stride(0)
-            jobs[k].d_out = o.data_ptr()
-            jobs[k].d_ws = w.data_ptr()
-            jobs[k].ws_bytes = w.numel()
-            jobs[k].tag = k if tags is None else tags[k]
-            jobs[k].flags = 0 if flags is None else flags[k]
+        if any(x.stride(1) != 1 for x in images):
+            raise ValueError("images must have unit column stride")
+        # the fht_job array, column by column (numpy view of the C struct layout)
+        jobs = np.zeros(n, dtype=_JOB_DTYPE)
+        jobs["plan"] = [p._h.value for p in plans]
+        jobs["d_in"] = [x.data_ptr() for x in images]
+        jobs["in_pitch"] = [x.stride(0) for x in images]
+        jobs["d_out"] = [o.data_ptr() for o in outs]
+        jobs["d_ws"] = [w.data_ptr() for w in workspaces]
+        jobs["ws_bytes"] = [w.numel() * w.element_size() for w in workspaces]
+        jobs["tag"] = np.arange(n) if tags is None else tags
+        if flags is not None:
+            jobs["flags"] = flags
         s = stream if stream is not None else torch.cuda.current_stream(torch.device("cuda", self.device_index))
-        C.check(self._lib.fht_submit(self._q, n, jobs, int(s.cuda_stream)), "fht_submit")
+        C.check(self._lib.fht_submit(self._q, n, jobs.ctypes.data_as(ctypes.POINTER(C.fht_job)), int(s.cuda_stream)),
+                "fht_submit")
         self._keep = [images, outs, workspaces, plans]
         return outs, plans, workspaces
 
