@@ -53,31 +53,6 @@ struct FusedItem {
 
 enum : int32_t { FUSED_GENERIC = 0, FUSED_BY64 = 1, FUSED_BAND = 2 };
 
-// Spine merged group by group (the "grouped spine"): for G consecutive output
-// slopes of a Split_T root the spine's merges are replayed bottom-up in
-// shared memory.  Level 0 is the bottom part (the last spine node's right
-// child); level j >= 1 is spine node j counted from the bottom, whose left
-// child is a part (a band or a 64-row block) and whose right child is level
-// j - 1.  Row ranges per level follow from the monotone tables t -> t2.
-struct SpineLevel {
-  int32_t m;          // rows of the node (level 0: of the bottom part)
-  int32_t tab;        // level >= 1: first entry of its merge table (t1, t2, s) in spine_tabs
-  int64_t part_row0;  // workspace offset of row 0 of the left part (level 0: of the bottom part)
-  int32_t part_m;     // rows of that part
-  int32_t part_w;     // width of a part row (extended: L + part_m - 1; cyclic: W)
-};
-
-struct SpineGroup {
-  int32_t q;          // quadrant
-  int32_t level0;     // first SpineLevel of the quadrant's spine
-  int32_t nlev;       // levels including level 0 (the root is level nlev - 1)
-  int32_t T0;         // first output slope of the group
-  int32_t G;          // output slopes in the group
-  int32_t n;          // rows of the root
-  int32_t smem_rows;  // rows of levels 0 .. nlev-2 held in shared memory for this group
-  int32_t halo;       // extra columns of level 0 beyond the tile (sum of shift ranges)
-};
-
 // The quadrant table passed by value to kernels.
 struct QuadDescs {
   QuadDesc q[4];

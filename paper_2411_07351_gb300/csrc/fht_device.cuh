@@ -156,6 +156,12 @@ __device__ __forceinline__ void cp_async_8(void* smem_dst, const void* gmem_src,
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gmem_src), "r"(src_bytes) : "memory");
 }
 
+// 16-byte copy; the bytes past src_bytes are zero-filled (bypasses L1).
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gmem_src, int32_t src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem_src), "r"(src_bytes) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <typename T>

@@ -193,21 +193,6 @@ __global__ void __launch_bounds__(256, sizeof(AccT) > 4 ? 1 : 3) spine_kernel(co
 // cp.async: 16-byte chunks whose bytes beyond the part row are zero-filled by
 // the copy itself (extended), or element by element with the cyclic wrap;
 // then every output element is the sum of its terms read from shared memory.
-__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gmem_src, int32_t src_bytes) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem_src), "r"(src_bytes) : "memory");
-}
-
-template <typename AccT>
-__device__ __forceinline__ void cp_async_elem(AccT* smem_dst, const AccT* gmem_src) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-  if constexpr (sizeof(AccT) == 8) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
-  } else {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
-  }
-}
-
 constexpr int kStageThreads = 256;
 constexpr int kStageQPT = kStageTile / kStageThreads;
 
@@ -364,7 +349,7 @@ __global__ void __launch_bounds__(kStageThreads) spine_staged_kernel(const Spine
         int32_t i = A + k;
         if (i >= g.wpart) i -= g.wpart;
         if (i >= g.wpart) i %= g.wpart;
-        cp_async_elem<AccT>(dst + k, rowp + i);
+        cp_async_elem_z<AccT>(dst + k, rowp + i, true);
       }
     }
   }
