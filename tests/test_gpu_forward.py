@@ -212,6 +212,15 @@ def test_spine_chunks_same_result(F, orc, spine_chunk):
     check_float(F, orc, imf, 15, "extended", spine_chunk=spine_chunk)
 
 
+def test_largest_size_cyclic(F, orc):
+    """h = 65535 (the largest supported): big parts of 32768, 16384 and 8192
+    rows summed from 4096-row bands, then a chunked spine; whole output."""
+    img = inputs.uniform_u8(65535, 65535, 2)
+    check_exact(F, orc, img, 15, "cyclic")
+    img2 = inputs.uniform_u8(2, 3, 65535)
+    check_exact(F, orc, img2, 15, "cyclic")
+
+
 @pytest.mark.parametrize("h,w", [(9000, 37), (12289, 5), (16500, 9)])
 def test_taller_than_8192(F, orc, h, w):
     """Split_T roots whose power-of-two part is taller than the largest band
