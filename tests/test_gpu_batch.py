@@ -154,3 +154,23 @@ def test_batch_graph_replay(F, queue):
     torch.cuda.synchronize()
     for o, r in zip(outs, ref):
         assert torch.equal(o, r)
+
+
+def test_batch_c3_full_size(F, orc):
+    """The full batching workload (4096 binary edge maps, h, w ~ U{17..511}, all
+    four quadrants, cyclic) in one persistent launch: every output equals the
+    per-image launches bit for bit, and a sample equals the oracle."""
+    from paper_2411_07351_gb300.batch import BatchQueue
+
+    imgs = inputs.c3_batch()
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    q = BatchQueue(max_jobs=len(xs), max_units=1 << 23)
+    outs, plans, _ = q.submit(xs, 15, "cyclic")
+    torch.cuda.synchronize()
+    assert q.status() == 0
+    for x, o, p in zip(xs, outs, plans):
+        assert torch.equal(o, p.forward(x))
+    for k in (0, 1000, 2047, 4095):
+        im = imgs[k].astype(np.int64)
+        assert np.array_equal(outs[k].cpu().numpy(), orc.fht(im, 15, orc.CYCLIC))
+    q.close()
