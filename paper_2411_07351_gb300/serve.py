@@ -9,11 +9,13 @@ launch (fht_submit) on the least busy of its streams (each stream holds up to
 ``max_inflight`` launches); a large request (at least ``plain_pixels``)
 fills the GPU by itself and runs the per-image kernels instead.  Batches on
 different streams overlap on the device; a request that arrives while others
-run joins the next batch as soon as memory and a stream are free.  Latency is
-arrival -> the host seeing the batch's completion event.
+run joins the next batch as soon as memory and a stream are free.  Plans are
+built on a thread pool; requests are admitted in arrival order among those
+whose plans are ready, so a plan still being built holds up only its own
+request.  Latency is arrival -> the host seeing the request's completion.
 
 ``PlainServer`` is the comparison: one fht_forward per request, launched on
-one stream as soon as the request arrives.
+one stream as soon as the request's plan is ready.
 """
 from __future__ import annotations
 
@@ -81,6 +83,23 @@ class PlanBuilder:
         self.pool.shutdown(wait=True)
 
 
+def _ready_in_order(waiting, window: int = 256):
+    """Requests of the first `window` waiting ones whose plans are built, in
+    arrival order (a request whose plan is still being built does not hold up
+    the ones behind it).  Returns a list, so the caller may remove from `waiting`."""
+    ready = []
+    for k, req in enumerate(waiting):
+        if k >= window:
+            break
+        if req.plan is None:
+            if not req.plan_future.done():
+                continue
+            req.plan = req.plan_future.result()
+            req.nbytes = req.plan.out_elems * 4 + max(req.plan.workspace_bytes, 256)
+        ready.append(req)
+    return ready
+
+
 @dataclass
 class _Batch:
     event: torch.cuda.Event
@@ -120,17 +139,11 @@ class Server:
         self.waiting.append(req)
 
     def _admit(self):
-        while self.waiting:
-            req = self.waiting[0]
-            if req.plan is None:
-                if not req.plan_future.done():
-                    break  # admission stays in arrival order
-                req.plan = req.plan_future.result()
-                req.nbytes = req.plan.out_elems * 4 + max(req.plan.workspace_bytes, 256)
+        for req in _ready_in_order(self.waiting):
             need = req.nbytes
             if self.used + need > self.budget and self.used > 0:
-                break
-            self.waiting.popleft()
+                break  # memory is admitted in arrival order among ready requests
+            self.waiting.remove(req)
             self.used += need
             self.max_used = max(self.max_used, self.used)
             self.admitted.append(req)
@@ -232,8 +245,9 @@ class Server:
 
 
 class PlainServer:
-    """One plain fht_forward per request, launched in arrival order on one
-    stream, under the same device-memory budget as the batched server."""
+    """One plain fht_forward per request, launched in arrival order (among
+    requests whose plans are built, as in Server) on one stream, under the same
+    device-memory budget as the batched server."""
 
     def __init__(self, device: int = 0, budget_bytes: int = 16 << 30, quads: int = C.FHT_QALL,
                  boundary: str = "cyclic", split: str = "T", keep_outputs: bool = True):
@@ -255,16 +269,10 @@ class PlainServer:
         self.waiting.append(req)
 
     def _launch(self):
-        while self.waiting:
-            req = self.waiting[0]
-            if req.plan is None:
-                if not req.plan_future.done():
-                    return
-                req.plan = req.plan_future.result()
-                req.nbytes = req.plan.out_elems * 4 + max(req.plan.workspace_bytes, 256)
+        for req in _ready_in_order(self.waiting):
             if self.used + req.nbytes > self.budget and self.used > 0:
                 return
-            self.waiting.popleft()
+            self.waiting.remove(req)
             self.used += req.nbytes
             self.max_used = max(self.max_used, self.used)
             p = req.plan
