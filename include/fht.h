@@ -264,7 +264,10 @@ fht_status fht_plan_check(fht_plan_t plan);
 fht_status fht_plan_destroy(fht_plan_t plan);
 
 /* Device status word kept at the start of a workspace: FHT_OK or the first
- * device-side error recorded by a kernel that used it.  Synchronises `stream`. */
+ * device-side error recorded by a kernel that used it.  Every fht_forward
+ * clears it in its first launch; a spine launch whose bounded wait for its
+ * bulk copies runs out (1 s) records FHT_ERR_TIMEOUT and leaves its tile
+ * unwritten.  Synchronises `stream`. */
 fht_status fht_ws_status(const void* d_ws, void* stream);
 
 const char* fht_status_string(fht_status status);

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/fht.h"
 #include "fht_desc.h"
 #include "fht_device.cuh"
 #include "fht_launch.hpp"
@@ -21,6 +22,10 @@ namespace fht {
 
 template <typename InT, typename AccT>
 __global__ void __launch_bounds__(512, 2) fused_kernel(FusedParams p) {
+  // the first launch of a forward clears the workspace status word (later
+  // launches record device-side errors there)
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    *reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p.ws) - kWsHeader) = 0;
   const FusedItem it = p.items[blockIdx.x];
   const int32_t tile = blockIdx.y;
   if (tile >= it.ntiles) return;
@@ -283,6 +288,8 @@ __global__ void __launch_bounds__(kStageThreads) spine_staged_kernel(const Spine
                                                            AccT* inner, QuadDescs quads) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AccT* S = reinterpret_cast<AccT*>(smem_raw);
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int32_t s_wait_ok;
   __shared__ StagedRow<AccT> ri[kSpineRows];
   __shared__ int32_t tc[kSpineRows], rq[kSpineRows];
   __shared__ __align__(16) int32_t so[kSpineRows][kMaxSpineTerms];
@@ -318,26 +325,71 @@ __global__ void __launch_bounds__(kStageThreads) spine_staged_kernel(const Spine
   }
   if (u0 >= wmax) return;
   const bool ext = quads.q[0].ext | quads.q[1].ext | quads.q[2].ext | quads.q[3].ext;
-  // stage the windows: one warp per segment, lanes over its 16-byte chunks
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int32_t s = warp; s < G.seg_count; s += nwarps) {
+  if (ext) {
+    // Extended: each window's in-row stretch [lo, lo + n) (16-byte multiples: rows are 128-byte
+    // aligned, window starts are multiples of 16 bytes) is one bulk copy; the few columns outside
+    // it (zeros beyond the part row, up to 15 bytes of tail) are written by the threads.
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, (uint32_t)G.seg_count);  // one arrival per window
+      s_wait_ok = 1;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // lane s announces window s's bytes and issues its copy
+      for (int32_t s = lane; s < G.seg_count; s += 32) {
+        const SpineSeg& g = sg[s];
+        const int32_t A = u0 + g.a_off, lo = A > 0 ? A : 0, hi = A + g.len < g.wpart ? A + g.len : g.wpart;
+        const int32_t n = hi > lo ? (hi - lo) / EPC * EPC : 0;
+        mbar_arrive_expect_tx(&bar, (uint32_t)n * (uint32_t)sizeof(AccT));
+        if (n > 0) bulk_copy_g2s(S + g.smem + (lo - A), ws + g.row + lo, (uint32_t)n * (uint32_t)sizeof(AccT), &bar);
+      }
+    }
+    for (int32_t s = warp; s < G.seg_count; s += nwarps) {
+      const SpineSeg g = sg[s];
+      const AccT* __restrict__ rowp = ws + g.row;
+      const int32_t A = u0 + g.a_off, lo = A > 0 ? A : 0, hi = A + g.len < g.wpart ? A + g.len : g.wpart;
+      const int32_t n = hi > lo ? (hi - lo) / EPC * EPC : 0;
+      AccT* dst = S + g.smem;
+      // columns left of the part row (the whole window when it ends left of column 0)
+      const int32_t left = lo - A < g.len ? lo - A : g.len;
+      for (int32_t e = lane; e < left; e += 32) dst[e] = AccT(0);
+      // the tail of the part row and the columns right of it
+      for (int32_t e = (lo - A) + n + lane; e < g.len; e += 32) {
+        const int32_t i = A + e;
+        dst[e] = i < g.wpart ? __ldg(rowp + i) : AccT(0);
+      }
+    }
+    // bounded wait for the bulk copies (they complete within microseconds)
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(&bar, 0)) {
+      if (globaltimer_ns() - t0 > 1000000000ull) {
+        s_wait_ok = 0;
+        break;
+      }
+    }
+    __syncthreads();
+    if (!s_wait_ok) {
+      // record the failure in the workspace status word, give the copies a
+      // last bounded chance to land, and leave this tile unwritten
+      if (threadIdx.x == 0) {
+        int32_t* status = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(inner) - kWsHeader);
+        atomicCAS(status, 0, (int32_t)FHT_ERR_TIMEOUT);
+        const uint64_t t1 = globaltimer_ns();
+        while (!mbar_try_wait(&bar, 0) && globaltimer_ns() - t1 < 1000000000ull) {
+        }
+      }
+      __syncthreads();
+      return;
+    }
+  }
+  // cyclic: stage the windows with cp.async, one warp per segment, lanes over its 16-byte chunks
+  for (int32_t s = warp; s < G.seg_count && !ext; s += nwarps) {
     const SpineSeg g = sg[s];
     const AccT* __restrict__ rowp = ws + g.row;
     const int32_t A = u0 + g.a_off;
     AccT* dst = S + g.smem;
-    if (ext) {
-      // chunks start at multiples of 16 bytes of the part row (rows are 128-byte aligned)
-      for (int32_t k = lane; k < g.len / EPC; k += 32) {
-        const int32_t i0 = A + k * EPC;
-        int32_t bytes = 0;
-        const AccT* src = rowp;
-        if (i0 >= 0 && i0 < g.wpart) {
-          bytes = (g.wpart - i0 < EPC ? g.wpart - i0 : EPC) * (int32_t)sizeof(AccT);
-          src = rowp + i0;
-        }
-        cp_async_16(dst + k * EPC, src, bytes);
-      }
-    } else if (g.wpart % EPC == 0) {
+    if (g.wpart % EPC == 0) {
       for (int32_t k = lane; k < g.len / EPC; k += 32) {
         int32_t i0 = A + k * EPC;
         if (i0 >= g.wpart) i0 -= g.wpart;

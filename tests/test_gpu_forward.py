@@ -250,3 +250,21 @@ def test_taller_than_8192(F, orc, h, w):
         assert (b.long().sum(1) == total).all()
     del blocks, x, p
     torch.cuda.empty_cache()
+
+
+def test_workspace_status_cleared_by_forward(F, orc):
+    """The workspace's device status word is cleared by every forward (the rest
+    of the workspace may hold anything on entry) and stays FHT_OK when the
+    staged spine's bounded waits all complete."""
+    from paper_2411_07351_gb300 import _capi
+
+    img = inputs.normal_f32(5, 1500, 700)
+    x = torch.from_numpy(img).cuda()
+    p = F.Plan(1500, 700, torch.float32, 15, "extended")
+    out, ws = p.new_output(), p.new_workspace()
+    ws.fill_(0xFF)  # garbage, including the status word
+    p.forward(x, out, ws)
+    lib = _capi.load()
+    st = lib.fht_ws_status(ws.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert st == _capi.FHT_OK
+    check_float(F, orc, img, 15, "extended")
