@@ -162,6 +162,15 @@ __device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gmem_src
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem_src), "r"(src_bytes) : "memory");
 }
 
+// ---- programmatic dependent launch ----
+// A launch made with programmatic stream serialisation may start while the
+// previous kernel on the stream drains; pdl_wait() blocks until that kernel
+// has completed and its writes are visible (it returns at once in a launch
+// made without the attribute).  pdl_launch_dependents() lets the next such
+// launch start once every CTA of this kernel has issued it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" :::); }
+
 // ---- bulk copies (TMA unit) completing on a shared-memory mbarrier ----
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 

@@ -22,6 +22,8 @@ namespace fht {
 
 template <typename InT, typename AccT>
 __global__ void __launch_bounds__(512, 2) fused_kernel(FusedParams p) {
+  pdl_launch_dependents();
+  pdl_wait();  // band items read the blocks of the launch before
   // the first launch of a forward clears the workspace status word (later
   // launches record device-side errors there)
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
@@ -44,6 +46,8 @@ __global__ void __launch_bounds__(512, 2) fused_kernel(FusedParams p) {
 template <typename AccT>
 __global__ void __launch_bounds__(256) upper_kernel(const RowJob* __restrict__ rows, int64_t nrows,
                                                    const AccT* __restrict__ ws_in, AccT* ws_out, AccT* out) {
+  pdl_launch_dependents();
+  pdl_wait();
   constexpr int U = 8;
   for (int64_t k = blockIdx.x; k < nrows; k += gridDim.x) {
     const RowJob J = rows[k];
@@ -122,6 +126,8 @@ __global__ void __launch_bounds__(256, sizeof(AccT) > 4 ? 1 : 3) spine_kernel(co
   __shared__ SpineRow sr[kSpineRows];
   __shared__ const AccT* tp[kSpineRows][kMaxSpineTerms];
   __shared__ int32_t s_straddle;
+  pdl_launch_dependents();
+  pdl_wait();
   const int64_t r0 = (int64_t)blockIdx.x * kSpineRows;
   const int32_t u0 = blockIdx.y * kSpineTilePlain;
   const int32_t nr = (int32_t)(nrows - r0 < kSpineRows ? nrows - r0 : kSpineRows);
@@ -295,6 +301,7 @@ __global__ void __launch_bounds__(kStageThreads) spine_staged_kernel(const Spine
   __shared__ __align__(16) int32_t so[kSpineRows][kMaxSpineTerms];
   __shared__ SpineSeg sg[kStageMaxSegs];
   constexpr int32_t EPC = 16 / (int32_t)sizeof(AccT);
+  pdl_launch_dependents();
   const int64_t r0 = (int64_t)blockIdx.x * kSpineRows;
   const int32_t u0 = blockIdx.y * kStageTile;
   const int32_t nr = (int32_t)(nrows - r0 < kSpineRows ? nrows - r0 : kSpineRows);
@@ -324,6 +331,8 @@ __global__ void __launch_bounds__(kStageThreads) spine_staged_kernel(const Spine
     uniform = uniform && tc[r] == tc[0] && rq[r] == rq[0] && ri[r].W == ri[0].W;
   }
   if (u0 >= wmax) return;
+  // the tables above are the plan's; the part rows below were written by the launches before
+  pdl_wait();
   const bool ext = quads.q[0].ext | quads.q[1].ext | quads.q[2].ext | quads.q[3].ext;
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   if (ext) {
@@ -498,6 +507,22 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
   auto mark = [&](int which) {
     if (ev) cudaEventRecord(ev[2 * launch + which], st);
   };
+  // Every launch after the first of a forward may start while the one before
+  // drains (its kernels wait for the data in griddepcontrol.wait); the first
+  // launch and the per-launch timing mode serialise normally.
+  auto go = [&](auto kernel, dim3 grid, unsigned block, size_t smem, auto... args) -> cudaError_t {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = (launch > 0 && !ev) ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+  };
   const HostPlan& P = *D.host;
   AccT* wsa = reinterpret_cast<AccT*>(static_cast<unsigned char*>(ws) + kWsHeader);
   FusedParams fp;
@@ -518,20 +543,19 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)P.fused.size(), P.max_ntiles);  // tiles <= 131070 / 32 fit in grid.y
   mark(0);
-  kfn<<<grid, P.cfg.threads, smem, st>>>(fp);
+  e = go(kfn, grid, P.cfg.threads, smem, fp);
   mark(1);
   launch++;
-  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (P.bands) {
     if (!P.band_items.empty()) {
       fp.items = D.band_items;
       dim3 bgrid((unsigned)P.band_items.size(), P.max_band_ntiles);
       mark(0);
-      kfn<<<bgrid, P.cfg.threads, smem, st>>>(fp);
+      e = go(kfn, bgrid, P.cfg.threads, smem, fp);
       mark(1);
       launch++;
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if (e != cudaSuccess) return e;
     }
     QuadDescs qd;
     for (int q = 0; q < 4; q++) qd.q[q] = P.quad[q];
@@ -550,16 +574,17 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
         if ((e = cudaFuncSetAttribute(kst, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
           return e;
         dim3 sgrid(groups, (unsigned)((maxW + kStageTile - 1) / kStageTile));
-        kst<<<sgrid, kStageThreads, smem, st>>>(D.spine_rows + b, n, D.spine_terms, D.spine_grps + P.spine_grp_begin[p],
-                                      D.spine_segs, wsa, static_cast<AccT*>(out), wsa, qd);
+        e = go(kst, sgrid, kStageThreads, smem, (const SpineRow*)(D.spine_rows + b), n,
+               (const SpineTerm*)D.spine_terms, (const SpineGrp*)(D.spine_grps + P.spine_grp_begin[p]),
+               (const SpineSeg*)D.spine_segs, (const AccT*)wsa, static_cast<AccT*>(out), wsa, qd);
       } else {
         dim3 sgrid(groups, (unsigned)((maxW + kSpineTilePlain - 1) / kSpineTilePlain));
-        spine_kernel<AccT><<<sgrid, 256, 0, st>>>(D.spine_rows + b, n, D.spine_terms, wsa,
-                                                  static_cast<AccT*>(out), wsa, qd);
+        e = go(spine_kernel<AccT>, sgrid, 256, 0, (const SpineRow*)(D.spine_rows + b), n,
+               (const SpineTerm*)D.spine_terms, (const AccT*)wsa, static_cast<AccT*>(out), wsa, qd);
       }
       mark(1);
       launch++;
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
@@ -568,10 +593,10 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
     if (n <= 0) continue;
     const unsigned blocks = (unsigned)std::min<int64_t>(n, 1 << 30);
     mark(0);
-    upper_kernel<AccT><<<blocks, 256, 0, st>>>(D.rows + b, n, wsa, wsa, static_cast<AccT*>(out));
+    e = go(upper_kernel<AccT>, dim3(blocks), 256, 0, (const RowJob*)(D.rows + b), n, (const AccT*)wsa, wsa,
+           static_cast<AccT*>(out));
     mark(1);
     launch++;
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
