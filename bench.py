@@ -673,12 +673,12 @@ def run_c5(args):
     field = np.where(g.random((hi, hi)) < 0.1, g.integers(1, 256, (hi, hi)), 0).astype(np.uint8)
     dfield = torch.from_numpy(field).cuda()
 
-    def make_requests():
-        gg = np.random.Generator(np.random.PCG64(60))
+    def make_requests(seed=60, seconds=None):
+        gg = np.random.Generator(np.random.PCG64(seed))
         t, out = 0.0, []
         while True:
             t += gg.exponential(1.0 / rate)
-            if t > dur:
+            if t > (dur if seconds is None else seconds):
                 return out
             h = int(round(math.exp(gg.uniform(math.log(lo), math.log(hi)))))
             w = int(round(math.exp(gg.uniform(math.log(lo), math.log(hi)))))
@@ -688,9 +688,17 @@ def run_c5(args):
     res = {}
     makers = (("served", lambda: Server(budget_bytes=16 << 30, streams=4, keep_outputs=False)),
               ("plain", lambda: PlainServer(keep_outputs=False)))
+    def warmed(mk):
+        # half a second of other requests first: kernels loaded, allocator and
+        # streams warm (the measured stream's shapes still need new plans)
+        srv = mk()
+        run_stream(srv, make_requests(seed=61, seconds=0.5))
+        srv.finished, srv.batches = [], 0
+        return srv
+
     for name, mk in makers:
         reqs = make_requests()
-        srv = mk()
+        srv = warmed(mk)
         done, wall = run_stream(srv, reqs)
         lat = [(r.done - r.arrival) * 1e3 for r in done]
         mp = sum(r.image.numel() for r in done) / 1e6
@@ -704,7 +712,7 @@ def run_c5(args):
         reqs = make_requests()[: int(nonlocal_rate * min(dur, 2.0))]
         for r in reqs:
             r.arrival /= 10.0
-        srv = mk()
+        srv = warmed(mk)
         done, wall = run_stream(srv, reqs)
         lat = [(r.done - r.arrival) * 1e3 for r in done]
         mp = sum(r.image.numel() for r in done) / 1e6
@@ -714,7 +722,8 @@ def run_c5(args):
     line = {"metric": METRIC + " served", "value": res["served"]["mpix_per_s"], "unit": UNIT, "n_gpus": 1,
             "higher_is_better": True, "dtype": "u8->i32", "data": "synthetic",
             "config": {"workload": f"c5: Poisson {rate:.0f} req/s for {dur} s, h, w log-uniform [64, 4096], "
-                                   "10% non-zero uint8 windows of a seeded field, 4 quadrants cyclic, 16 GB budget"},
+                                   "10% non-zero uint8 windows of a seeded field, 4 quadrants cyclic, 16 GB budget",
+                       "warm_up": "0.5 s of requests from another seed through each server before its measured run"},
             "served": res["served"], "plain": res["plain"]}
     print(json.dumps(line), flush=True)
 
