@@ -111,6 +111,28 @@ def test_host_only_plan_cannot_run(F):
     assert b"host-only" in lib.fht_last_error()
 
 
+def test_argument_errors_without_a_gpu(F):
+    # every entry point checks its arguments before touching a device
+    from paper_2411_07351_gb300 import _capi
+
+    lib = _capi.load()
+    p = F.Plan(8, 8, torch.float32, 1, device=-1)
+    h = ctypes.c_void_p()
+    assert lib.fht_pipe_create(ctypes.byref(h), p._h, 2, 1) == _capi.FHT_ERR_INVALID
+    assert b"host-only" in lib.fht_last_error()
+    assert lib.fht_pipe_create(ctypes.byref(h), None, 2, 1) == _capi.FHT_ERR_INVALID
+    assert lib.fht_pipe_submit(None, 16, 8, 16) == _capi.FHT_ERR_INVALID
+    assert lib.fht_pipe_sync(None) == _capi.FHT_ERR_INVALID
+    assert lib.fht_pipe_destroy(None) == _capi.FHT_OK
+    assert lib.fht_forward_noalloc(p._h, 16, 8, 16, None) == _capi.FHT_ERR_INVALID
+    assert lib.fht_submit(None, 1, None, None) == _capi.FHT_ERR_INVALID
+    assert lib.fht_queue_destroy(None) == _capi.FHT_OK
+    assert lib.fht_adjoint(p._h, 16, 16, 8, 256, p.adjoint_workspace_bytes, None) == _capi.FHT_ERR_INVALID
+    assert lib.fht_pattern_errors(0, 5, 0, None, None) == _capi.FHT_ERR_INVALID
+    assert lib.fht_plan_check(None) == _capi.FHT_ERR_INVALID
+    assert lib.fht_plan_destroy(None) == _capi.FHT_OK
+
+
 def test_byte_model_c2(F):
     # 4095^2 float32, four quadrants, extended; ideal = input once + output once.
     # Band schedule (Split_T, 64-row blocks): fused pass + band pass + spine sum,
