@@ -41,6 +41,9 @@ WORKLOADS = {
                         desc="4095x4095 float32 N(0,1) seed 2, 4 quadrants, extended boundary"),
     "c2-cyclic": dict(h=4095, w=4095, quads=15, boundary="cyclic",
                       desc="4095x4095 float32 N(0,1) seed 2, 4 quadrants, cyclic boundary"),
+    # the comparison method of the paper (balanced Split_S tree), same image
+    "c2-extended-split-s": dict(h=4095, w=4095, quads=15, boundary="extended", split="S",
+                                desc="4095x4095 float32 N(0,1) seed 2, 4 quadrants, extended boundary, FHT2DS"),
 }
 METRIC = "FHT Mpix/s (4 quadrants)"
 UNIT = "Mpix/s"
@@ -161,20 +164,24 @@ def oracle_sample_seconds(img, wl, rows: int):
 
     sub = np.ascontiguousarray(img[:rows])
     t = time.perf_counter()
-    oracle.fht(sub, 1, oracle.EXTENDED if wl["boundary"] == "extended" else oracle.CYCLIC)
+    oracle.fht(sub, 1, oracle.EXTENDED if wl["boundary"] == "extended" else oracle.CYCLIC, _rule(oracle, wl))
     return time.perf_counter() - t
+
+
+def _rule(oracle, wl):
+    return oracle.SPLIT_S if wl.get("split", "T") == "S" else oracle.SPLIT_T
 
 
 def _oracle_full_image(job):
     """Worker of the all-core oracle baseline: the full 4-quadrant transform of
     the seeded workload image, once (a spawned process: no CUDA state)."""
-    h, w, boundary = job
+    h, w, boundary, split = job
     import oracle
     from paper_2411_07351_gb300 import inputs
 
     img = inputs.c2_image(h=h, w=w)
     t = time.perf_counter()
-    oracle.fht(img, 15, oracle.EXTENDED if boundary == "extended" else oracle.CYCLIC)
+    oracle.fht(img, 15, oracle.EXTENDED if boundary == "extended" else oracle.CYCLIC, _rule(oracle, {"split": split}))
     return time.perf_counter() - t
 
 
@@ -191,7 +198,7 @@ def cpu_baselines(img, wl, min_seconds: float = 10.0):
     b = oracle.EXTENDED if wl["boundary"] == "extended" else oracle.CYCLIC
     runs, t0 = 0, time.perf_counter()
     while runs == 0 or time.perf_counter() - t0 < min_seconds:
-        oracle.fht(img, 15, b)
+        oracle.fht(img, 15, b, _rule(oracle, wl))
         runs += 1
     sec1 = time.perf_counter() - t0
     one = {"value": runs * h * w / sec1 / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -200,7 +207,7 @@ def cpu_baselines(img, wl, min_seconds: float = 10.0):
     n = os.cpu_count() or 1
     t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(n) as pool:
-        pool.map(_oracle_full_image, [(h, w, wl["boundary"])] * n)
+        pool.map(_oracle_full_image, [(h, w, wl["boundary"], wl.get("split", "T"))] * n)
     secn = time.perf_counter() - t0
     alln = {"value": n * h * w / secn / 1e6, "unit": UNIT, "cores": n, "kind": "oracle",
             "sample": f"{n} independent full 4-quadrant transforms of the {h}x{w} image, one per core, "
@@ -267,7 +274,7 @@ def run_reference(args, wl):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl["desc"], "h": wl["h"], "w": wl["w"], "quadrants": 4,
-                       "boundary": wl["boundary"], "split": "T", "sample": sample},
+                       "boundary": wl["boundary"], "split": wl.get("split", "T"), "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                              "cpu": _cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -294,7 +301,7 @@ def run_fht(args, wl):
     h, w = wl["h"], wl["w"]
     img = inputs.c2_image(h=h, w=w)
     x = torch.from_numpy(img).cuda()
-    plan = F.Plan(h, w, torch.float32, wl["quads"], wl["boundary"], "T", device=local)
+    plan = F.Plan(h, w, torch.float32, wl["quads"], wl["boundary"], wl.get("split", "T"), device=local)
     out = plan.new_output()
     ws = plan.new_workspace()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -410,7 +417,8 @@ def run_fht(args, wl):
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["desc"], "h": h, "w": w, "quadrants": 4, "boundary": wl["boundary"],
-                       "split": "T", "fused_rows": int(plan.info.fused_rows), "tile_cols": int(plan.info.tile_cols),
+                       "split": wl.get("split", "T"), "fused_rows": int(plan.info.fused_rows),
+                       "tile_cols": int(plan.info.tile_cols),
                        "l2": "256 MiB buffer written between timed steps, outside the step events",
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
