@@ -118,7 +118,7 @@ __device__ __forceinline__ void stage_rows(const FusedParams& p, const QuadDesc&
         if (Q.ext) {
           valid = valid && z >= 0 && z < Q.L;
         } else {
-          z %= Q.L;
+          if (z >= Q.L) z = z < 2 * Q.L ? z - Q.L : z % Q.L;
         }
         if (Q.flip) z = Q.L - 1 - z;
         const InT* __restrict__ rowp = in + (int64_t)(valid ? z : 0) * p.in_pitch + a;
@@ -246,7 +246,7 @@ __device__ __forceinline__ void stage_gathered_async(const FusedParams& p, const
         if (Q.ext) {
           ok = z >= 0 && z < it.wsrc;
         } else {
-          z = z % Q.W;
+          if (z >= Q.W) z = z < 2 * Q.W ? z - Q.W : z % Q.W;  // z >= 0 in the cyclic case
         }
         cp_async_elem_z<AccT>(dst + j, ok ? row + z : row, ok);
       }
@@ -308,7 +308,7 @@ __device__ __forceinline__ void stage_block_c(const FusedParams& p, const QuadDe
         if (Q.ext) {
           valid = valid && z >= 0 && z < Q.L;
         } else {
-          z %= Q.L;
+          if (z >= Q.L) z = z < 2 * Q.L ? z - Q.L : z % Q.L;
         }
         if (Q.flip) z = Q.L - 1 - z;
         const InT* __restrict__ rowp = in + (int64_t)(valid ? z : 0) * p.in_pitch + a;
@@ -509,7 +509,7 @@ __device__ __forceinline__ void stage_gathered(const FusedParams& p, const Fused
             if (Q.ext) {
               ok = ok && z >= 0 && z < it.wsrc;
             } else {
-              z = z % Q.W;
+              if (z >= Q.W) z = z < 2 * Q.W ? z - Q.W : z % Q.W;  // z >= 0 in the cyclic case
             }
           }
           v[rr][c] = ok ? ld_ws<kC>(row + z) : AccT(0);
