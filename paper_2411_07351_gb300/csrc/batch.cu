@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchJob*
   __shared__ int32_t s_ok;
   __shared__ SpineTerm st[kSpineRows][kMaxSpineTerms];
   __shared__ SpineRow sr[kSpineRows];
+  __shared__ __align__(16) BatchJob s_job;  // the current unit's job descriptor
   AccT* sm = reinterpret_cast<AccT*>(smem_raw);
   int32_t next = 0;  // thread 0: the unit index taken for the following turn
   if (threadIdx.x == 0) s_unit = atomicAdd(&counters[0], 1);
@@ -137,6 +138,10 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchJob*
     // take the next unit now, so the atomic's latency hides behind this unit's work
     if (threadIdx.x == 0) next = atomicAdd(&counters[0], 1);
     const BatchUnit U = units[ui];
+    // the job descriptor into shared memory (every field below is read many times)
+    static_assert(sizeof(BatchJob) % 4 == 0, "word copy");
+    for (int32_t k = threadIdx.x; k < (int32_t)(sizeof(BatchJob) / 4); k += blockDim.x)
+      reinterpret_cast<int32_t*>(&s_job)[k] = reinterpret_cast<const int32_t*>(&jobs[U.job])[k];
     if (threadIdx.x == 0) {
       int32_t ok = 1;
       if (U.need > 0) {
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchJob*
     }
     __syncthreads();
     if (s_ok) {
-      const BatchJob& jb = jobs[U.job];
+      const BatchJob& jb = s_job;
       switch (U.kind) {
         case UNIT_FUSED:
         case UNIT_BAND: {
