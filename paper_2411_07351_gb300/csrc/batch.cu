@@ -188,10 +188,12 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchJob*
       }
     }
     // publish this unit's writes before counting it done (skipped units are
-    // counted too, so that nothing waits on them)
-    __threadfence();
+    // counted too, so that nothing waits on them): the barrier orders every
+    // thread's writes before thread 0's gpu-scope fence, which is cumulative,
+    // and the fence orders them before the count
     __syncthreads();
     if (threadIdx.x == 0) {
+      __threadfence();
       const int32_t finished = atomicAdd(&counters[1 + U.job], 1) + 1;
       const BatchJob& jb = jobs[U.job];
       if (finished == jb.total_units) {
