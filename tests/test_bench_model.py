@@ -1,0 +1,45 @@
+"""The byte model bench.py reports its step roofline against (CPU only).
+
+The per-height model counts the HBM bytes of the Split_T recursion (Section 3,
+Algorithm 2) run one tree level per pass over subtrees of at most 64 rows:
+the image read once per quadrant, each leaf subtree written once, and every
+node above the leaves reading its two children and writing its own rows.  Row
+widths are L + m - 1 for an m-row node with the extended boundary and L with
+the cyclic one (Section 2).  The sums below are written out by hand for small
+trees; the 4095 x 4095 figures are the ones the bench quotes.
+"""
+import bench
+
+
+def test_leaf_only_tree():
+    # 64 x 64: one leaf per quadrant, no upper level
+    ext = 4 * (64 * 64 * 4 + 64 * (64 + 63) * 4)
+    cyc = 4 * (64 * 64 * 4 + 64 * 64 * 4)
+    assert bench.per_height_model_bytes(64, 64, True) == ext
+    assert bench.per_height_model_bytes(64, 64, False) == cyc
+
+
+def test_one_upper_level():
+    # 128 x 128: two 64-row leaves and one merge per quadrant
+    leaf = 64 * (128 + 63) * 4
+    merge = (2 * 64 * (128 + 63) + 128 * (128 + 127)) * 4
+    assert bench.per_height_model_bytes(128, 128, True) == 4 * (128 * 128 * 4 + 2 * leaf + merge)
+    leaf_c = 64 * 128 * 4
+    merge_c = (2 * 64 * 128 + 128 * 128) * 4
+    assert bench.per_height_model_bytes(128, 128, False) == 4 * (128 * 128 * 4 + 2 * leaf_c + merge_c)
+
+
+def test_uneven_split_and_transposed_quadrants():
+    # 100 x 30: quadrants 0, 1 split 100 rows (64 + 36) of length 30; quadrants 2, 3
+    # are the transpose, 30 rows of length 100 (one leaf)
+    ext_01 = 100 * 30 * 4 + (64 * 93 + 36 * 65) * 4 + (64 * 93 + 36 * 65 + 100 * 129) * 4
+    ext_23 = 30 * 100 * 4 + 30 * 129 * 4
+    assert bench.per_height_model_bytes(100, 30, True) == 2 * ext_01 + 2 * ext_23
+    cyc_01 = 100 * 30 * 4 + 100 * 30 * 4 + (100 * 30 + 100 * 30) * 4
+    cyc_23 = 30 * 100 * 4 + 30 * 100 * 4
+    assert bench.per_height_model_bytes(100, 30, False) == 2 * cyc_01 + 2 * cyc_23
+
+
+def test_headline_figures():
+    assert bench.per_height_model_bytes(4095, 4095, True) == 4_551_938_688
+    assert bench.per_height_model_bytes(4095, 4095, False) == 3_756_261_600
