@@ -104,13 +104,26 @@ __global__ void __launch_bounds__(512, 1) adj_fused_kernel(AdjFusedParams p) {
     for (int32_t k = warp; k < m; k += nwarps) {
       const int32_t b = ptr[k], e = ptr[k + 1];
       AccT* d = dst + (size_t)k * p.RP + p.PADL;
-      for (int32_t j = lane; j < TZin; j += 32) {
-        AccT acc = AccT(0);
-        for (int32_t t = b; t < e; t++) {
-          const MergeOp op = p.aops[t];
-          acc += src[(size_t)op.top * p.RP + p.PADL + j - op.s];
+      // one or two parent rows (a Brady-Yong level) with their row pointers
+      // taken once; the sum runs over the terms in the same order either way
+      if (e - b == 1) {
+        const MergeOp o0 = p.aops[b];
+        const AccT* s0 = src + (size_t)o0.top * p.RP + p.PADL - o0.s;
+        for (int32_t j = lane; j < TZin; j += 32) d[j] = AccT(0) + s0[j];
+      } else if (e - b == 2) {
+        const MergeOp o0 = p.aops[b], o1 = p.aops[b + 1];
+        const AccT* s0 = src + (size_t)o0.top * p.RP + p.PADL - o0.s;
+        const AccT* s1 = src + (size_t)o1.top * p.RP + p.PADL - o1.s;
+        for (int32_t j = lane; j < TZin; j += 32) d[j] = (AccT(0) + s0[j]) + s1[j];
+      } else {
+        for (int32_t j = lane; j < TZin; j += 32) {
+          AccT acc = AccT(0);
+          for (int32_t t = b; t < e; t++) {
+            const MergeOp op = p.aops[t];
+            acc += src[(size_t)op.top * p.RP + p.PADL + j - op.s];
+          }
+          d[j] = acc;
         }
-        d[j] = acc;
       }
     }
     AccT* tmp = src;
@@ -144,6 +157,9 @@ template <typename AccT>
 __global__ void __launch_bounds__(256) adj_upper_kernel(const AdjRow* __restrict__ rows, int64_t nrows,
                                                        const AdjTerm* __restrict__ terms, const AccT* ws_in,
                                                        AccT* ws_out, const AccT* __restrict__ gout) {
+  // every thread sums U elements of the row; each term is read once per U
+  // elements, and every element still adds its terms in order
+  constexpr int U = 4;
   for (int64_t k = blockIdx.x; k < nrows; k += gridDim.x) {
     const AdjRow R = rows[k];
     const bool fin = R.flags & ROW_FINAL;
@@ -151,25 +167,37 @@ __global__ void __launch_bounds__(256) adj_upper_kernel(const AdjRow* __restrict
     const bool neg = R.flags & ROW_NEG;
     const AccT* src = (fin ? gout : ws_in) + R.src;
     AccT* dst = ws_out + R.dst;
-    for (int32_t i = threadIdx.x; i < R.wdst; i += blockDim.x) {
-      AccT acc = AccT(0);
+    for (int32_t i0 = 0; i0 < R.wdst; i0 += (int32_t)blockDim.x * U) {
+      AccT acc[U];
+#pragma unroll
+      for (int q = 0; q < U; q++) acc[q] = AccT(0);
       for (int32_t c = 0; c < R.term_count; c++) {
         const AdjTerm T = terms[R.term_begin + c];
-        int32_t u = i + T.e;
-        if (ext) {
-          if (u < 0 || u >= R.wsrc) continue;
-        } else if (u >= R.W) {
-          u -= R.W;
+        const AccT* srow = src + (int64_t)T.t * R.src_pitch;
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+          const int32_t i = i0 + q * (int32_t)blockDim.x + (int32_t)threadIdx.x;
+          if (i >= R.wdst) continue;
+          int32_t u = i + T.e;
+          if (ext) {
+            if (u < 0 || u >= R.wsrc) continue;
+          } else if (u >= R.W) {
+            u -= R.W;
+          }
+          if (fin) {
+            int32_t X = neg ? R.kappa - u : u + R.kappa;
+            if (X < 0) X += R.W;
+            if (X >= R.W) X -= R.W;
+            u = X;
+          }
+          acc[q] += srow[u];
         }
-        if (fin) {
-          int32_t X = neg ? R.kappa - u : u + R.kappa;
-          if (X < 0) X += R.W;
-          if (X >= R.W) X -= R.W;
-          u = X;
-        }
-        acc += src[(int64_t)T.t * R.src_pitch + u];
       }
-      dst[i] = acc;
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const int32_t i = i0 + q * (int32_t)blockDim.x + (int32_t)threadIdx.x;
+        if (i < R.wdst) dst[i] = acc[q];
+      }
     }
   }
 }
