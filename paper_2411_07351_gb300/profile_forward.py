@@ -3,8 +3,10 @@
     python -m paper_2411_07351_gb300.profile_forward --h 2048 --w 2048 --reps 3
 
 Each rep launches the plan's kernels once (fused pass, then the band pass and
-the spine launches, or one pass per upper tree height).  Nothing is timed
-here; use it under ncu.
+the spine launches, or one pass per upper tree height); with --adjoint each
+rep also runs the adjoint (one pass per upper tree height, highest first, the
+fused subtrees in reverse, the sum of the quadrants' gradients).  Nothing is
+timed here; use it under ncu.
 """
 import argparse
 import ctypes
@@ -22,15 +24,19 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--dtype", choices=["f32", "u8"], default="f32")
     ap.add_argument("--boundary", choices=["cyclic", "extended"], default="extended")
+    ap.add_argument("--adjoint", action="store_true")
     a = ap.parse_args()
     if a.dtype == "f32":
         x = torch.from_numpy(inputs.normal_f32(2, a.h, a.w)).cuda()
     else:
         x = torch.from_numpy(inputs.uniform_u8(2, a.h, a.w)).cuda()
-    p = F.Plan(a.h, a.w, x.dtype, F.FHT_QALL, a.boundary)
-    out, ws = p.new_output(), p.new_workspace()
+    p = F.Plan(a.h, a.w, x.dtype, F.FHT_QALL, a.boundary, with_adjoint=a.adjoint)
+    out, ws = p.new_output(), p.new_workspace(adjoint=a.adjoint)
+    gin = torch.empty((a.h, a.w), dtype=p.out_dtype, device="cuda") if a.adjoint else None
     for _ in range(a.reps):
         p.forward(x, out, ws)
+        if a.adjoint:
+            p.adjoint(out, gin, ws)
     torch.cuda.synchronize()
     from paper_2411_07351_gb300 import _capi
 
