@@ -1,0 +1,87 @@
+"""Host logic of the serving loop (CPU only): readiness and admission.
+
+Requests are admitted in arrival order among those whose plans are built,
+while the device-memory budget (output + workspace of every admitted,
+unfinished request) has room; a request whose plan is still being built
+holds up only itself, and a request larger than the whole budget still runs
+when nothing else holds memory.  Plans and requests are stand-ins here: no
+GPU call is made.
+"""
+import collections
+import concurrent.futures as cf
+from types import SimpleNamespace
+
+from paper_2411_07351_gb300 import serve
+
+
+def _req(rid, out_elems, ws_bytes, ready=True):
+    f = cf.Future()
+    if ready:
+        f.set_result(SimpleNamespace(out_elems=out_elems, workspace_bytes=ws_bytes))
+    return serve.Request(rid=rid, arrival=float(rid), image=None, plan_future=f)
+
+
+def _server(budget):
+    s = serve.Server.__new__(serve.Server)  # admission state only, no streams or queues
+    s.waiting = collections.deque()
+    s.admitted = collections.deque()
+    s.used = 0
+    s.max_used = 0
+    s.budget = budget
+    return s
+
+
+def test_ready_in_order_skips_unbuilt_plans():
+    a, b, c = _req(0, 10, 600), _req(1, 10, 600, ready=False), _req(2, 5, 0)
+    got = serve._ready_in_order(collections.deque([a, b, c]))
+    assert [r.rid for r in got] == [0, 2]
+    assert a.nbytes == 10 * 4 + 600
+    assert c.nbytes == 5 * 4 + 256  # workspaces are at least 256 bytes
+    assert b.plan is None
+
+
+def test_ready_in_order_window():
+    reqs = [_req(k, 1, 256) for k in range(10)]
+    got = serve._ready_in_order(collections.deque(reqs), window=4)
+    assert [r.rid for r in got] == [0, 1, 2, 3]
+
+
+def test_admission_respects_budget_and_order():
+    s = _server(budget=2000)
+    reqs = [_req(k, 100, 600) for k in range(5)]  # 1000 bytes each
+    s.waiting.extend(reqs)
+    s._admit()
+    assert [r.rid for r in s.admitted] == [0, 1]
+    assert s.used == 2000 and s.max_used == 2000
+    assert [r.rid for r in s.waiting] == [2, 3, 4]
+    # a finished request frees its bytes; the next one in order is admitted
+    s.used -= reqs[0].nbytes
+    s._admit()
+    assert [r.rid for r in s.admitted] == [0, 1, 2]
+    assert s.used == 2000
+
+
+def test_unbuilt_plan_does_not_hold_up_later_requests():
+    s = _server(budget=10_000)
+    slow = _req(0, 100, 100, ready=False)
+    fast = [_req(k, 100, 100) for k in (1, 2)]
+    s.waiting.extend([slow] + fast)
+    s._admit()
+    assert [r.rid for r in s.admitted] == [1, 2]
+    assert [r.rid for r in s.waiting] == [0]
+    slow.plan_future.set_result(SimpleNamespace(out_elems=100, workspace_bytes=100))
+    s._admit()
+    assert [r.rid for r in s.admitted] == [1, 2, 0]
+
+
+def test_oversized_request_runs_alone():
+    s = _server(budget=100)
+    big, small = _req(0, 1000, 1000), _req(1, 1, 256)
+    s.waiting.extend([big, small])
+    s._admit()
+    # nothing held memory, so the oversized request is admitted; the next waits for it
+    assert [r.rid for r in s.admitted] == [0]
+    assert [r.rid for r in s.waiting] == [1]
+    s.used -= big.nbytes
+    s._admit()
+    assert [r.rid for r in s.admitted] == [0, 1]
