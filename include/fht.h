@@ -29,6 +29,18 @@
  *    message is available from fht_last_error() (per thread).
  *  - Calls that take a stream only enqueue work: they never synchronise and
  *    never allocate device memory.  The caller owns every buffer it passes.
+ *    One exception: the first fht_adjoint on a plan built without the
+ *    adjoint tables (fht_tuning_t.with_adjoint = 0) builds them, frees the
+ *    plan's old device tables and uploads new ones, synchronously.  Build
+ *    the plan with with_adjoint = 1, or make one adjoint call first, before
+ *    capturing adjoint calls into a CUDA graph.
+ *  - Threads: a plan may be used by several host threads at once for
+ *    fht_forward, fht_forward_timed, fht_plan_info and fht_submit jobs, and
+ *    its first fht_adjoint builds the adjoint tables under the plan's lock;
+ *    but no other call on the same plan may run while that first adjoint
+ *    call does.  A queue (fht_queue_t) or a pipe (fht_pipe_t) belongs to one
+ *    thread at a time.  fht_forward_noalloc calls share one scratch array
+ *    (see there).
  */
 #ifndef FHT_H
 #define FHT_H
