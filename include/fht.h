@@ -272,6 +272,29 @@ fht_status fht_pattern_errors(int32_t n_lo, int32_t n_hi, fht_split split, int64
  * FHT_OK, or FHT_ERR_INVALID with the first violation in fht_last_error(). */
 fht_status fht_plan_check(fht_plan_t plan);
 
+/* Host copies of a plan's tables, for inspection and host-side tests (no
+ * counterpart in the paper).  *data receives a pointer to `*count` elements
+ * of `*elem_size` bytes, owned by the plan and valid until fht_plan_destroy
+ * (or until a first fht_adjoint rebuilds the tables).  The element layouts
+ * are those of the library's internal descriptor header (csrc/fht_desc.h:
+ * QuadDesc, FusedItem, MergeOp, RowJob, SpineRow, SpineTerm) and are not a
+ * stable interface.  Offsets in the tables are element offsets into the
+ * output, or into the workspace after its 256-byte header.
+ * FHT_ERR_INVALID for a NULL argument or an unknown table. */
+typedef enum {
+  FHT_TABLE_QUADS = 0,        /* QuadDesc[4] (entries of absent quadrants are unused) */
+  FHT_TABLE_FUSED = 1,        /* FusedItem: fused subtrees (64-row blocks and the rest) */
+  FHT_TABLE_OPS = 2,          /* MergeOp: the fused subtrees' programs */
+  FHT_TABLE_ROWS = 3,         /* RowJob: per-height upper passes, pass after pass */
+  FHT_TABLE_PASS_BEGIN = 4,   /* int64: rows of pass p are [begin[p], begin[p + 1]) */
+  FHT_TABLE_BAND_ITEMS = 5,   /* FusedItem: band items (band schedule) */
+  FHT_TABLE_SPINE_ROWS = 6,   /* SpineRow (band schedule) */
+  FHT_TABLE_SPINE_TERMS = 7,  /* SpineTerm */
+  FHT_TABLE_SPINE_BEGIN = 8   /* int64: spine rows of launch k are [begin[k], begin[k + 1]) */
+} fht_table;
+
+fht_status fht_plan_table(fht_plan_t plan, fht_table table, const void** data, int64_t* count, int32_t* elem_size);
+
 /* Release a plan and its device tables.  NULL is accepted. */
 fht_status fht_plan_destroy(fht_plan_t plan);
 

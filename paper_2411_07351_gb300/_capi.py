@@ -18,6 +18,8 @@ FHT_U8_I32, FHT_I32_I32, FHT_F32_F32, FHT_F64_F64 = range(4)
 FHT_Q0, FHT_Q1, FHT_Q2, FHT_Q3, FHT_QALL = 1, 2, 4, 8, 15
 FHT_CYCLIC, FHT_EXTENDED = 0, 1
 FHT_SPLIT_T, FHT_SPLIT_S = 0, 1
+FHT_TABLE_QUADS, FHT_TABLE_FUSED, FHT_TABLE_OPS, FHT_TABLE_ROWS, FHT_TABLE_PASS_BEGIN, FHT_TABLE_BAND_ITEMS, \
+    FHT_TABLE_SPINE_ROWS, FHT_TABLE_SPINE_TERMS, FHT_TABLE_SPINE_BEGIN = range(9)
 
 
 class fht_tuning_t(ctypes.Structure):
@@ -53,6 +55,8 @@ SIGNATURES = {
     "fht_plan_info": (ctypes.c_int, [_vp, ctypes.POINTER(fht_plan_info_t)]),
     "fht_forward": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _sz, _vp]),
     "fht_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _sz, _vp]),
+    "fht_plan_table": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_i64),
+                                      ctypes.POINTER(_i32)]),
     "fht_plan_check": (ctypes.c_int, [_vp]),
     "fht_plan_launches": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "fht_plan_launch_info": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),

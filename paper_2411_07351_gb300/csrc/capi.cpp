@@ -326,6 +326,41 @@ fht_status fht_plan_check(fht_plan_t plan) {
   return FHT_OK;
 }
 
+fht_status fht_plan_table(fht_plan_t plan, fht_table table, const void** data, int64_t* count, int32_t* elem_size) {
+  if (!plan || !data || !count || !elem_size) return fail(FHT_ERR_INVALID, "fht_plan_table: NULL argument");
+  const fht::HostPlan& P = plan->host;
+  auto give = [&](const auto& v) {
+    *data = v.data();
+    *count = (int64_t)v.size();
+    *elem_size = (int32_t)sizeof(v[0]);
+    return FHT_OK;
+  };
+  switch (table) {
+    case FHT_TABLE_QUADS:
+      *data = P.quad;
+      *count = 4;
+      *elem_size = (int32_t)sizeof(P.quad[0]);
+      return FHT_OK;
+    case FHT_TABLE_FUSED:
+      return give(P.fused);
+    case FHT_TABLE_OPS:
+      return give(P.ops);
+    case FHT_TABLE_ROWS:
+      return give(P.rows);
+    case FHT_TABLE_PASS_BEGIN:
+      return give(P.pass_begin);
+    case FHT_TABLE_BAND_ITEMS:
+      return give(P.band_items);
+    case FHT_TABLE_SPINE_ROWS:
+      return give(P.spine_rows);
+    case FHT_TABLE_SPINE_TERMS:
+      return give(P.spine_terms);
+    case FHT_TABLE_SPINE_BEGIN:
+      return give(P.spine_pass_begin);
+  }
+  return fail(FHT_ERR_INVALID, "fht_plan_table: unknown table");
+}
+
 fht_status fht_plan_destroy(fht_plan_t plan) {
   if (!plan) return FHT_OK;
   if (plan->dev.device < 0) {

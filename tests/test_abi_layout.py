@@ -26,7 +26,9 @@ STRUCTS = {
 CONSTANTS = ["FHT_OK", "FHT_ERR_INVALID", "FHT_ERR_NOMEM", "FHT_ERR_CUDA", "FHT_ERR_TIMEOUT", "FHT_ERR_BUSY",
              "FHT_ERR_UNSUPPORTED", "FHT_ERR_DEVICE", "FHT_U8_I32", "FHT_I32_I32", "FHT_F32_F32", "FHT_F64_F64",
              "FHT_Q0", "FHT_Q1", "FHT_Q2", "FHT_Q3", "FHT_QALL", "FHT_CYCLIC", "FHT_EXTENDED", "FHT_SPLIT_T",
-             "FHT_SPLIT_S", "FHT_JOB_WITHHOLD_DEPENDENCY"]
+             "FHT_SPLIT_S", "FHT_JOB_WITHHOLD_DEPENDENCY", "FHT_TABLE_QUADS", "FHT_TABLE_FUSED", "FHT_TABLE_OPS",
+             "FHT_TABLE_ROWS", "FHT_TABLE_PASS_BEGIN", "FHT_TABLE_BAND_ITEMS", "FHT_TABLE_SPINE_ROWS",
+             "FHT_TABLE_SPINE_TERMS", "FHT_TABLE_SPINE_BEGIN"]
 
 
 @pytest.fixture(scope="module")
