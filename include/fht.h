@@ -277,9 +277,12 @@ fht_status fht_plan_check(fht_plan_t plan);
  * of `*elem_size` bytes, owned by the plan and valid until fht_plan_destroy
  * (or until a first fht_adjoint rebuilds the tables).  The element layouts
  * are those of the library's internal descriptor header (csrc/fht_desc.h:
- * QuadDesc, FusedItem, MergeOp, RowJob, SpineRow, SpineTerm) and are not a
+ * QuadDesc, FusedItem, MergeOp, RowJob, SpineRow, SpineTerm, AdjRow,
+ * AdjTerm) and are not a
  * stable interface.  Offsets in the tables are element offsets into the
- * output, or into the workspace after its 256-byte header.
+ * output, or into the workspace after its 256-byte header.  The adjoint
+ * tables are empty until the plan has them (with_adjoint = 1, or after a
+ * first fht_adjoint).
  * FHT_ERR_INVALID for a NULL argument or an unknown table. */
 typedef enum {
   FHT_TABLE_QUADS = 0,        /* QuadDesc[4] (entries of absent quadrants are unused) */
@@ -290,7 +293,12 @@ typedef enum {
   FHT_TABLE_BAND_ITEMS = 5,   /* FusedItem: band items (band schedule) */
   FHT_TABLE_SPINE_ROWS = 6,   /* SpineRow (band schedule) */
   FHT_TABLE_SPINE_TERMS = 7,  /* SpineTerm */
-  FHT_TABLE_SPINE_BEGIN = 8   /* int64: spine rows of launch k are [begin[k], begin[k + 1]) */
+  FHT_TABLE_SPINE_BEGIN = 8,  /* int64: spine rows of launch k are [begin[k], begin[k + 1]) */
+  FHT_TABLE_ADJ_ROWS = 9,     /* AdjRow: adjoint per-height passes, highest first */
+  FHT_TABLE_ADJ_TERMS = 10,   /* AdjTerm */
+  FHT_TABLE_ADJ_BEGIN = 11,   /* int64: adjoint rows of pass p are [begin[p], begin[p + 1]) */
+  FHT_TABLE_ADJ_PTR = 12,     /* int32: fused adjoint programs, row pointers into FHT_TABLE_ADJ_OPS */
+  FHT_TABLE_ADJ_OPS = 13      /* MergeOp: (top = forward row, s = shift) terms of the fused adjoint */
 } fht_table;
 
 fht_status fht_plan_table(fht_plan_t plan, fht_table table, const void** data, int64_t* count, int32_t* elem_size);

@@ -19,7 +19,8 @@ FHT_Q0, FHT_Q1, FHT_Q2, FHT_Q3, FHT_QALL = 1, 2, 4, 8, 15
 FHT_CYCLIC, FHT_EXTENDED = 0, 1
 FHT_SPLIT_T, FHT_SPLIT_S = 0, 1
 FHT_TABLE_QUADS, FHT_TABLE_FUSED, FHT_TABLE_OPS, FHT_TABLE_ROWS, FHT_TABLE_PASS_BEGIN, FHT_TABLE_BAND_ITEMS, \
-    FHT_TABLE_SPINE_ROWS, FHT_TABLE_SPINE_TERMS, FHT_TABLE_SPINE_BEGIN = range(9)
+    FHT_TABLE_SPINE_ROWS, FHT_TABLE_SPINE_TERMS, FHT_TABLE_SPINE_BEGIN, FHT_TABLE_ADJ_ROWS, FHT_TABLE_ADJ_TERMS, \
+    FHT_TABLE_ADJ_BEGIN, FHT_TABLE_ADJ_PTR, FHT_TABLE_ADJ_OPS = range(14)
 
 
 class fht_tuning_t(ctypes.Structure):

@@ -357,6 +357,16 @@ fht_status fht_plan_table(fht_plan_t plan, fht_table table, const void** data, i
       return give(P.spine_terms);
     case FHT_TABLE_SPINE_BEGIN:
       return give(P.spine_pass_begin);
+    case FHT_TABLE_ADJ_ROWS:
+      return give(P.arows);
+    case FHT_TABLE_ADJ_TERMS:
+      return give(P.aterms);
+    case FHT_TABLE_ADJ_BEGIN:
+      return give(P.apass_begin);
+    case FHT_TABLE_ADJ_PTR:
+      return give(P.aptr);
+    case FHT_TABLE_ADJ_OPS:
+      return give(P.aops);
   }
   return fail(FHT_ERR_INVALID, "fht_plan_table: unknown table");
 }

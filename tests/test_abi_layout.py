@@ -28,7 +28,8 @@ CONSTANTS = ["FHT_OK", "FHT_ERR_INVALID", "FHT_ERR_NOMEM", "FHT_ERR_CUDA", "FHT_
              "FHT_Q0", "FHT_Q1", "FHT_Q2", "FHT_Q3", "FHT_QALL", "FHT_CYCLIC", "FHT_EXTENDED", "FHT_SPLIT_T",
              "FHT_SPLIT_S", "FHT_JOB_WITHHOLD_DEPENDENCY", "FHT_TABLE_QUADS", "FHT_TABLE_FUSED", "FHT_TABLE_OPS",
              "FHT_TABLE_ROWS", "FHT_TABLE_PASS_BEGIN", "FHT_TABLE_BAND_ITEMS", "FHT_TABLE_SPINE_ROWS",
-             "FHT_TABLE_SPINE_TERMS", "FHT_TABLE_SPINE_BEGIN"]
+             "FHT_TABLE_SPINE_TERMS", "FHT_TABLE_SPINE_BEGIN", "FHT_TABLE_ADJ_ROWS", "FHT_TABLE_ADJ_TERMS",
+             "FHT_TABLE_ADJ_BEGIN", "FHT_TABLE_ADJ_PTR", "FHT_TABLE_ADJ_OPS"]
 
 
 @pytest.fixture(scope="module")

@@ -337,3 +337,103 @@ def test_tables_follow_the_rounding_rule(F, orc, h, w, differ):
     assert np.array_equal(exact, orc.fht(img.astype(np.int64), 15, orc.EXTENDED))
     assert np.array_equal(flt, ref_float)
     assert np.array_equal(exact, flt) != differ
+
+
+ADJ_ROW = np.dtype({"names": ["dst", "src", "src_pitch", "wdst", "wsrc", "W", "flags", "kappa", "term_begin",
+                              "term_count"], "formats": ["<i8"] * 2 + ["<i4"] * 8}, align=True)
+ADJ_TERM = np.dtype({"names": ["t", "e"], "formats": ["<i4"] * 2}, align=True)
+DTYPES.update({"AdjRow": ADJ_ROW, "AdjTerm": ADJ_TERM})
+
+
+def _adjoint_tables(F, plan):
+    from paper_2411_07351_gb300 import _capi as C
+
+    T = _tables(F, plan)
+    T.update({
+        "arows": _table(F, plan, C.FHT_TABLE_ADJ_ROWS, ADJ_ROW),
+        "aterms": _table(F, plan, C.FHT_TABLE_ADJ_TERMS, ADJ_TERM),
+        "abegin": _table(F, plan, C.FHT_TABLE_ADJ_BEGIN, np.dtype("<i8")),
+        "aptr": _table(F, plan, C.FHT_TABLE_ADJ_PTR, np.dtype("<i4")),
+        "aops": _table(F, plan, C.FHT_TABLE_ADJ_OPS, MERGE),
+    })
+    return T
+
+
+def _execute_adjoint(F, plan, gout):
+    """The adjoint schedule from the tables: per-height gather passes (highest
+    first), then every fused subtree's levels in reverse, then the sum of the
+    quadrants' image gradients."""
+    T = _adjoint_tables(F, plan)
+    h, w = plan.h, plan.w
+    ws = np.zeros((plan.adjoint_workspace_bytes - 256) // 4, dtype=np.int64)
+    ab, terms = T["abegin"], T["aterms"]
+    for p in range(len(ab) - 1):
+        for R in T["arows"][ab[p]: ab[p + 1]]:
+            src = gout if R["flags"] & ROW_FINAL else ws
+            i = np.arange(R["wdst"])
+            acc = np.zeros(R["wdst"], dtype=np.int64)
+            for k in terms[R["term_begin"]: R["term_begin"] + R["term_count"]]:
+                u = i + k["e"]
+                if R["flags"] & ROW_EXT:
+                    ok = (u >= 0) & (u < R["wsrc"])
+                else:
+                    ok = np.ones_like(u, dtype=bool)
+                    u = np.mod(u, R["W"])
+                if R["flags"] & ROW_FINAL:
+                    u = np.mod(R["kappa"] - u if R["flags"] & ROW_NEG else u + R["kappa"], R["W"])
+                vals = src[R["src"] + k["t"] * int(R["src_pitch"]) + np.clip(u, 0, None)]
+                acc += np.where(ok, vals, 0)
+            ws[R["dst"] + i] = acc
+    for it in T["fused"]:
+        Q = T["quads"][it["q"]]
+        m, c, wn, L = int(it["m"]), int(it["c"]), int(it["wn"]), int(Q["L"])
+        x = np.arange(-(m - 1), L)  # view columns: the gradient reaches m - 1 columns left of the row
+        u = x + c
+        ok = (u >= 0) & (u < wn) if Q["ext"] else np.ones_like(u, dtype=bool)
+        u = np.clip(u, 0, wn - 1) if Q["ext"] else np.mod(u, Q["W"])
+        cur = np.zeros((m, len(x)), dtype=np.int64)
+        for r in range(m):
+            if it["final_"]:
+                X = np.mod(Q["sigma"] * u + Q["kappa"], Q["W"])
+                cur[r] = np.where(ok, gout[it["dst"] + r * Q["W"] + X], 0)
+            else:
+                cur[r] = np.where(ok, ws[it["dst"] + r * it["dst_pitch"] + u], 0)
+        for lev in range(it["nlev"] - 1, -1, -1):
+            ptr = T["aptr"][it["aprog"] + lev * (m + 1): it["aprog"] + (lev + 1) * (m + 1)]
+            nxt = np.zeros_like(cur)
+            for k in range(m):
+                for op in T["aops"][ptr[k]: ptr[k + 1]]:
+                    s = int(op["s"])
+                    nxt[k, s:] += cur[op["top"], : len(x) - s]  # g[k][j] += g'[top][j - s]
+            cur = nxt
+        z = np.arange(L)
+        zz = L - 1 - z if Q["flip"] else z
+        for r in range(m):
+            leaf = cur[r, z + m - 1]
+            if Q["transpose"]:
+                ws[Q["grad_off"] + zz * w + it["a"] + r] = leaf
+            else:
+                ws[Q["grad_off"] + (it["a"] + r) * w + zz] = leaf
+    gin = np.zeros((h, w), dtype=np.int64)
+    for q in range(4):
+        if plan.quads & (1 << q):
+            off = int(T["quads"][q]["grad_off"])
+            gin += ws[off: off + h * w].reshape(h, w)
+    return gin
+
+
+ADJ = [(h, w, b, s, fr) for (h, w) in [(1, 1), (1, 6), (7, 1), (5, 3), (17, 13), (40, 70), (100, 37), (131, 45)]
+       for b in ("cyclic", "extended") for (s, fr) in (("T", 0), ("S", 0), ("T", 16))]
+
+
+@pytest.mark.parametrize("h,w,boundary,split,fused_rows", ADJ)
+def test_adjoint_tables_give_the_oracle_adjoint(F, orc, h, w, boundary, split, fused_rows):
+    import torch
+
+    plan = F.Plan(h, w, torch.uint8, F.FHT_QALL, boundary, split=split, fused_rows=fused_rows, with_adjoint=True,
+                  device=-1)
+    gout = np.random.default_rng(h * 31 + w).integers(-50, 50, size=plan.out_elems).astype(np.int64)
+    got = _execute_adjoint(F, plan, gout)
+    ref = orc.adjoint(gout.astype(np.float64), h, w, 15, orc.EXTENDED if boundary == "extended" else orc.CYCLIC,
+                      orc.SPLIT_S if split == "S" else orc.SPLIT_T)
+    assert np.array_equal(got, ref.astype(np.int64)), f"{(got != ref).sum()} of {got.size} differ"
