@@ -437,3 +437,32 @@ def test_adjoint_tables_give_the_oracle_adjoint(F, orc, h, w, boundary, split, f
     ref = orc.adjoint(gout.astype(np.float64), h, w, 15, orc.EXTENDED if boundary == "extended" else orc.CYCLIC,
                       orc.SPLIT_S if split == "S" else orc.SPLIT_T)
     assert np.array_equal(got, ref.astype(np.int64)), f"{(got != ref).sum()} of {got.size} differ"
+
+
+def _sweep(n, seed):
+    rng = np.random.default_rng(seed)
+    cases = []
+    for _ in range(n):
+        h, w = (int(v) for v in rng.integers(1, 400, size=2))
+        split = "S" if rng.random() < 0.3 else "T"
+        fr = int(rng.choice([0, 0, 8, 16, 32]))
+        boundary = "extended" if rng.random() < 0.5 else "cyclic"
+        quads = int(rng.integers(1, 16))
+        cases.append((h, w, boundary, split, fr, quads))
+    return cases
+
+
+@pytest.mark.parametrize("h,w,boundary,split,fused_rows,quads", _sweep(30, 2024))
+def test_random_shapes_forward_and_adjoint(F, orc, h, w, boundary, split, fused_rows, quads):
+    import torch
+
+    b = orc.EXTENDED if boundary == "extended" else orc.CYCLIC
+    rule = orc.SPLIT_S if split == "S" else orc.SPLIT_T
+    plan = F.Plan(h, w, torch.uint8, quads, boundary, split=split, fused_rows=fused_rows, with_adjoint=True,
+                  device=-1)
+    rng = np.random.default_rng(h * 7919 + w)
+    img = rng.integers(0, 256, size=(h, w)).astype(np.uint8)
+    assert np.array_equal(_execute(F, plan, img), orc.fht(img.astype(np.int64), quads, b, rule))
+    gout = rng.integers(-50, 50, size=plan.out_elems).astype(np.int64)
+    ref = orc.adjoint(gout.astype(np.float64), h, w, quads, b, rule)
+    assert np.array_equal(_execute_adjoint(F, plan, gout), ref.astype(np.int64))
