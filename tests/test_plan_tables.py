@@ -466,3 +466,27 @@ def test_random_shapes_forward_and_adjoint(F, orc, h, w, boundary, split, fused_
     gout = rng.integers(-50, 50, size=plan.out_elems).astype(np.int64)
     ref = orc.adjoint(gout.astype(np.float64), h, w, quads, b, rule)
     assert np.array_equal(_execute_adjoint(F, plan, gout), ref.astype(np.int64))
+
+
+@pytest.mark.parametrize("split", ["T", "S"])
+@pytest.mark.parametrize("boundary", ["cyclic", "extended"])
+def test_64_row_blocks_are_classical_brady_yong(F, split, boundary):
+    """The 64-row block kernel does not read its program: it merges adjacent
+    blocks of M rows as  out[2M g + t] = in[2M g + t//2] + in[2M g + M + t//2]
+    shifted by ceil(t/2), six times.  Every 64-row item's program in the plan
+    (which the host interpreter above runs and checks against the oracle) must
+    be exactly that."""
+    import torch
+
+    plan = F.Plan(300, 200, torch.uint8, 15, boundary, split=split, device=-1)
+    T = _tables(F, plan)
+    items = [it for it in T["fused"] if it["kind"] == FUSED_BY64]
+    assert items and all(it["m"] == 64 and it["nlev"] == 6 for it in items)
+    for it in items:
+        prog = T["ops"][it["prog"]: it["prog"] + 6 * 64].reshape(6, 64)
+        for lev in range(6):
+            M = 1 << lev
+            for r in range(64):
+                g, t = divmod(r, 2 * M)
+                op = prog[lev][r]
+                assert (op["top"], op["bot"], op["s"]) == (2 * M * g + t // 2, 2 * M * g + M + t // 2, (t + 1) // 2)
