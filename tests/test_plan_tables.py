@@ -478,7 +478,9 @@ def test_64_row_blocks_are_classical_brady_yong(F, split, boundary):
     be exactly that."""
     import torch
 
-    plan = F.Plan(300, 200, torch.uint8, 15, boundary, split=split, device=-1)
+    # Split_S halves, so it makes 64-row subtrees only under heights 64 * 2^k
+    h, w = (300, 200) if split == "T" else (256, 320)
+    plan = F.Plan(h, w, torch.uint8, 15, boundary, split=split, device=-1)
     T = _tables(F, plan)
     items = [it for it in T["fused"] if it["kind"] == FUSED_BY64]
     assert items and all(it["m"] == 64 and it["nlev"] == 6 for it in items)
