@@ -492,3 +492,69 @@ def test_64_row_blocks_are_classical_brady_yong(F, split, boundary):
                 g, t = divmod(r, 2 * M)
                 op = prog[lev][r]
                 assert (op["top"], op["bot"], op["s"]) == (2 * M * g + t // 2, 2 * M * g + M + t // 2, (t + 1) // 2)
+
+
+def _launch_bytes_from_tables(T, in_size, acc):
+    """Compulsory bytes of every forward launch, counted from the tables: the
+    distinct rows a launch reads (each at its row width) and the rows it
+    writes, once each."""
+    Qs = T["quads"]
+    fused = sum(int(it["m"]) * int(Qs[it["q"]]["L"]) * in_size + int(it["m"]) * int(it["wn"]) * acc
+                for it in T["fused"])
+    launches = [fused]
+    if len(T["band_items"]) or len(T["spine_rows"]):
+        if len(T["band_items"]):
+            reads, writes = set(), 0
+            for it in T["band_items"]:
+                B, G = int(it["B"]), 64 // int(it["B"])
+                for g in range(G):
+                    for b in range(B):
+                        reads.add((int(it["src"]) + (64 * b + int(it["K0"]) + g) * int(it["src_pitch"]),
+                                   int(it["wsrc"])))
+                writes += G * B * int(it["wn"])
+            launches.append((sum(wd for _, wd in reads) + writes) * acc)
+        sb, terms = T["spine_begin"], T["spine_terms"]
+        for p in range(len(sb) - 1):
+            rows = T["spine_rows"][sb[p]: sb[p + 1]]
+            if len(rows) == 0:
+                continue
+            reads = {(int(S["row"]), int(S["wpart"])) for R in rows
+                     for S in terms[R["term_begin"]: R["term_begin"] + R["term_count"]]}
+            launches.append((sum(wd for _, wd in reads) + sum(int(R["w"]) for R in rows)) * acc)
+    else:
+        pb = T["pass_begin"]
+        for p in range(len(pb) - 1):
+            rows = T["rows"][pb[p]: pb[p + 1]]
+            if len(rows) == 0:
+                continue
+            reads = {(int(J["top"]), int(J["wtop"])) for J in rows} | {(int(J["bot"]), int(J["wbot"])) for J in rows}
+            launches.append((sum(wd for _, wd in reads) + sum(int(J["wout"]) for J in rows)) * acc)
+    return launches
+
+
+@pytest.mark.parametrize("h,w,boundary,split,dtype", [
+    (4095, 4095, "extended", "T", "float32"), (4095, 4095, "cyclic", "T", "float32"),
+    (2047, 300, "extended", "T", "uint8"), (8300, 3, "cyclic", "T", "uint8"),
+    (1000, 700, "extended", "S", "float32"), (257, 257, "cyclic", "T", "uint8")])
+def test_launch_model_bytes_match_the_tables(F, h, w, boundary, split, dtype):
+    """The per-launch model bytes the bench divides by each launch's time
+    (fht_plan_launch_info) equal the distinct rows each launch reads and
+    writes according to its own tables."""
+    import torch
+
+    from paper_2411_07351_gb300 import _capi as C
+
+    tdt = {"float32": torch.float32, "uint8": torch.uint8}[dtype]
+    plan = F.Plan(h, w, tdt, F.FHT_QALL, boundary, split=split, device=-1)
+    T = _tables(F, plan)
+    want = _launch_bytes_from_tables(T, 4 if dtype == "float32" else 1, 4)
+    lib = C.load()
+    n = ctypes.c_int32()
+    C.check(lib.fht_plan_launches(plan._h, ctypes.byref(n)), "fht_plan_launches")
+    got = []
+    for k in range(n.value):
+        kind, by = ctypes.c_int32(), ctypes.c_int64()
+        C.check(lib.fht_plan_launch_info(plan._h, k, ctypes.byref(kind), ctypes.byref(by)), "fht_plan_launch_info")
+        got.append(by.value)
+    assert got == want
+    assert sum(got) == plan.info.model_bytes
