@@ -558,3 +558,24 @@ def test_launch_model_bytes_match_the_tables(F, h, w, boundary, split, dtype):
         got.append(by.value)
     assert got == want
     assert sum(got) == plan.info.model_bytes
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 17, 64, 100, 257, 1000])
+@pytest.mark.parametrize("split,fused_rows", [("T", 32), ("T", 8), ("S", 0)])
+def test_executed_additions_are_theorem_1(F, orc, n, split, fused_rows):
+    """Cyclic, one quadrant, per-height schedule: every merged row is one
+    addition per column, so the additions the tables perform (fused programs'
+    merged rows and per-height rows, W columns each) are Theorem 1's f(n)."""
+    import torch
+
+    plan = F.Plan(n, n, torch.uint8, F.FHT_Q0, "cyclic", split=split, fused_rows=fused_rows, device=-1)
+    T = _tables(F, plan)
+    assert len(T["spine_rows"]) == 0
+    W = n
+    merged = 0
+    for it in T["fused"]:
+        ops = T["ops"][it["prog"]: it["prog"] + it["nlev"] * it["m"]]
+        merged += int((ops["bot"] >= 0).sum())
+    merged += len(T["rows"])
+    rule = orc.SPLIT_S if split == "S" else orc.SPLIT_T
+    assert merged * W == orc.adds(n, rule) == plan.info.adds
