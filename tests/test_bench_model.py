@@ -7,7 +7,13 @@ node above the leaves reading its two children and writing its own rows.  Row
 widths are L + m - 1 for an m-row node with the extended boundary and L with
 the cyclic one (Section 2).  The sums below are written out by hand for small
 trees; the 4095 x 4095 figures are the ones the bench quotes.
+
+Also: the bench reports a kernel's captured DRAM traffic only while the
+forward kernels' sources hash as they did at the capture, and takes its peak
+from the measured copy bandwidth when there is one, else the fallback.
 """
+import os
+
 import bench
 
 
@@ -43,3 +49,42 @@ def test_uneven_split_and_transposed_quadrants():
 def test_headline_figures():
     assert bench.per_height_model_bytes(4095, 4095, True) == 4_551_938_688
     assert bench.per_height_model_bytes(4095, 4095, False) == 3_756_261_600
+
+
+def _fake_root(tmp_path, traffic_hash=None, peaks=None):
+    import json
+    import shutil
+
+    csrc = tmp_path / "paper_2411_07351_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for fn in bench.FORWARD_SOURCES:
+        shutil.copy(os.path.join(bench.ROOT, "paper_2411_07351_gb300", "csrc", fn), csrc / fn)
+    (tmp_path / "profiles").mkdir()
+    if traffic_hash is not None:
+        (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(
+            {"c2-extended": {"fused_kernel": {"source_hash": traffic_hash, "dram_bytes_per_launch": 123}}}))
+    if peaks is not None:
+        (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps(peaks))
+    return str(tmp_path)
+
+
+def test_traffic_only_for_the_captured_sources(tmp_path, monkeypatch):
+    root = _fake_root(tmp_path / "a", traffic_hash="0" * 16)
+    monkeypatch.setattr(bench, "ROOT", root)
+    assert bench._traffic("fused_kernel", "c2-extended") is None  # taken on other sources
+    root = _fake_root(tmp_path / "c", traffic_hash=bench._source_hash())
+    monkeypatch.setattr(bench, "ROOT", root)
+    assert bench._traffic("fused_kernel", "c2-extended") == 123
+    assert bench._traffic("band_kernel", "c2-extended") is None
+    # any change to a forward source voids the figure
+    src = os.path.join(root, "paper_2411_07351_gb300", "csrc", "fht_forward.cu")
+    with open(src, "a") as f:
+        f.write("\n// changed\n")
+    assert bench._traffic("fused_kernel", "c2-extended") is None
+
+
+def test_peak_is_measured_else_the_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", _fake_root(tmp_path / "a", peaks={"hbm_gbs": 6697.2}))
+    assert bench._peaks() == (6697.2, "measured")
+    monkeypatch.setattr(bench, "ROOT", _fake_root(tmp_path / "b"))
+    assert bench._peaks() == (6800.0, "fallback")
