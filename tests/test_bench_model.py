@@ -9,8 +9,9 @@ the cyclic one (Section 2).  The sums below are written out by hand for small
 trees; the 4095 x 4095 figures are the ones the bench quotes.
 
 Also: the bench reports a kernel's captured DRAM traffic only while the
-forward kernels' sources hash as they did at the capture, and takes its peak
-from the measured copy bandwidth when there is one, else the fallback.
+forward kernels' sources hash as they did at the capture, takes its peak
+from the measured copy bandwidth when there is one, else the fallback, and
+reads the median SM clock and the throttle reasons from its clock samples.
 """
 import os
 
@@ -88,3 +89,34 @@ def test_peak_is_measured_else_the_fallback(tmp_path, monkeypatch):
     assert bench._peaks() == (6697.2, "measured")
     monkeypatch.setattr(bench, "ROOT", _fake_root(tmp_path / "b"))
     assert bench._peaks() == (6800.0, "fallback")
+
+
+class _DoneProcess:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_samples_give_median_and_throttle_reasons(tmp_path):
+    # nvidia-smi --format=csv,noheader,nounits lines of the fields in bench.CLOCK_FIELDS
+    path = tmp_path / "clocks.csv"
+    path.write_text(
+        "0, 2070, 2070, 330.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 1980, 2070, 900.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+        "0, 2070, 2070, 310.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "garbage line\n"
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    d = bench.clocks_stop((_DoneProcess(), str(path)))
+    assert d["sm_mhz"] == 2070 and d["sm_max_mhz"] == 2070 and d["samples"] == 3
+    assert d["power_w_max"] == 900.0
+    assert d["reasons"] == ["sw_power_cap"]  # kept and noted; not a reason to reject
+    path.write_text("0, 1200, 2070, 500.0, 0x8, Active, Not Active, Active, Not Active\n")
+    d = bench.clocks_stop((_DoneProcess(), str(path)))
+    assert d["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and d["sm_mhz"] == 1200
+
+
+def test_no_nvidia_smi_is_reported():
+    d = bench.clocks_stop((None, "unused"))
+    assert d["sm_mhz"] is None and d["reasons"] == ["nvidia-smi unavailable"]
