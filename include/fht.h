@@ -165,8 +165,18 @@ fht_status fht_forward_timed(fht_plan_t plan, const void* d_in, int64_t in_pitch
  *  - All calls share the one array, which keeps the last call's contents:
  *    calls whose kernels overlap on the GPU (different streams without
  *    ordering between them) race on it.  Order them on one stream.
- *  - Arguments, output and errors as for fht_forward. */
+ *  - The looked-up address is kept for the life of the process: do not
+ *    call it on a device after cudaDeviceReset there.
+ *  - Arguments, output and errors as for fht_forward; the device-side status
+ *    word (a bulk-copy wait that ran out) is read with fht_noalloc_status. */
 fht_status fht_forward_noalloc(fht_plan_t plan, const void* d_in, int64_t in_pitch, void* d_out, void* stream);
+
+/* Device-side status of the last fht_forward_noalloc on `device`: what
+ * fht_ws_status reports for a caller's own workspace, read from the built-in
+ * scratch.  FHT_OK, or FHT_ERR_TIMEOUT when a launch's bounded wait for its
+ * bulk copies ran out and left part of the output unwritten.  Synchronises
+ * `stream`; allocates nothing. */
+fht_status fht_noalloc_status(int device, void* stream);
 
 /* ---- host-memory pipeline ----
  * Forward transforms of images held in host memory, the copies included:

@@ -63,6 +63,7 @@ SIGNATURES = {
     "fht_plan_launch_info": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "fht_forward_timed": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp), _i32]),
     "fht_forward_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "fht_noalloc_status": (ctypes.c_int, [ctypes.c_int, _vp]),
     "fht_plan_destroy": (ctypes.c_int, [_vp]),
     "fht_pattern_errors": (ctypes.c_int, [_i32, _i32, ctypes.c_int, _vp, _vp]),
     "fht_queue_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i32, _i64]),

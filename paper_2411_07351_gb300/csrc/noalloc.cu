@@ -35,6 +35,19 @@ fht_status fht_capi_fail(fht_status st, const std::string& msg);
 struct fht_plan_s;
 const fht::DevicePlan* fht_capi_device_plan(fht_plan_t plan);
 
+// The array's device address on `device` (looked up once, with that device
+// current; the caller has made it current).
+static cudaError_t scratch_address(int device, void** out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  cudaError_t e = cudaSuccess;
+  if (!g_scratch_ptr[device]) {
+    e = cudaGetSymbolAddress(&g_scratch_ptr[device], g_noalloc_scratch);
+    if (e != cudaSuccess) g_scratch_ptr[device] = nullptr;
+  }
+  *out = g_scratch_ptr[device];
+  return e;
+}
+
 extern "C" fht_status fht_forward_noalloc(fht_plan_t plan, const void* d_in, int64_t in_pitch, void* d_out,
                                           void* stream) {
   const fht::DevicePlan* D = fht_capi_device_plan(plan);
@@ -55,24 +68,34 @@ extern "C" fht_status fht_forward_noalloc(fht_plan_t plan, const void* d_in, int
   if (e != cudaSuccess) return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_forward_noalloc: ") + cudaGetErrorString(e));
   if (prev != D->device && (e = cudaSetDevice(D->device)) != cudaSuccess)
     return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_forward_noalloc: ") + cudaGetErrorString(e));
+  // one-time set-up per device, with that device current: the array's
+  // device address (its name in host code is only a host-side stand-in)
   void* scratch = nullptr;
-  {
-    // one-time set-up per device, with that device current: the array's
-    // device address (its name in host code is only a host-side stand-in)
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[D->device]) {
-      e = cudaGetSymbolAddress(&g_scratch_ptr[D->device], g_noalloc_scratch);
-      if (e != cudaSuccess) g_scratch_ptr[D->device] = nullptr;
-    }
-    scratch = g_scratch_ptr[D->device];
-  }
-  if (e == cudaSuccess && scratch) {
-    // the status header is the only part that must start at zero
-    e = cudaMemsetAsync(scratch, 0, fht::kWsHeader, (cudaStream_t)stream);
-    if (e == cudaSuccess) e = fht::launch_forward(*D, d_in, in_pitch, d_out, scratch, (cudaStream_t)stream);
-  }
+  e = scratch_address(D->device, &scratch);
+  // Nothing in the scratch needs clearing here: the first launch of every
+  // forward resets the status word at its start, and every other byte is
+  // written before it is read within the same forward.
+  if (e == cudaSuccess && scratch)
+    e = fht::launch_forward(*D, d_in, in_pitch, d_out, scratch, (cudaStream_t)stream);
   if (prev >= 0 && prev != D->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_forward_noalloc: ") + cudaGetErrorString(e));
   if (!scratch) return fht_capi_fail(FHT_ERR_CUDA, "fht_forward_noalloc: scratch address unavailable");
   return FHT_OK;
+}
+
+// The device-side status word of the last fht_forward_noalloc on `device`
+// (the same word fht_ws_status reads from a caller's workspace).
+extern "C" fht_status fht_noalloc_status(int device, void* stream) {
+  if (device < 0 || device >= kMaxDevices) return fht_capi_fail(FHT_ERR_INVALID, "fht_noalloc_status: bad device");
+  int prev = -1;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e != cudaSuccess) return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_noalloc_status: ") + cudaGetErrorString(e));
+  if (prev != device && (e = cudaSetDevice(device)) != cudaSuccess)
+    return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_noalloc_status: ") + cudaGetErrorString(e));
+  void* scratch = nullptr;
+  e = scratch_address(device, &scratch);
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  if (e != cudaSuccess || !scratch)
+    return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_noalloc_status: ") + cudaGetErrorString(e));
+  return fht_ws_status(scratch, stream);
 }

@@ -39,8 +39,13 @@ class Request:
     image: torch.Tensor     # 2-D CUDA tensor (may be a strided view)
     out: torch.Tensor | None = None
     ws: torch.Tensor | None = None
-    nbytes: int = 0
+    nbytes: int = 0         # out_bytes + ws_bytes, held from admission
+    out_bytes: int = 0
+    ws_bytes: int = 0
     done: float | None = None
+    t_ready: float | None = None   # the serving loop saw the plan built
+    t_admit: float | None = None   # admitted under the memory budget
+    t_launch: float | None = None  # its launch was enqueued
     plan: object = None
     batch_size: int = 0
     plan_future: object = None
@@ -83,7 +88,7 @@ class PlanBuilder:
         self.pool.shutdown(wait=True)
 
 
-def _ready_in_order(waiting, window: int = 256):
+def _ready_in_order(waiting, window: int = 256, now_fn=None):
     """Requests of the first `window` waiting ones whose plans are built, in
     arrival order (a request whose plan is still being built does not hold up
     the ones behind it).  Returns a list, so the caller may remove from `waiting`."""
@@ -95,7 +100,11 @@ def _ready_in_order(waiting, window: int = 256):
             if not req.plan_future.done():
                 continue
             req.plan = req.plan_future.result()
-            req.nbytes = req.plan.out_elems * 4 + max(req.plan.workspace_bytes, 256)
+            req.out_bytes = req.plan.out_elems * 4
+            req.ws_bytes = max(req.plan.workspace_bytes, 256)
+            req.nbytes = req.out_bytes + req.ws_bytes
+            if now_fn is not None:
+                req.t_ready = now_fn()
         ready.append(req)
     return ready
 
@@ -138,19 +147,24 @@ class Server:
         self.builder.request(req)
         self.waiting.append(req)
 
-    def _admit(self):
-        for req in _ready_in_order(self.waiting):
+    def _admit(self, now_fn=None):
+        for req in _ready_in_order(self.waiting, now_fn=now_fn):
             need = req.nbytes
             if self.used + need > self.budget and self.used > 0:
                 break  # memory is admitted in arrival order among ready requests
             self.waiting.remove(req)
             self.used += need
             self.max_used = max(self.max_used, self.used)
+            if now_fn is not None:
+                req.t_admit = now_fn()
             self.admitted.append(req)
 
-    def _finish(self, r, t):
+    def _finish(self, r, t, release_ws: bool):
+        # A batched request's output is complete when its flag is seen, but its
+        # workspace stays allocated until the whole launch has ended: only the
+        # output's bytes are released here in that case (see _retire).
         r.done = t
-        self.used -= r.nbytes
+        self.used -= r.nbytes if release_ws else r.out_bytes
         if not self.keep_outputs:
             r.out = None
         self.finished.append(r)
@@ -161,23 +175,25 @@ class Server:
             for rid in q.poll(cap=4096):
                 r = self.by_rid.pop(rid, None)
                 if r is not None:
-                    self._finish(r, now_fn())
+                    self._finish(r, now_fn(), release_ws=False)
         still = []
         for b in self.running:
             if b.plain:
                 if b.event.query():
                     r = b.reqs[0]
-                    self._finish(r, now_fn())
+                    self._finish(r, now_fn(), release_ws=True)
                     r.ws = None
                     self.inflight[b.slot] -= 1
                 else:
                     still.append(b)
                 continue
-            # a launch's workspaces are released, and its stream slot counted
-            # free, once every request is done and the launch has ended
+            # a launch's workspaces are released (and their bytes returned to
+            # the budget), and its stream slot counted free, once every
+            # request is done and the launch has ended
             if all(r.done is not None for r in b.reqs) and b.event.query():
                 for r in b.reqs:
                     r.ws = None
+                    self.used -= r.ws_bytes
                 self.inflight[b.slot] -= 1
             else:
                 still.append(b)
@@ -187,7 +203,7 @@ class Server:
         k = min(range(len(self.streams)), key=lambda i: self.inflight[i])
         return k if self.inflight[k] < self.max_inflight else None
 
-    def _launch(self):
+    def _launch(self, now_fn=None):
         while self.admitted:
             slot = self._pick_stream()
             if slot is None:
@@ -205,6 +221,8 @@ class Server:
                     ev = torch.cuda.Event()
                     ev.record(s)
                 r.batch_size = 1
+                if now_fn is not None:
+                    r.t_launch = now_fn()
                 self.running.append(_Batch(ev, [r], slot, s, plain=True))
                 self.inflight[slot] += 1
                 self.batches += 1
@@ -226,14 +244,18 @@ class Server:
                                          tags=[r.rid for r in reqs], plans=[r.plan for r in reqs])
                 ev = torch.cuda.Event()
                 ev.record(s)
+            if now_fn is not None:
+                t = now_fn()
+                for r in reqs:
+                    r.t_launch = t
             self.running.append(_Batch(ev, reqs, slot, s))
             self.inflight[slot] += 1
             self.batches += 1
 
     def step(self, now_fn):
         self._retire(now_fn)
-        self._admit()
-        self._launch()
+        self._admit(now_fn)
+        self._launch(now_fn)
 
     def idle(self) -> bool:
         return not (self.waiting or self.admitted or self.running)
@@ -268,13 +290,15 @@ class PlainServer:
         self.builder.request(req)
         self.waiting.append(req)
 
-    def _launch(self):
-        for req in _ready_in_order(self.waiting):
+    def _launch(self, now_fn=None):
+        for req in _ready_in_order(self.waiting, now_fn=now_fn):
             if self.used + req.nbytes > self.budget and self.used > 0:
                 return
             self.waiting.remove(req)
             self.used += req.nbytes
             self.max_used = max(self.max_used, self.used)
+            if now_fn is not None:
+                req.t_admit = req.t_launch = now_fn()
             p = req.plan
             with torch.cuda.stream(self.stream):
                 req.out = p.new_output()
@@ -295,7 +319,7 @@ class PlainServer:
             if not self.keep_outputs:
                 r.out = None
             self.finished.append(r)
-        self._launch()
+        self._launch(now_fn)
 
     def idle(self) -> bool:
         return not (self.running or self.waiting)

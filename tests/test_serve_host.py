@@ -85,3 +85,55 @@ def test_oversized_request_runs_alone():
     s.used -= big.nbytes
     s._admit()
     assert [r.rid for r in s.admitted] == [0, 1]
+
+
+class _FakeQueue:
+    def __init__(self):
+        self.flags = []
+
+    def poll(self, cap=4096):
+        got, self.flags = self.flags[:cap], self.flags[cap:]
+        return got
+
+
+class _FakeEvent:
+    def __init__(self):
+        self.fired = False
+
+    def query(self):
+        return self.fired
+
+
+def test_batched_workspace_stays_counted_until_the_launch_ends():
+    # Requests of one persistent launch report completion one by one, but
+    # their workspaces stay allocated until the launch itself has ended: the
+    # budget must keep counting those bytes until then.
+    s = _server(budget=10_000)
+    s.keep_outputs = True
+    s.finished = []
+    s.queues = [_FakeQueue()]
+    s.inflight = [1]
+    reqs = [_req(k, 100, 600) for k in range(3)]  # 400 output + 600 workspace bytes each
+    s.waiting.extend(reqs)
+    s._admit()
+    assert s.used == 3000
+    ev = _FakeEvent()
+    s.by_rid = {r.rid: r for r in reqs}
+    for r in reqs:
+        r.ws = object()
+    s.running = [serve._Batch(ev, list(reqs), 0)]
+    held = lambda: sum(r.ws_bytes for r in reqs if r.ws is not None) + sum(
+        r.out_bytes for r in reqs if r.done is None)
+    clock = iter(range(100))
+    now = lambda: float(next(clock))
+    s.queues[0].flags = [0, 1]
+    s._retire(now)
+    assert s.used == held() == 400 + 3 * 600
+    s.queues[0].flags = [2]
+    s._retire(now)
+    # every request is done but the launch has not ended: workspaces still held
+    assert s.used == held() == 3 * 600 and s.running and s.inflight == [1]
+    ev.fired = True
+    s._retire(now)
+    assert s.used == held() == 0 and not s.running and s.inflight == [0]
+    assert [r.rid for r in s.finished] == [0, 1, 2]

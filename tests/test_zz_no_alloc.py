@@ -60,6 +60,33 @@ def test_noalloc_matches_forward_twice(lib):
         assert bool(((ref - got).abs() <= 1e-5 * mass).all())
 
 
+def test_noalloc_near_the_limit_allocates_nothing(lib):
+    # 648 x 1266 uint8, 4 quadrants, cyclic: a workspace 35 KB short of the
+    # 32 MiB scratch, so the last bytes of the array are used
+    from paper_2411_07351_gb300 import _capi
+
+    p = _plan(648, 1266, torch.uint8, "cyclic")
+    assert (32 << 20) - 64 * 1024 < p.workspace_bytes <= (32 << 20)
+    x = torch.from_numpy(inputs.uniform_u8(25, 648, 1266)).cuda()
+    ref, got = _both(lib, p, x)  # also the warm-up of this shape
+    assert torch.equal(ref, got)
+    s = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    outs = [torch.full_like(ref, -1) for _ in range(3)]
+    for o in outs:
+        _capi.check(lib.fht_forward_noalloc(p._h, x.data_ptr(), x.stride(0), o.data_ptr(), s), "fht_forward_noalloc")
+    torch.cuda.synchronize()
+    # nothing was allocated by the calls: neither through torch nor by the driver
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == allocs0
+    assert torch.cuda.mem_get_info()[0] == free0
+    for o in outs:
+        assert torch.equal(o, ref)
+    # the device-side status word of the built-in scratch reads clean
+    assert lib.fht_noalloc_status(torch.cuda.current_device(), s) == _capi.FHT_OK
+
+
 def test_noalloc_rejects_plans_above_the_scratch_size(lib):
     from paper_2411_07351_gb300 import _capi
 
