@@ -73,3 +73,21 @@ def test_brute_at_transposed_index(orc):
     q2 = qs2 >= 2
     v, _ = orc.brute_at(img, qs2[q2], ts2[q2], xs2[q2], 0)
     np.testing.assert_array_equal(v, v_t)
+
+
+def test_parallel_digests_match_direct_runs(orc):
+    # the spawned-process driver used by the whole-workload GPU checks returns,
+    # per image, the digest of exactly what the oracle computes in-process
+    from oracle import parallel
+
+    rng = np.random.default_rng(3)
+    imgs = [rng.integers(0, 256, size=(int(h), int(w)), dtype=np.uint8)
+            for h, w in rng.integers(1, 60, size=(9, 2))]
+    got = parallel.int32_digests(imgs, QALL, 0, procs=3)
+    assert sorted(got) == list(range(len(imgs)))
+    for k, im in enumerate(imgs):
+        assert got[k] == parallel.digest(orc.fht(im.astype(np.int64), QALL, 0).astype(np.int32))
+    # a changed element changes the digest
+    ref = orc.fht(imgs[0].astype(np.int64), QALL, 0).astype(np.int32)
+    ref[len(ref) // 2] += 1
+    assert parallel.digest(ref) != got[0]

@@ -71,10 +71,10 @@ def test_noalloc_near_the_limit_allocates_nothing(lib):
     ref, got = _both(lib, p, x)  # also the warm-up of this shape
     assert torch.equal(ref, got)
     s = torch.cuda.current_stream().cuda_stream
+    outs = [torch.full_like(ref, -1) for _ in range(3)]
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
-    outs = [torch.full_like(ref, -1) for _ in range(3)]
     for o in outs:
         _capi.check(lib.fht_forward_noalloc(p._h, x.data_ptr(), x.stride(0), o.data_ptr(), s), "fht_forward_noalloc")
     torch.cuda.synchronize()
