@@ -365,7 +365,7 @@ def run_fht(args, wl):
         for k in range(launches):
             per_launch[k] += kev[2 * k].elapsed_time(kev[2 * k + 1])
     per_launch /= KP
-    kind_names = {0: "fused_kernel", 1: "upper_kernel", 2: "band_kernel", 3: "spine_kernel"}
+    kind_names = {0: "fused_kernel", 1: "upper_kernel", 2: "band_kernel", 3: "spine_kernel", 4: "block_kernel"}
     kernels = {}
     for k in range(launches):
         nm = kind_names[kinds[k]]

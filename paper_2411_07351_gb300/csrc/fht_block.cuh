@@ -1,0 +1,277 @@
+// Register-tiled Brady-Yong block path (4-byte accumulators): the 64-row
+// blocks of the fused pass with every merge level done in registers.
+//
+// A perfect block of R = 2^r child blocks of M rows each (the children
+// already Brady-Yong transformed) becomes one block of R M rows.  Following
+// the merges of Algorithm 1 through r levels (at a power-of-two node t1 = t2 =
+// floor(t/2) and the bottom child is shifted by ceil(t/2)), output slope
+// t = R k + i (k in [0, M), i in [0, R)) of child e (rows e M + k) is read at
+//     column x + e k + p_i(e),
+// where p_i is the R-row Brady-Yong pattern:  p^1_0(0) = 0 and
+//     p^{2R}_i(e) = p^R_{i/2}(e)               for e <  R,
+//     p^{2R}_i(e) = p^R_{i/2}(e - R) + ceil(i/2)  for e >= R.
+// A thread owns four consecutive output columns x = j .. j + 3 (j a multiple
+// of four) of all R slopes i of one (group, k).  Child e is read over columns
+// [j + e k, j + e k + 4 + e) with 16-byte shared loads; their misalignment
+// (e k) mod 4 depends only on k mod 4, which is uniform across a warp, so a
+// four-way switch on it makes every shifted read a compile-time register
+// index.  The R outputs are then built level by level in registers (the
+// Brady-Yong sharing: about log2 R additions per output).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fht_desc.h"
+#include "fht_device.cuh"
+
+namespace fht {
+
+// Geometry (kVTile, kVThreads, kVPitch: fht_desc.h): the staged window of
+// kVTile + 63 columns is merged in place in one shared buffer; kVPitch / 4 is
+// odd, so that 8 rows x 4 columns of the transposed staging hit 32 distinct
+// banks.
+constexpr int kVWin = kVTile + 64;  // staged columns (the window needs kVTile + 63)
+static_assert(kVWin <= kVPitch && kVPitch % 4 == 0 && (kVPitch / 4) % 2 == 1, "shared row geometry");
+
+template <int R>
+__host__ __device__ constexpr int by_off(int i, int e) {
+  if constexpr (R == 1) {
+    return 0;
+  } else {
+    return e < R / 2 ? by_off<R / 2>(i / 2, e) : by_off<R / 2>(i / 2, e - R / 2) + (i + 1) / 2;
+  }
+}
+
+static_assert(by_off<4>(0, 1) == 0 && by_off<4>(1, 1) == 0 && by_off<4>(2, 1) == 1 && by_off<4>(3, 1) == 1 &&
+                  by_off<4>(1, 2) == 1 && by_off<4>(2, 2) == 1 && by_off<4>(3, 2) == 2 && by_off<4>(3, 3) == 3 &&
+                  by_off<4>(1, 3) == 1 && by_off<4>(2, 3) == 2,
+              "4-row pattern: child 1 at floor(i/2), child 2 at ceil(i/2), child 3 at their sum");
+static_assert(by_off<8>(7, 5) == 5 && by_off<8>(0, 7) == 0 && by_off<8>(5, 6) == 4,
+              "8-row pattern: the last slope is the diagonal, slope 0 the column");
+
+// Misalignment of child e's first column for k = A (mod 4).
+__host__ __device__ constexpr int v_misalign(int e, int A) { return (e * A) & 3; }
+// 16-byte vectors that cover child e's columns [0, 4 + e) from that start.
+__host__ __device__ constexpr int v_nvec(int e, int A) { return (v_misalign(e, A) + 4 + e + 3) / 4; }
+
+// out[i][x] = sum_e c[E0 + e][a_e + x + p_i(e)], e in [0, R), x in [0, W),
+// built as the Brady-Yong recursion: the top half's sub-block at x plus the
+// bottom half's at x + ceil(i/2).
+template <int R, int W, int E0, int A, typename T>
+__device__ __forceinline__ void by_regs(const T (&c)[8][16], T (&out)[R][W]) {
+  if constexpr (R == 1) {
+    constexpr int a = v_misalign(E0, A);
+#pragma unroll
+    for (int x = 0; x < W; x++) out[0][x] = c[E0][a + x];
+  } else {
+    T top[R / 2][W];
+    T bot[R / 2][W + R / 2];
+    by_regs<R / 2, W, E0, A, T>(c, top);
+    by_regs<R / 2, W + R / 2, E0 + R / 2, A, T>(c, bot);
+#pragma unroll
+    for (int i = 0; i < R; i++)
+#pragma unroll
+      for (int x = 0; x < W; x++) out[i][x] = top[i / 2][x] + bot[i / 2][x + (i + 1) / 2];
+  }
+}
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  using type = float4;
+};
+template <>
+struct Vec4<int32_t> {
+  using type = int4;
+};
+
+template <typename T>
+__device__ __forceinline__ void lds4(const T* p, T* d) {
+  const typename Vec4<T>::type v = *reinterpret_cast<const typename Vec4<T>::type*>(p);
+  d[0] = v.x;
+  d[1] = v.y;
+  d[2] = v.z;
+  d[3] = v.w;
+}
+
+template <typename T>
+__device__ __forceinline__ void sts4(T* p, const T* s) {
+  typename Vec4<T>::type v;
+  v.x = s[0];
+  v.y = s[1];
+  v.z = s[2];
+  v.w = s[3];
+  *reinterpret_cast<typename Vec4<T>::type*>(p) = v;
+}
+
+// The R slopes of one (group, k) at columns j .. j + 3: child e is shared
+// row `row0 + e * M` (row0 = group * R * M + k), read from column j + e k.
+template <int R, int M, int A, typename T>
+__device__ __forceinline__ void by_item(const T* S, int32_t row0, int32_t k, int32_t j, T (&out)[R][4]) {
+  T c[8][16];
+#pragma unroll
+  for (int e = 0; e < R; e++) {
+    const T* src = S + (row0 + e * M) * kVPitch + j + e * k - v_misalign(e, A);
+#pragma unroll
+    for (int v = 0; v < v_nvec(e, A); v++) lds4<T>(src + 4 * v, &c[e][4 * v]);
+  }
+  by_regs<R, 4, 0, A, T>(c, out);
+}
+
+// Stage the window of rows [8 w, 8 w + 8) of the block (warp w stages the
+// rows its first pass merges, so no CTA barrier is needed before that pass):
+// block row r = view row a + r, window column z = view column x0 + z,
+// z in [0, kVWin), wrapped (cyclic) or zero outside [0, L) (extended), with
+// the quadrant's transpose / column reversal.
+template <typename InT, typename AccT>
+__device__ __forceinline__ void v_stage(const InT* __restrict__ in, int64_t pitch, const QuadDesc& Q, int32_t a,
+                                        int32_t x0, AccT* S) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!Q.transpose) {
+    // lanes along the window columns; two batches of four rows, every load
+    // of a batch in flight before its shared stores
+    const bool inside = x0 >= 0 && x0 + kVWin <= Q.L;
+#pragma unroll 1
+    for (int rb = 0; rb < 8; rb += 4) {
+      AccT v[4][kVWin / 32];
+#pragma unroll
+      for (int rr = 0; rr < 4; rr++) {
+        const InT* __restrict__ rowp = in + (int64_t)(a + 8 * warp + rb + rr) * pitch;
+        if (inside) {
+          const InT* __restrict__ src = Q.flip ? rowp + (Q.L - 1 - x0 - lane) : rowp + x0 + lane;
+          const int32_t step = Q.flip ? -32 : 32;
+#pragma unroll
+          for (int c = 0; c < kVWin / 32; c++) v[rr][c] = (AccT)__ldg(src + c * step);
+        } else {
+#pragma unroll
+          for (int c = 0; c < kVWin / 32; c++) v[rr][c] = load_view_elem<InT, AccT>(rowp, Q, x0 + 32 * c + lane);
+        }
+      }
+#pragma unroll
+      for (int rr = 0; rr < 4; rr++) {
+        AccT* dst = S + (8 * warp + rb + rr) * kVPitch + lane;
+#pragma unroll
+        for (int c = 0; c < kVWin / 32; c++) dst[32 * c] = v[rr][c];
+      }
+    }
+  } else {
+    // transposed view: block row r is image column a + r, window column z an
+    // image row.  Lane = (r & 7) + 8 (z & 3): a warp instruction reads 32
+    // bytes of four image rows and writes 8 rows x 4 columns of shared memory
+    // (distinct banks: kVPitch / 4 is odd).
+    const int32_t rl = lane & 7, zl = lane >> 3;
+    const int32_t r = 8 * warp + rl;
+#pragma unroll 1
+    for (int zb = 0; zb < kVWin; zb += 128) {
+      AccT v[32];
+#pragma unroll
+      for (int c = 0; c < 32; c++) {
+        int32_t z = x0 + zb + 4 * c + zl;
+        bool ok = true;
+        if (Q.ext) {
+          ok = z >= 0 && z < Q.L;
+        } else if (z >= Q.L) {
+          z = z < 2 * Q.L ? z - Q.L : z % Q.L;
+        } else if (z < 0) {
+          z += Q.L;  // not reached: cyclic windows start at column >= 0
+        }
+        if (Q.flip) z = Q.L - 1 - z;
+        v[c] = ok ? (AccT)__ldg(in + (int64_t)z * pitch + a + r) : AccT(0);
+      }
+#pragma unroll
+      for (int c = 0; c < 32; c++) S[r * kVPitch + zb + 4 * c + zl] = v[c];
+    }
+  }
+}
+
+// First pass, in place: the eight 8-row groups of the staged window become
+// 8-row Brady-Yong blocks over columns [0, kVTile + 56).  Warp w owns group w
+// (its rows are read and written by no other warp) and walks its columns
+// left to right, 128 per step: a step reads up to 8 columns into the next
+// step's range, which that step only overwrites later.
+template <typename AccT>
+__device__ __forceinline__ void v_pass1(AccT* S) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kW = kVTile + 56;
+#pragma unroll 1
+  for (int32_t j0 = 0; j0 < kW; j0 += 128) {
+    const int32_t j = j0 + 4 * lane;
+    AccT o[8][4];
+    if (j < kW) by_item<8, 1, 0, AccT>(S, 8 * warp, 0, j, o);
+    __syncwarp();  // every lane's reads of this step before any lane's writes
+    if (j < kW) {
+#pragma unroll
+      for (int i = 0; i < 8; i++) sts4<AccT>(S + (8 * warp + i) * kVPitch + j, o[i]);
+    }
+    __syncwarp();
+  }
+}
+
+// Second pass: the eight 8-row blocks become the 64-row block; slope 8 k + i
+// of child e reads shared row 8 e + k.  Warp w computes k = w for the tile's
+// columns and stores the eight rows to global memory.
+template <int A, typename AccT>
+__device__ __forceinline__ void v_pass2_k(const AccT* S, int32_t k, const FusedItem& it, const QuadDesc& Q,
+                                          AccT* __restrict__ base, int32_t u0, int32_t ncols, bool vec_ok) {
+  const int32_t lane = threadIdx.x & 31;
+  const int64_t pitch = it.dst_pitch;
+#pragma unroll 1
+  for (int32_t j0 = 0; j0 < kVTile; j0 += 128) {
+    const int32_t j = j0 + 4 * lane;
+    if (j >= ncols) break;
+    AccT o[8][4];
+    by_item<8, 8, A, AccT>(S, k, k, j, o);
+    AccT* row = base + (int64_t)(8 * k) * pitch;
+    if (vec_ok && j + 4 <= ncols) {
+#pragma unroll
+      for (int i = 0; i < 8; i++) sts4<AccT>(row + i * pitch + u0 + j, o[i]);
+    } else {
+#pragma unroll
+      for (int x = 0; x < 4; x++) {
+        if (j + x >= ncols) break;
+        int32_t X = u0 + j + x;
+        if (it.final_) {
+          X = Q.sigma * X + Q.kappa;
+          if (X < 0) X += Q.W;
+          if (X >= Q.W) X -= Q.W;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) row[i * pitch + X] = o[i][x];
+      }
+    }
+  }
+}
+
+// One 64-row block x one tile of kVTile columns (blockDim.x == kVThreads).
+template <typename InT, typename AccT>
+__device__ __forceinline__ void v_block(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile,
+                                        AccT* S) {
+  const int32_t u0 = tile * kVTile;
+  v_stage<InT, AccT>(static_cast<const InT*>(p.in), p.in_pitch, Q, it.a, u0 - it.c, S);
+  __syncwarp();
+  v_pass1<AccT>(S);
+  __syncthreads();
+  const int32_t ncols = min(kVTile, it.wn - u0);
+  AccT* __restrict__ base = (it.final_ ? static_cast<AccT*>(p.out) : static_cast<AccT*>(p.ws)) + it.dst;
+  // 16-byte stores need node-local columns (no output map) on 16-byte aligned rows
+  const bool vec_ok = !it.final_ && ((it.dst | (int64_t)it.dst_pitch) & 3) == 0 &&
+                      (reinterpret_cast<uintptr_t>(p.ws) & 15) == 0;
+  const int32_t k = threadIdx.x >> 5;
+  switch (k & 3) {
+    case 0:
+      v_pass2_k<0, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      break;
+    case 1:
+      v_pass2_k<1, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      break;
+    case 2:
+      v_pass2_k<2, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      break;
+    default:
+      v_pass2_k<3, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      break;
+  }
+}
+
+}  // namespace fht

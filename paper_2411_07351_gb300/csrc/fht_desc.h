@@ -53,13 +53,21 @@ struct FusedItem {
 
 enum : int32_t { FUSED_GENERIC = 0, FUSED_BY64 = 1, FUSED_BAND = 2 };
 
+// Register-tiled 64-row block path (4-byte accumulators, its own launch):
+// CTAs of kVThreads threads, column tiles of kVTile, one shared buffer of 64
+// rows x kVPitch elements.  kVPitch >= kVTile + 64, a multiple of 4 with
+// kVPitch / 4 odd.
+constexpr int32_t kVTile = 192;
+constexpr int32_t kVThreads = 256;
+constexpr int32_t kVPitch = 260;
+
 // The quadrant table passed by value to kernels.
 struct QuadDescs {
   QuadDesc q[4];
 };
 
 // Kinds of forward kernel launches (fht_plan_launch_info).
-enum : int32_t { LAUNCH_FUSED = 0, LAUNCH_UPPER = 1, LAUNCH_BAND = 2, LAUNCH_SPINE = 3 };
+enum : int32_t { LAUNCH_FUSED = 0, LAUNCH_UPPER = 1, LAUNCH_BAND = 2, LAUNCH_SPINE = 3, LAUNCH_BLOCK = 4 };
 
 // One output row of a root whose tree is a Split_T spine over "parts"
 // (perfect bands of 2^k rows, 64-row blocks and one remainder subtree):

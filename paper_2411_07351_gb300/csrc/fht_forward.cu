@@ -15,6 +15,7 @@
 
 #include "../../include/fht.h"
 #include "fht_desc.h"
+#include "fht_block.cuh"
 #include "fht_device.cuh"
 #include "fht_launch.hpp"
 
@@ -39,6 +40,25 @@ __global__ void __launch_bounds__(512, 2) fused_kernel(FusedParams p) {
   } else {
     fused_generic<InT, AccT>(p, it, Q, tile, sm, sm + (size_t)p.Fm * p.RP);
   }
+}
+
+// Register-tiled 64-row blocks (fht_block.cuh): one CTA = one block x one
+// tile of kVTile columns.  The blocks read only the input image, so the launch
+// does not wait for the one before it (the generic subtrees of the same
+// forward) to start; it waits before it exits, so that its completion still
+// implies that launch's, which the next launch relies on.
+template <typename InT, typename AccT>
+__global__ void __launch_bounds__(kVThreads, 3) block_kernel(FusedParams p, int32_t first) {
+  pdl_launch_dependents();
+  if (first && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    *reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p.ws) - kWsHeader) = 0;
+  const FusedItem it = p.items[blockIdx.x];
+  const int32_t tile = blockIdx.y;
+  if (tile < it.ntiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    v_block<InT, AccT>(p, it, p.quad[it.q], tile, reinterpret_cast<AccT*>(smem_raw));
+  }
+  pdl_wait();
 }
 
 // One CTA per output row; every thread keeps U independent element pairs in
@@ -462,7 +482,13 @@ void fused_geometry(const HostPlan& P, FusedGeometry& g) {
   if (g.RA % 2 == 0) g.RA++;
   size_t by64 = P.n_by64 > 0 ? (size_t)64 * (g.RS + g.RA) * P.acc_size : 0;
   g.smem = std::max(generic, by64);
+  g.gsmem = generic;
+  g.vsmem = P.vblock ? (size_t)64 * kVPitch * P.acc_size : 0;
 }
+
+// Fused launches of a forward: one, or on the register-tiled path the
+// generic subtrees' (if any) and then the 64-row blocks'.
+static int32_t fused_launches(const HostPlan& P) { return P.vblock ? 1 + (P.n_generic > 0) : 1; }
 
 static int32_t spine_passes(const HostPlan& P) {
   int32_t n = 0;
@@ -471,24 +497,34 @@ static int32_t spine_passes(const HostPlan& P) {
 }
 
 int32_t forward_launches(const HostPlan& P) {
-  if (P.bands) return 1 + (P.band_items.empty() ? 0 : 1) + spine_passes(P);
-  return 1 + (int32_t)P.pass_bytes.size();
+  const int32_t nf = fused_launches(P);
+  if (P.bands) return nf + (P.band_items.empty() ? 0 : 1) + spine_passes(P);
+  return nf + (int32_t)P.pass_bytes.size();
 }
 
 void forward_launch_info(const HostPlan& P, int32_t k, int32_t& kind, int64_t& bytes) {
-  if (k == 0) {
-    kind = LAUNCH_FUSED;
-    bytes = P.fused_bytes;
+  const int32_t nf = fused_launches(P);
+  if (k < nf) {
+    if (!P.vblock) {
+      kind = LAUNCH_FUSED;
+      bytes = P.fused_bytes;
+    } else if (k + 1 < nf) {
+      kind = LAUNCH_FUSED;  // the generic subtrees
+      bytes = P.generic_bytes;
+    } else {
+      kind = LAUNCH_BLOCK;
+      bytes = P.by64_bytes;
+    }
   } else if (!P.bands) {
     kind = LAUNCH_UPPER;
-    bytes = P.pass_bytes[k - 1];
-  } else if (k == 1 && !P.band_items.empty()) {
+    bytes = P.pass_bytes[k - nf];
+  } else if (k == nf && !P.band_items.empty()) {
     kind = LAUNCH_BAND;
     bytes = P.band_bytes;
   } else {
     kind = LAUNCH_SPINE;
     // the k-th spine launch (empty passes launch nothing)
-    int32_t s = k - 1 - (P.band_items.empty() ? 0 : 1);
+    int32_t s = k - nf - (P.band_items.empty() ? 0 : 1);
     bytes = 0;
     for (size_t p = 0; p + 1 < P.spine_pass_begin.size(); p++) {
       if (P.spine_pass_begin[p + 1] == P.spine_pass_begin[p]) continue;
@@ -541,12 +577,37 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
   auto kfn = fused_kernel<InT, AccT>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)P.fused.size(), P.max_ntiles);  // tiles <= 131070 / 32 fit in grid.y
-  mark(0);
-  e = go(kfn, grid, P.cfg.threads, smem, fp);
-  mark(1);
-  launch++;
-  if (e != cudaSuccess) return e;
+  if (!P.vblock) {
+    dim3 grid((unsigned)P.fused.size(), P.max_ntiles);  // tiles <= 131070 / 32 fit in grid.y
+    mark(0);
+    e = go(kfn, grid, P.cfg.threads, smem, fp);
+    mark(1);
+    launch++;
+    if (e != cudaSuccess) return e;
+  } else if constexpr (sizeof(AccT) == 4) {
+    if (P.n_generic > 0) {
+      dim3 grid((unsigned)P.n_generic, P.max_generic_ntiles);
+      mark(0);
+      e = go(kfn, grid, P.cfg.threads, D.geo.gsmem, fp);
+      mark(1);
+      launch++;
+      if (e != cudaSuccess) return e;
+    }
+    auto kbl = block_kernel<InT, AccT>;
+    if ((e = cudaFuncSetAttribute(kbl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D.geo.vsmem)) !=
+        cudaSuccess)
+      return e;
+    FusedParams bp = fp;
+    bp.items = D.fused + P.n_generic;
+    dim3 grid((unsigned)P.n_by64, P.max_by64_ntiles);
+    mark(0);
+    e = go(kbl, grid, kVThreads, D.geo.vsmem, bp, (int32_t)(P.n_generic == 0));
+    mark(1);
+    launch++;
+    if (e != cudaSuccess) return e;
+  } else {
+    return cudaErrorInvalidValue;  // the planner enables the register-tiled path for 4-byte accumulators only
+  }
   if (P.bands) {
     if (!P.band_items.empty()) {
       fp.items = D.band_items;

@@ -13,6 +13,8 @@ struct FusedGeometry {
   int32_t RP = 0, Fm = 1;  // generic path: row pitch and rows per buffer
   int32_t RS = 0, RA = 0;  // 64-row fast path: pitches of the two buffers
   size_t smem = 0;         // dynamic shared memory (bytes)
+  size_t gsmem = 0;        // generic subtrees alone (their own launch on the register-tiled path)
+  size_t vsmem = 0;        // register-tiled 64-row block launch
 };
 
 struct DevicePlan {
@@ -48,7 +50,8 @@ cudaError_t launch_adjoint(const DevicePlan& D, const void* gout, void* gin, int
                            cudaStream_t st);
 
 // Kernel launches of one forward transform, and the kind of launch k
-// (LAUNCH_FUSED, LAUNCH_UPPER, LAUNCH_BAND, LAUNCH_SPINE) with its model bytes.
+// (LAUNCH_FUSED, LAUNCH_UPPER, LAUNCH_BAND, LAUNCH_SPINE, LAUNCH_BLOCK) with
+// its model bytes.
 int32_t forward_launches(const HostPlan& P);
 void forward_launch_info(const HostPlan& P, int32_t k, int32_t& kind, int64_t& bytes);
 

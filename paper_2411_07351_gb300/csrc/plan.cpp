@@ -760,6 +760,18 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
   // generic items first: they are few and slower, so they start in the first wave
   std::stable_sort(P.fused.begin(), P.fused.end(),
                    [](const FusedItem& x, const FusedItem& y) { return x.kind < y.kind; });
+  for (const FusedItem& fi : P.fused) {
+    const int64_t b = (int64_t)fi.m * P.quad[fi.q].L * P.in_size + (int64_t)fi.m * fi.wn * P.acc_size;
+    if (fi.kind == FUSED_GENERIC) {
+      P.n_generic++;
+      P.max_generic_ntiles = std::max(P.max_generic_ntiles, fi.ntiles);
+      P.generic_bytes += b;
+    } else {
+      P.max_by64_ntiles = std::max(P.max_by64_ntiles, fi.ntiles);
+      P.by64_bytes += b;
+    }
+  }
+  P.vblock = P.acc_size == 4 && cfg.TW == kVTile && cfg.threads == kVThreads && P.n_by64 > 0;
   P.out_elems = out_off;
   P.ws_bytes = kWsHeader + (size_t)ws_off * acc;
   // adjoint: one h x w gradient image per quadrant after the forward buffers

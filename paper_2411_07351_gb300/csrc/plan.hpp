@@ -98,6 +98,13 @@ struct HostPlan {
   int32_t generic_shift = 0;          // largest shift of a generic fused merge
   int32_t generic_tw = 0;             // column tile of generic fused items
   int32_t n_by64 = 0;                 // fused items on the 64-row Brady-Yong fast path
+  // register-tiled block path (4-byte accumulators, tile kVTile, kVThreads
+  // threads): the 64-row blocks run in a launch of their own, after one for
+  // the generic subtrees (fused[0 .. n_generic) sorts first)
+  bool vblock = false;
+  int32_t n_generic = 0;
+  int32_t max_generic_ntiles = 0, max_by64_ntiles = 0;
+  int64_t generic_bytes = 0, by64_bytes = 0;  // model bytes of the two kinds of fused items
   int64_t adds = 0, model_bytes = 0, ideal_bytes = 0;
   // band schedule (Split_T with 64-row fused blocks): one gathered
   // Brady-Yong pass for every perfect band above the blocks, then one

@@ -48,6 +48,14 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
         return at("fused", k) + "fast-path buffers too small";
       if ((tw + 60 - 1) + 3 >= g.RS || (tw + 48 - 1) + 12 >= g.RA || (tw - 1) + 48 >= g.RS)
         return at("fused", k) + "fast-path shifted read beyond a shared row";
+      if (P.vblock) {
+        // register-tiled launch: window kVTile + 63 staged as kVTile + 64 columns of
+        // kVPitch-element rows; its own grid and shared size
+        if (tw != kVTile || kVTile + 64 > kVPitch) return at("fused", k) + "register-tiled tile geometry";
+        if ((int64_t)k < P.n_generic || it.ntiles > P.max_by64_ntiles)
+          return at("fused", k) + "64-row block outside the block launch's grid";
+        if ((size_t)64 * kVPitch * P.acc_size > g.vsmem) return at("fused", k) + "block launch shared size";
+      }
       // the program must be the Brady-Yong block the fast path hard-codes
       for (int32_t l = 0; l < 6; l++) {
         const int32_t b = 1 << (l + 1);
@@ -59,6 +67,9 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
         }
       }
     } else {
+      if (P.vblock && ((int64_t)k >= P.n_generic || it.ntiles > P.max_generic_ntiles ||
+                       (size_t)2 * g.Fm * g.RP * P.acc_size > g.gsmem))
+        return at("fused", k) + "generic subtree outside its launch's grid or shared size";
       if (it.m > g.Fm) return at("fused", k) + "subtree taller than the shared buffers";
       if ((size_t)2 * g.Fm * g.RP * P.acc_size > g.smem) return at("fused", k) + "generic buffers too small";
       for (int32_t l = 0; l < it.nlev; l++)

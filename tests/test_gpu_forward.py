@@ -138,6 +138,42 @@ def test_float_launch_shapes(F, orc, tile_cols, threads):
     check_exact(F, orc, imi, 15, "extended", tile_cols=tile_cols, threads=threads)
 
 
+VTILE = dict(tile_cols=192, threads=256)
+
+
+@pytest.mark.parametrize("boundary", ["cyclic", "extended"])
+def test_register_tiled_blocks_u8(F, orc, boundary):
+    """The register-tiled 64-row block launch (tiles of 192 columns, 256
+    threads): 64-row roots (stored through the quadrant column map), blocks
+    only (h a multiple of 64, one launch), blocks after a generic remainder
+    launch, widths around the tile and narrow ones, every quadrant."""
+    for h, w in [(64, 1), (64, 3), (64, 200), (128, 191), (128, 192), (128, 193), (65, 33), (200, 385),
+                 (191, 64), (256, 17), (320, 450), (1000, 77)]:
+        img = inputs.uniform_u8(1000 + h * 3 + w, h, w)
+        check_exact(F, orc, img, 15, boundary, **VTILE)
+        check_exact(F, orc, img, 1, boundary, **VTILE)
+
+
+@pytest.mark.parametrize("boundary", ["cyclic", "extended"])
+def test_register_tiled_blocks_f32_i32(F, orc, boundary):
+    for h, w in [(64, 64), (129, 300), (700, 515), (4096, 65)]:
+        img = inputs.normal_f32(77 + h + w, h, w)
+        check_float(F, orc, img, 15, boundary, **VTILE)
+    imi = inputs.uniform_u8(33, 300, 200).astype(np.int32) - 128
+    check_exact(F, orc, imi, 15, boundary, **VTILE)
+
+
+def test_register_tiled_pitched_input(F, orc):
+    img = inputs.uniform_u8(19, 130, 71)
+    big = torch.zeros((130, 100), dtype=torch.uint8)
+    big[:, :71] = torch.from_numpy(img)
+    x = big.cuda()[:, :71]
+    p = F.Plan(130, 71, torch.uint8, 15, "extended", **VTILE)
+    p.check()
+    got = p.forward(x).cpu().numpy().astype(np.int64)
+    assert np.array_equal(got, orc.fht(img.astype(np.int64), 15, orc.EXTENDED))
+
+
 def test_pitched_input(F, orc):
     img = inputs.uniform_u8(9, 100, 70)
     big = torch.zeros((100, 96), dtype=torch.uint8)

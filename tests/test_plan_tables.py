@@ -494,14 +494,21 @@ def test_64_row_blocks_are_classical_brady_yong(F, split, boundary):
                 assert (op["top"], op["bot"], op["s"]) == (2 * M * g + t // 2, 2 * M * g + M + t // 2, (t + 1) // 2)
 
 
-def _launch_bytes_from_tables(T, in_size, acc):
+def _launch_bytes_from_tables(T, in_size, acc, vblock=False):
     """Compulsory bytes of every forward launch, counted from the tables: the
     distinct rows a launch reads (each at its row width) and the rows it
-    writes, once each."""
+    writes, once each.  With the register-tiled block path the generic
+    subtrees (if any) and the 64-row blocks are two launches."""
     Qs = T["quads"]
-    fused = sum(int(it["m"]) * int(Qs[it["q"]]["L"]) * in_size + int(it["m"]) * int(it["wn"]) * acc
-                for it in T["fused"])
-    launches = [fused]
+
+    def item_bytes(it):
+        return int(it["m"]) * int(Qs[it["q"]]["L"]) * in_size + int(it["m"]) * int(it["wn"]) * acc
+
+    if vblock:
+        gen = [item_bytes(it) for it in T["fused"] if int(it["kind"]) == 0]
+        launches = ([sum(gen)] if gen else []) + [sum(item_bytes(it) for it in T["fused"] if int(it["kind"]) != 0)]
+    else:
+        launches = [sum(item_bytes(it) for it in T["fused"])]
     if len(T["band_items"]) or len(T["spine_rows"]):
         if len(T["band_items"]):
             reads, writes = set(), 0
@@ -535,8 +542,9 @@ def _launch_bytes_from_tables(T, in_size, acc):
 @pytest.mark.parametrize("h,w,boundary,split,dtype", [
     (4095, 4095, "extended", "T", "float32"), (4095, 4095, "cyclic", "T", "float32"),
     (2047, 300, "extended", "T", "uint8"), (8300, 3, "cyclic", "T", "uint8"),
-    (1000, 700, "extended", "S", "float32"), (257, 257, "cyclic", "T", "uint8")])
-def test_launch_model_bytes_match_the_tables(F, h, w, boundary, split, dtype):
+    (1000, 700, "extended", "S", "float32"), (257, 257, "cyclic", "T", "uint8"), (4096, 640, "cyclic", "T", "uint8")])
+@pytest.mark.parametrize("tile", [(128, 512), (192, 256)])
+def test_launch_model_bytes_match_the_tables(F, h, w, boundary, split, dtype, tile):
     """The per-launch model bytes the bench divides by each launch's time
     (fht_plan_launch_info) equal the distinct rows each launch reads and
     writes according to its own tables."""
@@ -545,9 +553,10 @@ def test_launch_model_bytes_match_the_tables(F, h, w, boundary, split, dtype):
     from paper_2411_07351_gb300 import _capi as C
 
     tdt = {"float32": torch.float32, "uint8": torch.uint8}[dtype]
-    plan = F.Plan(h, w, tdt, F.FHT_QALL, boundary, split=split, device=-1)
+    plan = F.Plan(h, w, tdt, F.FHT_QALL, boundary, split=split, device=-1, tile_cols=tile[0], threads=tile[1])
     T = _tables(F, plan)
-    want = _launch_bytes_from_tables(T, 4 if dtype == "float32" else 1, 4)
+    vblock = tile == (192, 256) and any(int(it["kind"]) == 1 for it in T["fused"])
+    want = _launch_bytes_from_tables(T, 4 if dtype == "float32" else 1, 4, vblock)
     lib = C.load()
     n = ctypes.c_int32()
     C.check(lib.fht_plan_launches(plan._h, ctypes.byref(n)), "fht_plan_launches")
