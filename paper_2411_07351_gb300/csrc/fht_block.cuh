@@ -129,31 +129,28 @@ __device__ __forceinline__ void v_stage(const InT* __restrict__ in, int64_t pitc
                                         int32_t x0, AccT* S) {
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (!Q.transpose) {
-    // lanes along the window columns; two batches of four rows, every load
-    // of a batch in flight before its shared stores
+    // lanes along the window columns; all 64 loads of a lane in flight
+    // before its shared stores
     const bool inside = x0 >= 0 && x0 + kVWin <= Q.L;
-#pragma unroll 1
-    for (int rb = 0; rb < 8; rb += 4) {
-      AccT v[4][kVWin / 32];
+    AccT v[8][kVWin / 32];
 #pragma unroll
-      for (int rr = 0; rr < 4; rr++) {
-        const InT* __restrict__ rowp = in + (int64_t)(a + 8 * warp + rb + rr) * pitch;
-        if (inside) {
-          const InT* __restrict__ src = Q.flip ? rowp + (Q.L - 1 - x0 - lane) : rowp + x0 + lane;
-          const int32_t step = Q.flip ? -32 : 32;
+    for (int rr = 0; rr < 8; rr++) {
+      const InT* __restrict__ rowp = in + (int64_t)(a + 8 * warp + rr) * pitch;
+      if (inside) {
+        const InT* __restrict__ src = Q.flip ? rowp + (Q.L - 1 - x0 - lane) : rowp + x0 + lane;
+        const int32_t step = Q.flip ? -32 : 32;
 #pragma unroll
-          for (int c = 0; c < kVWin / 32; c++) v[rr][c] = (AccT)__ldg(src + c * step);
-        } else {
+        for (int c = 0; c < kVWin / 32; c++) v[rr][c] = (AccT)__ldg(src + c * step);
+      } else {
 #pragma unroll
-          for (int c = 0; c < kVWin / 32; c++) v[rr][c] = load_view_elem<InT, AccT>(rowp, Q, x0 + 32 * c + lane);
-        }
+        for (int c = 0; c < kVWin / 32; c++) v[rr][c] = load_view_elem<InT, AccT>(rowp, Q, x0 + 32 * c + lane);
       }
+    }
 #pragma unroll
-      for (int rr = 0; rr < 4; rr++) {
-        AccT* dst = S + (8 * warp + rb + rr) * kVPitch + lane;
+    for (int rr = 0; rr < 8; rr++) {
+      AccT* dst = S + (8 * warp + rr) * kVPitch + lane;
 #pragma unroll
-        for (int c = 0; c < kVWin / 32; c++) dst[32 * c] = v[rr][c];
-      }
+      for (int c = 0; c < kVWin / 32; c++) dst[32 * c] = v[rr][c];
     }
   } else {
     // transposed view: block row r is image column a + r, window column z an
@@ -162,22 +159,30 @@ __device__ __forceinline__ void v_stage(const InT* __restrict__ in, int64_t pitc
     // (distinct banks: kVPitch / 4 is odd).
     const int32_t rl = lane & 7, zl = lane >> 3;
     const int32_t r = 8 * warp + rl;
+    const bool inside = x0 >= 0 && x0 + kVWin <= Q.L;
 #pragma unroll 1
     for (int zb = 0; zb < kVWin; zb += 128) {
       AccT v[32];
+      if (inside) {
+        // image rows z0, z0 + 4, ... (reversed for the leftward quadrant)
+        const int32_t z0 = x0 + zb + zl;
+        const InT* __restrict__ src = in + (int64_t)(Q.flip ? Q.L - 1 - z0 : z0) * pitch + a + r;
+        const int64_t step = Q.flip ? -4 * pitch : 4 * pitch;
 #pragma unroll
-      for (int c = 0; c < 32; c++) {
-        int32_t z = x0 + zb + 4 * c + zl;
-        bool ok = true;
-        if (Q.ext) {
-          ok = z >= 0 && z < Q.L;
-        } else if (z >= Q.L) {
-          z = z < 2 * Q.L ? z - Q.L : z % Q.L;
-        } else if (z < 0) {
-          z += Q.L;  // not reached: cyclic windows start at column >= 0
+        for (int c = 0; c < 32; c++) v[c] = (AccT)__ldg(src + c * step);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 32; c++) {
+          int32_t z = x0 + zb + 4 * c + zl;
+          bool ok = true;
+          if (Q.ext) {
+            ok = z >= 0 && z < Q.L;
+          } else if (z >= Q.L) {
+            z = z < 2 * Q.L ? z - Q.L : z % Q.L;  // cyclic windows start at column >= 0
+          }
+          if (Q.flip) z = Q.L - 1 - z;
+          v[c] = ok ? (AccT)__ldg(in + (int64_t)z * pitch + a + r) : AccT(0);
         }
-        if (Q.flip) z = Q.L - 1 - z;
-        v[c] = ok ? (AccT)__ldg(in + (int64_t)z * pitch + a + r) : AccT(0);
       }
 #pragma unroll
       for (int c = 0; c < 32; c++) S[r * kVPitch + zb + 4 * c + zl] = v[c];
@@ -185,22 +190,91 @@ __device__ __forceinline__ void v_stage(const InT* __restrict__ in, int64_t pitc
   }
 }
 
-// First pass, in place: the eight 8-row groups of the staged window become
-// 8-row Brady-Yong blocks over columns [0, kVTile + 56).  Warp w owns group w
-// (its rows are read and written by no other warp) and walks its columns
-// left to right, 128 per step: a step reads up to 8 columns into the next
-// step's range, which that step only overwrites later.
+// Band items: staged row r = g B + b holds row K = K0 + g of the band's block
+// b, pre-shifted by K b (window column z reads block column x0 + K b + c_src
+// + z), so that each group of B rows is then a B-row Brady-Yong transform.
+// Warp w stages rows [8 w, 8 w + 8).
 template <typename AccT>
+__device__ __forceinline__ void v_stage_band(const AccT* __restrict__ ws, const FusedItem& it, const QuadDesc& Q,
+                                             int32_t x0, AccT* S) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t lim = Q.ext ? it.wsrc : Q.W;
+  AccT v[8][kVWin / 32];
+#pragma unroll
+  for (int rr = 0; rr < 8; rr++) {
+    const int32_t r = 8 * warp + rr;
+    const int32_t g = r / it.B, b = r - g * it.B;
+    const int32_t K = it.K0 + g;
+    const AccT* __restrict__ row = ws + it.src + (int64_t)(64 * b + K) * it.src_pitch;
+    const int32_t base = x0 + K * b + it.c_src;  // >= 0 in the cyclic case
+    if (base >= 0 && base + kVWin <= lim) {
+#pragma unroll
+      for (int c = 0; c < kVWin / 32; c++) v[rr][c] = __ldg(row + base + 32 * c + lane);
+    } else {
+#pragma unroll
+      for (int c = 0; c < kVWin / 32; c++) {
+        int32_t z = base + 32 * c + lane;
+        bool ok = true;
+        if (Q.ext) {
+          ok = z >= 0 && z < it.wsrc;
+        } else if (z >= Q.W) {
+          z = z < 2 * Q.W ? z - Q.W : z % Q.W;
+        }
+        v[rr][c] = ok ? __ldg(row + z) : AccT(0);
+      }
+    }
+  }
+#pragma unroll
+  for (int rr = 0; rr < 8; rr++) {
+    AccT* dst = S + (8 * warp + rr) * kVPitch + lane;
+#pragma unroll
+    for (int c = 0; c < kVWin / 32; c++) dst[32 * c] = v[rr][c];
+  }
+}
+
+// Store the R rows o[i] (slopes row0 + i of the item) at columns j .. j + 3 of
+// the tile: 16-byte stores into node-local workspace rows, else element by
+// element through the quadrant's column map (a root) and the tile's edge.
+template <int R, typename AccT>
+__device__ __forceinline__ void v_store(const FusedItem& it, const QuadDesc& Q, AccT* __restrict__ base,
+                                        int32_t row0, int32_t u0, int32_t j, int32_t ncols, bool vec_ok,
+                                        const AccT (&o)[R][4]) {
+  const int64_t pitch = it.dst_pitch;
+  AccT* row = base + (int64_t)row0 * pitch;
+  if (vec_ok && j + 4 <= ncols) {
+#pragma unroll
+    for (int i = 0; i < R; i++) sts4<AccT>(row + i * pitch + u0 + j, o[i]);
+  } else {
+#pragma unroll
+    for (int x = 0; x < 4; x++) {
+      if (j + x >= ncols) break;
+      int32_t X = u0 + j + x;
+      if (it.final_) {
+        X = Q.sigma * X + Q.kappa;
+        if (X < 0) X += Q.W;
+        if (X >= Q.W) X -= Q.W;
+      }
+#pragma unroll
+      for (int i = 0; i < R; i++) row[i * pitch + X] = o[i][x];
+    }
+  }
+}
+
+// First pass, in place (groups of B >= 8 rows): the eight 8-row groups of the
+// staged window become 8-row Brady-Yong blocks over columns [0, W1).  Warp w
+// owns rows [8 w, 8 w + 8) (read and written by no other warp) and walks its
+// columns left to right, 128 per step: a step reads up to 8 columns into the
+// next step's range, which that step only overwrites later.
+template <int W1, typename AccT>
 __device__ __forceinline__ void v_pass1(AccT* S) {
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int kW = kVTile + 56;
 #pragma unroll 1
-  for (int32_t j0 = 0; j0 < kW; j0 += 128) {
+  for (int32_t j0 = 0; j0 < W1; j0 += 128) {
     const int32_t j = j0 + 4 * lane;
     AccT o[8][4];
-    if (j < kW) by_item<8, 1, 0, AccT>(S, 8 * warp, 0, j, o);
+    if (j < W1) by_item<8, 1, 0, AccT>(S, 8 * warp, 0, j, o);
     __syncwarp();  // every lane's reads of this step before any lane's writes
-    if (j < kW) {
+    if (j < W1) {
 #pragma unroll
       for (int i = 0; i < 8; i++) sts4<AccT>(S + (8 * warp + i) * kVPitch + j, o[i]);
     }
@@ -208,68 +282,106 @@ __device__ __forceinline__ void v_pass1(AccT* S) {
   }
 }
 
-// Second pass: the eight 8-row blocks become the 64-row block; slope 8 k + i
-// of child e reads shared row 8 e + k.  Warp w computes k = w for the tile's
-// columns and stores the eight rows to global memory.
-template <int A, typename AccT>
-__device__ __forceinline__ void v_pass2_k(const AccT* S, int32_t k, const FusedItem& it, const QuadDesc& Q,
-                                          AccT* __restrict__ base, int32_t u0, int32_t ncols, bool vec_ok) {
-  const int32_t lane = threadIdx.x & 31;
-  const int64_t pitch = it.dst_pitch;
+// Groups of B = R1 <= 8 rows: one pass, straight to global memory.
+template <int R1, typename AccT>
+__device__ __forceinline__ void v_pass1_out(const AccT* S, const FusedItem& it, const QuadDesc& Q,
+                                            AccT* __restrict__ base, int32_t u0, int32_t ncols, bool vec_ok) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int32_t j0 = 0; j0 < kVTile; j0 += 128) {
     const int32_t j = j0 + 4 * lane;
     if (j >= ncols) break;
-    AccT o[8][4];
-    by_item<8, 8, A, AccT>(S, k, k, j, o);
-    AccT* row = base + (int64_t)(8 * k) * pitch;
-    if (vec_ok && j + 4 <= ncols) {
-#pragma unroll
-      for (int i = 0; i < 8; i++) sts4<AccT>(row + i * pitch + u0 + j, o[i]);
-    } else {
-#pragma unroll
-      for (int x = 0; x < 4; x++) {
-        if (j + x >= ncols) break;
-        int32_t X = u0 + j + x;
-        if (it.final_) {
-          X = Q.sigma * X + Q.kappa;
-          if (X < 0) X += Q.W;
-          if (X >= Q.W) X -= Q.W;
-        }
-#pragma unroll
-        for (int i = 0; i < 8; i++) row[i * pitch + X] = o[i][x];
-      }
+#pragma unroll 1
+    for (int32_t sg = 0; sg < 8; sg += R1) {
+      AccT o[R1][4];
+      by_item<R1, 1, 0, AccT>(S, 8 * warp + sg, 0, j, o);
+      v_store<R1, AccT>(it, Q, base, 8 * warp + sg, u0, j, ncols, vec_ok, o);
     }
   }
 }
 
-// One 64-row block x one tile of kVTile columns (blockDim.x == kVThreads).
+// Second pass: in each group g of B = 8 R2 rows the R2 8-row blocks become
+// the B-row block; slope R2 k + i reads child e at shared row g B + 8 e + k.
+// Warp w computes k = w of every group.
+template <int R2, int A, typename AccT>
+__device__ __forceinline__ void v_pass2_k(const AccT* S, int32_t k, const FusedItem& it, const QuadDesc& Q,
+                                          AccT* __restrict__ base, int32_t u0, int32_t ncols, bool vec_ok) {
+  const int32_t lane = threadIdx.x & 31;
+  constexpr int B = 8 * R2;
+#pragma unroll 1
+  for (int32_t g = 0; g < 64 / B; g++) {
+#pragma unroll 1
+    for (int32_t j0 = 0; j0 < kVTile; j0 += 128) {
+      const int32_t j = j0 + 4 * lane;
+      if (j >= ncols) break;
+      AccT o[R2][4];
+      by_item<R2, 8, A, AccT>(S, g * B + k, k, j, o);
+      v_store<R2, AccT>(it, Q, base, g * B + R2 * k, u0, j, ncols, vec_ok, o);
+    }
+  }
+}
+
+template <int R2, typename AccT>
+__device__ __forceinline__ void v_pass2(const AccT* S, const FusedItem& it, const QuadDesc& Q, AccT* __restrict__ base,
+                                        int32_t u0, int32_t ncols, bool vec_ok) {
+  const int32_t k = threadIdx.x >> 5;
+  switch (k & 3) {
+    case 0:
+      v_pass2_k<R2, 0, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      break;
+    case 1:
+      v_pass2_k<R2, 1, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      break;
+    case 2:
+      v_pass2_k<R2, 2, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      break;
+    default:
+      v_pass2_k<R2, 3, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      break;
+  }
+}
+
+// One 64-row block (FUSED_BY64) or band item (FUSED_BAND: groups of 2^L rows)
+// x one tile of kVTile columns (blockDim.x == kVThreads).
 template <typename InT, typename AccT>
 __device__ __forceinline__ void v_block(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile,
                                         AccT* S) {
   const int32_t u0 = tile * kVTile;
-  v_stage<InT, AccT>(static_cast<const InT*>(p.in), p.in_pitch, Q, it.a, u0 - it.c, S);
+  if (it.kind == FUSED_BAND) {
+    v_stage_band<AccT>(static_cast<const AccT*>(p.ws), it, Q, u0 - it.c, S);
+  } else {
+    v_stage<InT, AccT>(static_cast<const InT*>(p.in), p.in_pitch, Q, it.a, u0 - it.c, S);
+  }
   __syncwarp();
-  v_pass1<AccT>(S);
-  __syncthreads();
   const int32_t ncols = min(kVTile, it.wn - u0);
   AccT* __restrict__ base = (it.final_ ? static_cast<AccT*>(p.out) : static_cast<AccT*>(p.ws)) + it.dst;
   // 16-byte stores need node-local columns (no output map) on 16-byte aligned rows
   const bool vec_ok = !it.final_ && ((it.dst | (int64_t)it.dst_pitch) & 3) == 0 &&
                       (reinterpret_cast<uintptr_t>(p.ws) & 15) == 0;
-  const int32_t k = threadIdx.x >> 5;
-  switch (k & 3) {
-    case 0:
-      v_pass2_k<0, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+  switch (it.L) {
+    case 6:
+      v_pass1<kVTile + 56, AccT>(S);
+      __syncthreads();
+      v_pass2<8, AccT>(S, it, Q, base, u0, ncols, vec_ok);
       break;
-    case 1:
-      v_pass2_k<1, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+    case 5:
+      v_pass1<kVTile + 24, AccT>(S);
+      __syncthreads();
+      v_pass2<4, AccT>(S, it, Q, base, u0, ncols, vec_ok);
+      break;
+    case 4:
+      v_pass1<kVTile + 8, AccT>(S);
+      __syncthreads();
+      v_pass2<2, AccT>(S, it, Q, base, u0, ncols, vec_ok);
+      break;
+    case 3:
+      v_pass1_out<8, AccT>(S, it, Q, base, u0, ncols, vec_ok);
       break;
     case 2:
-      v_pass2_k<2, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      v_pass1_out<4, AccT>(S, it, Q, base, u0, ncols, vec_ok);
       break;
     default:
-      v_pass2_k<3, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      v_pass1_out<2, AccT>(S, it, Q, base, u0, ncols, vec_ok);
       break;
   }
 }

@@ -42,15 +42,19 @@ __global__ void __launch_bounds__(512, 2) fused_kernel(FusedParams p) {
   }
 }
 
-// Register-tiled 64-row blocks (fht_block.cuh): one CTA = one block x one
-// tile of kVTile columns.  The blocks read only the input image, so the launch
-// does not wait for the one before it (the generic subtrees of the same
-// forward) to start; it waits before it exits, so that its completion still
-// implies that launch's, which the next launch relies on.
+// Register-tiled block path (fht_block.cuh): one CTA = one 64-row block or
+// band item x one tile of kVTile columns.  The 64-row blocks read only the
+// input image, so their launch does not wait for the one before it (the
+// generic subtrees of the same forward) to start; it waits before it exits,
+// so that its completion still implies that launch's, which the next launch
+// relies on.  The band launch reads the blocks and waits first.
+enum : int32_t { VB_FIRST = 1, VB_WAIT_FIRST = 2 };
+
 template <typename InT, typename AccT>
-__global__ void __launch_bounds__(kVThreads, 3) block_kernel(FusedParams p, int32_t first) {
+__global__ void __launch_bounds__(kVThreads, 3) block_kernel(FusedParams p, int32_t flags) {
   pdl_launch_dependents();
-  if (first && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+  if (flags & VB_WAIT_FIRST) pdl_wait();
+  if ((flags & VB_FIRST) && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     *reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p.ws) - kWsHeader) = 0;
   const FusedItem it = p.items[blockIdx.x];
   const int32_t tile = blockIdx.y;
@@ -58,7 +62,7 @@ __global__ void __launch_bounds__(kVThreads, 3) block_kernel(FusedParams p, int3
     extern __shared__ __align__(16) unsigned char smem_raw[];
     v_block<InT, AccT>(p, it, p.quad[it.q], tile, reinterpret_cast<AccT*>(smem_raw));
   }
-  pdl_wait();
+  if (!(flags & VB_WAIT_FIRST)) pdl_wait();
 }
 
 // One CTA per output row; every thread keeps U independent element pairs in
@@ -601,7 +605,7 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
     bp.items = D.fused + P.n_generic;
     dim3 grid((unsigned)P.n_by64, P.max_by64_ntiles);
     mark(0);
-    e = go(kbl, grid, kVThreads, D.geo.vsmem, bp, (int32_t)(P.n_generic == 0));
+    e = go(kbl, grid, kVThreads, D.geo.vsmem, bp, (int32_t)(P.n_generic == 0 ? VB_FIRST : 0));
     mark(1);
     launch++;
     if (e != cudaSuccess) return e;
@@ -613,7 +617,15 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
       fp.items = D.band_items;
       dim3 bgrid((unsigned)P.band_items.size(), P.max_band_ntiles);
       mark(0);
-      e = go(kfn, bgrid, P.cfg.threads, smem, fp);
+      if constexpr (sizeof(AccT) == 4) {
+        if (P.vblock) {
+          e = go(block_kernel<InT, AccT>, bgrid, kVThreads, D.geo.vsmem, fp, (int32_t)VB_WAIT_FIRST);
+        } else {
+          e = go(kfn, bgrid, P.cfg.threads, smem, fp);
+        }
+      } else {
+        e = go(kfn, bgrid, P.cfg.threads, smem, fp);
+      }
       mark(1);
       launch++;
       if (e != cudaSuccess) return e;

@@ -143,12 +143,13 @@ VTILE = dict(tile_cols=192, threads=256)
 
 @pytest.mark.parametrize("boundary", ["cyclic", "extended"])
 def test_register_tiled_blocks_u8(F, orc, boundary):
-    """The register-tiled 64-row block launch (tiles of 192 columns, 256
-    threads): 64-row roots (stored through the quadrant column map), blocks
-    only (h a multiple of 64, one launch), blocks after a generic remainder
-    launch, widths around the tile and narrow ones, every quadrant."""
+    """The register-tiled block launches (tiles of 192 columns, 256 threads):
+    64-row roots (stored through the quadrant column map), blocks only (h a
+    multiple of 64, one launch), blocks after a generic remainder launch,
+    bands of every group size 2..64 blocks (a 4096-row band is the root),
+    widths around the tile and narrow ones, every quadrant."""
     for h, w in [(64, 1), (64, 3), (64, 200), (128, 191), (128, 192), (128, 193), (65, 33), (200, 385),
-                 (191, 64), (256, 17), (320, 450), (1000, 77)]:
+                 (191, 64), (256, 17), (320, 450), (1000, 77), (1100, 30), (2100, 21), (4096, 13)]:
         img = inputs.uniform_u8(1000 + h * 3 + w, h, w)
         check_exact(F, orc, img, 15, boundary, **VTILE)
         check_exact(F, orc, img, 1, boundary, **VTILE)
