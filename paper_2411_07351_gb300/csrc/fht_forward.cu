@@ -56,7 +56,8 @@ enum : int32_t { VB_FIRST = 1, VB_WAIT_FIRST = 2 };
 // kPipeProducers producer warps stage unit n into ring slot n mod kPipeBufs
 // (cp.async for 4-byte data) while the kVThreads consumer threads merge the
 // unit before it.  full[b]: the slot's staging has landed (one arrival per
-// producer thread); mid[b]: every consumer warp finished the first pass;
+// producer thread); mid[b]: every consumer warp finished the first pass (one
+// phase per unit, also for the one-pass units);
 // empty[b]: every consumer warp finished reading the slot.  Every wait is
 // bounded (1 s): one that gives up records FHT_ERR_TIMEOUT in the workspace
 // status word and the CTA stops taking units.
@@ -115,14 +116,23 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         give_up();
         break;
       }
+      // every unit completes one phase of mid[sb] (units of groups of at most
+      // 8 rows have one pass and arrive without waiting), so that its phase
+      // count stays the slot's use count
+      bool arrived = false;
       const bool ok = v_merge<AccT>(p, it, Q, tile, S, [&]() {
         __syncwarp();
         if (lane == 0) mbar_arrive(&mid[sb]);
+        arrived = true;
         return mbar_wait_bounded(&mid[sb], ph);
       });
       if (!ok) {
         give_up();
         break;
+      }
+      if (!arrived) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&mid[sb]);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[sb]);

@@ -149,7 +149,8 @@ def test_register_tiled_blocks_u8(F, orc, boundary):
     bands of every group size 2..64 blocks (a 4096-row band is the root),
     widths around the tile and narrow ones, every quadrant."""
     for h, w in [(64, 1), (64, 3), (64, 200), (128, 191), (128, 192), (128, 193), (65, 33), (200, 385),
-                 (191, 64), (256, 17), (320, 450), (1000, 77), (1100, 30), (2100, 21), (4096, 13)]:
+                 (191, 64), (256, 17), (320, 450), (1000, 77), (1100, 30), (2100, 21), (4096, 13), (4095, 9),
+                 (3071, 40)]:
         img = inputs.uniform_u8(1000 + h * 3 + w, h, w)
         check_exact(F, orc, img, 15, boundary, **VTILE)
         check_exact(F, orc, img, 1, boundary, **VTILE)
