@@ -74,10 +74,6 @@ cudaError_t upload_tables(fht_plan_s* p) {
   tp.add(&d.spine_terms, h.spine_terms);
   tp.add(&d.spine_segs, h.spine_segs);
   tp.add(&d.spine_grps, h.spine_grps);
-  tp.add(&d.block_units, h.block_units);
-  tp.add(&d.band_units, h.band_units);
-  if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, p->dev.device) != cudaSuccess || d.sms < 1)
-    d.sms = 1;
   if (h.has_adjoint) {
     tp.add(&d.arows, h.arows);
     tp.add(&d.aterms, h.aterms);
@@ -118,8 +114,6 @@ void free_dev(fht_plan_s* p) {
   d.spine_terms = nullptr;
   d.spine_segs = nullptr;
   d.spine_grps = nullptr;
-  d.block_units = nullptr;
-  d.band_units = nullptr;
 }
 
 }  // namespace

@@ -119,11 +119,12 @@ __device__ __forceinline__ void by_item(const T* S, int32_t row0, int32_t k, int
   by_regs<R, 4, 0, A, T>(c, out);
 }
 
-// Stage the window of rows [8 w, 8 w + 8) of the block (warp w stages the
-// rows its first pass merges, so no CTA barrier is needed before that pass):
-// block row r = view row a + r, window column z = view column x0 + z,
-// z in [0, kVWin), wrapped (cyclic) or zero outside [0, L) (extended), with
-// the quadrant's transpose / column reversal.
+// Stage the window of the block: block row r = view row a + r, window column
+// z = view column x0 + z.  Untransposed views: warp w stages rows
+// [8 w, 8 w + 8), the rows its first pass merges (no CTA barrier needed
+// before that pass); transposed views need one (see below).  z in
+// [0, kVWin), wrapped (cyclic) or zero outside [0, L) (extended), with the
+// quadrant's transpose / column reversal.
 template <typename InT, typename AccT>
 __device__ __forceinline__ void v_stage(const InT* __restrict__ in, int64_t pitch, const QuadDesc& Q, int32_t a,
                                         int32_t x0, AccT* S) {
@@ -154,39 +155,30 @@ __device__ __forceinline__ void v_stage(const InT* __restrict__ in, int64_t pitc
     }
   } else {
     // transposed view: block row r is image column a + r, window column z an
-    // image row.  Lane = (r & 7) + 8 (z & 3): a warp instruction reads 32
-    // bytes of four image rows and writes 8 rows x 4 columns of shared memory
-    // (distinct banks: kVPitch / 4 is odd).
-    const int32_t rl = lane & 7, zl = lane >> 3;
-    const int32_t r = 8 * warp + rl;
-    const bool inside = x0 >= 0 && x0 + kVWin <= Q.L;
-#pragma unroll 1
-    for (int zb = 0; zb < kVWin; zb += 128) {
-      AccT v[32];
-      if (inside) {
-        // image rows z0, z0 + 4, ... (reversed for the leftward quadrant)
-        const int32_t z0 = x0 + zb + zl;
-        const InT* __restrict__ src = in + (int64_t)(Q.flip ? Q.L - 1 - z0 : z0) * pitch + a + r;
-        const int64_t step = Q.flip ? -4 * pitch : 4 * pitch;
+    // image row.  Lanes run along 32 block rows (one 128-byte stretch of an
+    // image row per load); warp w covers rows 32 (w & 1) + lane and the 64
+    // window columns [64 (w >> 1), + 64), four at a time into one 16-byte
+    // shared store (conflict-free: the rows of a quarter-warp start kVPitch
+    // words apart, 16 bytes apart modulo 128).  The boundary test depends on
+    // the column only, so it is uniform across the warp.
+    const int32_t r = 32 * (warp & 1) + lane;
+    const int32_t zc = 64 * (warp >> 1);
+    const InT* __restrict__ col = in + a + r;
+    AccT v[64];
 #pragma unroll
-        for (int c = 0; c < 32; c++) v[c] = (AccT)__ldg(src + c * step);
-      } else {
-#pragma unroll
-        for (int c = 0; c < 32; c++) {
-          int32_t z = x0 + zb + 4 * c + zl;
-          bool ok = true;
-          if (Q.ext) {
-            ok = z >= 0 && z < Q.L;
-          } else if (z >= Q.L) {
-            z = z < 2 * Q.L ? z - Q.L : z % Q.L;  // cyclic windows start at column >= 0
-          }
-          if (Q.flip) z = Q.L - 1 - z;
-          v[c] = ok ? (AccT)__ldg(in + (int64_t)z * pitch + a + r) : AccT(0);
-        }
+    for (int c = 0; c < 64; c++) {
+      int32_t z = x0 + zc + c;
+      bool ok = true;
+      if (Q.ext) {
+        ok = z >= 0 && z < Q.L;
+      } else if (z >= Q.L) {
+        z = z < 2 * Q.L ? z - Q.L : z % Q.L;  // cyclic windows start at column >= 0
       }
-#pragma unroll
-      for (int c = 0; c < 32; c++) S[r * kVPitch + zb + 4 * c + zl] = v[c];
+      if (Q.flip) z = Q.L - 1 - z;
+      v[c] = ok ? (AccT)__ldg(col + (int64_t)z * pitch) : AccT(0);
     }
+#pragma unroll
+    for (int c = 0; c < 64; c += 4) sts4<AccT>(S + r * kVPitch + zc + c, &v[c]);
   }
 }
 
@@ -395,197 +387,15 @@ __device__ __forceinline__ void v_block(const FusedParams& p, const FusedItem& i
   } else {
     v_stage<InT, AccT>(static_cast<const InT*>(p.in), p.in_pitch, Q, it.a, x0, S);
   }
-  __syncwarp();
+  if (it.kind != FUSED_BAND && Q.transpose) {
+    __syncthreads();  // transposed staging crosses the warps' row groups
+  } else {
+    __syncwarp();
+  }
   v_merge<AccT>(p, it, Q, tile, S, [] {
     __syncthreads();
     return true;
   });
-}
-
-// ---------------------------------------------------------------------------
-// Warp-specialised persistent form: one CTA per SM walks a list of (item,
-// tile) units.  kPipeProducers warps stage unit n into ring buffer n mod
-// kPipeBufs while the kVThreads / 32 consumer warps merge the unit before it;
-// full[] / empty[] mbarriers hand the buffers over.
-// ---------------------------------------------------------------------------
-constexpr int kPipeBufs = kPipeBufsHost;
-constexpr int kPipeProducers = 4;
-constexpr int kPipeThreads = kVThreads + 32 * kPipeProducers;
-constexpr int kPipeProdThreads = 32 * kPipeProducers;
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Arrives on `bar` once every cp.async this thread issued so far has landed
-// (the arrival is one of the barrier's expected arrivals).
-__device__ __forceinline__ void mbar_arrive_cp_async(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Bounded wait for phase `parity` of `bar`: false after ~1 s.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer_ns() - t0 > 1000000000ull) return false;
-  }
-  return true;
-}
-
-// Producer staging of a 64-row block window (4-byte input, cp.async element
-// copies: no registers held, every copy of the unit in flight at once; the
-// copies outside the view's real columns read nothing and write zeros).
-// Producer warp pw stages rows [16 pw, 16 pw + 16).  Same window as v_stage.
-template <typename InT, typename AccT>
-__device__ __forceinline__ void p_stage_async(const InT* __restrict__ in, int64_t pitch, const QuadDesc& Q, int32_t a,
-                                              int32_t x0, AccT* S, int32_t pw, int32_t lane) {
-  static_assert(sizeof(InT) == 4 && sizeof(AccT) == 4, "element copies of 4-byte inputs");
-  const bool inside = x0 >= 0 && x0 + kVWin <= Q.L;
-  if (!Q.transpose) {
-#pragma unroll 1
-    for (int rr = 0; rr < 16; rr++) {
-      const int32_t r = 16 * pw + rr;
-      const InT* __restrict__ rowp = in + (int64_t)(a + r) * pitch;
-      AccT* dst = S + r * kVPitch + lane;
-      if (inside) {
-        const InT* src = Q.flip ? rowp + (Q.L - 1 - x0 - lane) : rowp + x0 + lane;
-        const int32_t step = Q.flip ? -32 : 32;
-#pragma unroll
-        for (int c = 0; c < kVWin / 32; c++) cp_async_4(dst + 32 * c, src + c * step, 4);
-      } else {
-#pragma unroll
-        for (int c = 0; c < kVWin / 32; c++) {
-          int32_t z = x0 + 32 * c + lane;
-          bool ok = true;
-          if (Q.ext) {
-            ok = z >= 0 && z < Q.L;
-          } else if (z >= Q.L) {
-            z = z < 2 * Q.L ? z - Q.L : z % Q.L;  // cyclic windows start at column >= 0
-          }
-          if (Q.flip) z = Q.L - 1 - z;
-          cp_async_4(dst + 32 * c, ok ? rowp + z : rowp, ok ? 4 : 0);
-        }
-      }
-    }
-  } else {
-    // lane = (r & 7) + 8 (z & 3), as in v_stage
-    const int32_t rl = lane & 7, zl = lane >> 3;
-#pragma unroll 1
-    for (int rb = 0; rb < 2; rb++) {
-      const int32_t r = 16 * pw + 8 * rb + rl;
-      AccT* dst = S + r * kVPitch + zl;
-      if (inside) {
-        const int32_t z0 = x0 + zl;
-        const InT* src = in + (int64_t)(Q.flip ? Q.L - 1 - z0 : z0) * pitch + a + r;
-        const int64_t step = Q.flip ? -4 * pitch : 4 * pitch;
-#pragma unroll 8
-        for (int c = 0; c < kVWin / 4; c++) cp_async_4(dst + 4 * c, src + c * step, 4);
-      } else {
-#pragma unroll 8
-        for (int c = 0; c < kVWin / 4; c++) {
-          int32_t z = x0 + 4 * c + zl;
-          bool ok = true;
-          if (Q.ext) {
-            ok = z >= 0 && z < Q.L;
-          } else if (z >= Q.L) {
-            z = z < 2 * Q.L ? z - Q.L : z % Q.L;
-          }
-          if (Q.flip) z = Q.L - 1 - z;
-          cp_async_4(dst + 4 * c, ok ? in + (int64_t)z * pitch + a + r : in, ok ? 4 : 0);
-        }
-      }
-    }
-  }
-}
-
-// Producer staging of a block window from 1-byte input (widened to the
-// 4-byte accumulator, so through registers): batches of 4 rows x 8 loads.
-template <typename InT, typename AccT>
-__device__ __forceinline__ void p_stage_regs(const InT* __restrict__ in, int64_t pitch, const QuadDesc& Q, int32_t a,
-                                             int32_t x0, AccT* S, int32_t pw, int32_t lane) {
-  const bool inside = x0 >= 0 && x0 + kVWin <= Q.L;
-  if (!Q.transpose) {
-#pragma unroll 1
-    for (int rb = 0; rb < 16; rb += 4) {
-      AccT v[4][kVWin / 32];
-#pragma unroll
-      for (int rr = 0; rr < 4; rr++) {
-        const InT* __restrict__ rowp = in + (int64_t)(a + 16 * pw + rb + rr) * pitch;
-        if (inside) {
-          const InT* src = Q.flip ? rowp + (Q.L - 1 - x0 - lane) : rowp + x0 + lane;
-          const int32_t step = Q.flip ? -32 : 32;
-#pragma unroll
-          for (int c = 0; c < kVWin / 32; c++) v[rr][c] = (AccT)__ldg(src + c * step);
-        } else {
-#pragma unroll
-          for (int c = 0; c < kVWin / 32; c++) v[rr][c] = load_view_elem<InT, AccT>(rowp, Q, x0 + 32 * c + lane);
-        }
-      }
-#pragma unroll
-      for (int rr = 0; rr < 4; rr++) {
-        AccT* dst = S + (16 * pw + rb + rr) * kVPitch + lane;
-#pragma unroll
-        for (int c = 0; c < kVWin / 32; c++) dst[32 * c] = v[rr][c];
-      }
-    }
-  } else {
-    const int32_t rl = lane & 7, zl = lane >> 3;
-#pragma unroll 1
-    for (int rb = 0; rb < 2; rb++) {
-      const int32_t r = 16 * pw + 8 * rb + rl;
-#pragma unroll 1
-      for (int zb = 0; zb < kVWin; zb += 128) {
-        AccT v[32];
-#pragma unroll
-        for (int c = 0; c < 32; c++) {
-          int32_t z = x0 + zb + 4 * c + zl;
-          bool ok = true;
-          if (Q.ext) {
-            ok = z >= 0 && z < Q.L;
-          } else if (z >= Q.L) {
-            z = z < 2 * Q.L ? z - Q.L : z % Q.L;
-          }
-          if (Q.flip) z = Q.L - 1 - z;
-          v[c] = ok ? (AccT)__ldg(in + (int64_t)z * pitch + a + r) : AccT(0);
-        }
-#pragma unroll
-        for (int c = 0; c < 32; c++) S[r * kVPitch + zb + 4 * c + zl] = v[c];
-      }
-    }
-  }
-}
-
-// Producer staging of a band item's gathered rows (workspace, cp.async).
-template <typename AccT>
-__device__ __forceinline__ void p_stage_band(const AccT* __restrict__ ws, const FusedItem& it, const QuadDesc& Q,
-                                             int32_t x0, AccT* S, int32_t pw, int32_t lane) {
-  const int32_t lim = Q.ext ? it.wsrc : Q.W;
-#pragma unroll 1
-  for (int rr = 0; rr < 16; rr++) {
-    const int32_t r = 16 * pw + rr;
-    const int32_t g = r / it.B, b = r - g * it.B;
-    const int32_t K = it.K0 + g;
-    const AccT* __restrict__ row = ws + it.src + (int64_t)(64 * b + K) * it.src_pitch;
-    const int32_t base = x0 + K * b + it.c_src;  // >= 0 in the cyclic case
-    AccT* dst = S + r * kVPitch + lane;
-    if (base >= 0 && base + kVWin <= lim) {
-#pragma unroll
-      for (int c = 0; c < kVWin / 32; c++) cp_async_4(dst + 32 * c, row + base + 32 * c + lane, 4);
-    } else {
-#pragma unroll
-      for (int c = 0; c < kVWin / 32; c++) {
-        int32_t z = base + 32 * c + lane;
-        bool ok = true;
-        if (Q.ext) {
-          ok = z >= 0 && z < it.wsrc;
-        } else if (z >= Q.W) {
-          z = z < 2 * Q.W ? z - Q.W : z % Q.W;
-        }
-        cp_async_4(dst + 32 * c, ok ? row + z : row, ok ? 4 : 0);
-      }
-    }
-  }
 }
 
 }  // namespace fht

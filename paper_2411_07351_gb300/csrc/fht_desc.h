@@ -60,7 +60,6 @@ enum : int32_t { FUSED_GENERIC = 0, FUSED_BY64 = 1, FUSED_BAND = 2 };
 constexpr int32_t kVTile = 192;
 constexpr int32_t kVThreads = 256;
 constexpr int32_t kVPitch = 260;
-constexpr int32_t kPipeBufsHost = 3;  // shared ring slots of the persistent form (kPipeBufs on the device)
 
 // The quadrant table passed by value to kernels.
 struct QuadDescs {

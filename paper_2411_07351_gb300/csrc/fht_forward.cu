@@ -51,94 +51,18 @@ __global__ void __launch_bounds__(512, 2) fused_kernel(FusedParams p) {
 // that launch's, which the next launch relies on.
 enum : int32_t { VB_FIRST = 1, VB_WAIT_FIRST = 2 };
 
-// Warp-specialised persistent form (fht_block.cuh): one CTA per SM walks the
-// units (item << 9 | tile) u = blockIdx.x, blockIdx.x + gridDim.x, ...; the
-// kPipeProducers producer warps stage unit n into ring slot n mod kPipeBufs
-// (cp.async for 4-byte data) while the kVThreads consumer threads merge the
-// unit before it.  full[b]: the slot's staging has landed (one arrival per
-// producer thread); mid[b]: every consumer warp finished the first pass (one
-// phase per unit, also for the one-pass units);
-// empty[b]: every consumer warp finished reading the slot.  Every wait is
-// bounded (1 s): one that gives up records FHT_ERR_TIMEOUT in the workspace
-// status word and the CTA stops taking units.
 template <typename InT, typename AccT>
-__global__ void __launch_bounds__(kPipeThreads, 1)
-    block_pipe_kernel(FusedParams p, const int32_t* __restrict__ units, int32_t nunits, int32_t flags) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[kPipeBufs], mid[kPipeBufs], empty[kPipeBufs];
+__global__ void __launch_bounds__(kVThreads, 3) block_kernel(FusedParams p, int32_t flags) {
   pdl_launch_dependents();
   if (flags & VB_WAIT_FIRST) pdl_wait();
-  int32_t* status = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p.ws) - kWsHeader);
-  if ((flags & VB_FIRST) && blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
-  if (threadIdx.x == 0) {
-    for (int b = 0; b < kPipeBufs; b++) {
-      mbar_init(&full[b], kPipeProdThreads);
-      mbar_init(&mid[b], kVThreads / 32);
-      mbar_init(&empty[b], kVThreads / 32);
-    }
+  if ((flags & VB_FIRST) && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    *reinterpret_cast<int32_t*>(static_cast<unsigned char*>(p.ws) - kWsHeader) = 0;
+  const FusedItem it = p.items[blockIdx.x];
+  const int32_t tile = blockIdx.y;
+  if (tile < it.ntiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    v_block<InT, AccT>(p, it, p.quad[it.q], tile, reinterpret_cast<AccT*>(smem_raw));
   }
-  __syncthreads();
-  AccT* bufs = reinterpret_cast<AccT*>(smem_raw);
-  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool producer = warp >= kVThreads / 32;
-  auto give_up = [&]() {
-    atomicCAS(status, 0, (int32_t)FHT_ERR_TIMEOUT);
-  };
-  int32_t n = 0;
-  for (int32_t u = blockIdx.x; u < nunits; u += gridDim.x, n++) {
-    const int32_t sb = n % kPipeBufs;
-    const uint32_t ph = (uint32_t)(n / kPipeBufs) & 1u;
-    AccT* S = bufs + (size_t)sb * 64 * kVPitch;
-    const int32_t code = __ldg(units + u);
-    const FusedItem& it = p.items[code >> 9];
-    const int32_t tile = code & 511;
-    const QuadDesc& Q = p.quad[it.q];
-    if (producer) {
-      // the slot's previous unit (n - kPipeBufs) must be fully read
-      if (n >= kPipeBufs && !mbar_wait_bounded(&empty[sb], ph ^ 1u)) {
-        give_up();
-        break;
-      }
-      const int32_t x0 = tile * kVTile - it.c;
-      const int32_t pw = warp - kVThreads / 32;
-      if (it.kind == FUSED_BAND) {
-        p_stage_band<AccT>(static_cast<const AccT*>(p.ws), it, Q, x0, S, pw, lane);
-        mbar_arrive_cp_async(&full[sb]);
-      } else if constexpr (sizeof(InT) == 4) {
-        p_stage_async<InT, AccT>(static_cast<const InT*>(p.in), p.in_pitch, Q, it.a, x0, S, pw, lane);
-        mbar_arrive_cp_async(&full[sb]);
-      } else {
-        p_stage_regs<InT, AccT>(static_cast<const InT*>(p.in), p.in_pitch, Q, it.a, x0, S, pw, lane);
-        mbar_arrive(&full[sb]);
-      }
-    } else {
-      if (!mbar_wait_bounded(&full[sb], ph)) {
-        give_up();
-        break;
-      }
-      // every unit completes one phase of mid[sb] (units of groups of at most
-      // 8 rows have one pass and arrive without waiting), so that its phase
-      // count stays the slot's use count
-      bool arrived = false;
-      const bool ok = v_merge<AccT>(p, it, Q, tile, S, [&]() {
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&mid[sb]);
-        arrived = true;
-        return mbar_wait_bounded(&mid[sb], ph);
-      });
-      if (!ok) {
-        give_up();
-        break;
-      }
-      if (!arrived) {
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&mid[sb]);
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[sb]);
-    }
-  }
-  if (producer) cp_async_wait_all();  // nothing of this CTA's may still be landing when it exits
   if (!(flags & VB_WAIT_FIRST)) pdl_wait();
 }
 
@@ -564,7 +488,7 @@ void fused_geometry(const HostPlan& P, FusedGeometry& g) {
   size_t by64 = P.n_by64 > 0 ? (size_t)64 * (g.RS + g.RA) * P.acc_size : 0;
   g.smem = std::max(generic, by64);
   g.gsmem = generic;
-  g.vsmem = P.vblock ? (size_t)kPipeBufs * 64 * kVPitch * P.acc_size : 0;
+  g.vsmem = P.vblock ? (size_t)64 * kVPitch * P.acc_size : 0;
 }
 
 // Fused launches of a forward: one, or on the register-tiled path the
@@ -674,15 +598,14 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
       launch++;
       if (e != cudaSuccess) return e;
     }
-    auto kbl = block_pipe_kernel<InT, AccT>;
+    auto kbl = block_kernel<InT, AccT>;
     if ((e = cudaFuncSetAttribute(kbl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D.geo.vsmem)) !=
         cudaSuccess)
       return e;
     FusedParams bp = fp;
     bp.items = D.fused + P.n_generic;
-    const int32_t nu = (int32_t)P.block_units.size();
     mark(0);
-    e = go(kbl, dim3((unsigned)std::min(nu, D.sms)), kPipeThreads, D.geo.vsmem, bp, (const int32_t*)D.block_units, nu,
+    e = go(kbl, dim3((unsigned)P.n_by64, P.max_by64_ntiles), kVThreads, D.geo.vsmem, bp,
            (int32_t)(P.n_generic == 0 ? VB_FIRST : 0));
     mark(1);
     launch++;
@@ -697,13 +620,11 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
       mark(0);
       if constexpr (sizeof(AccT) == 4) {
         if (P.vblock) {
-          auto kbp = block_pipe_kernel<InT, AccT>;
+          auto kbp = block_kernel<InT, AccT>;
           if ((e = cudaFuncSetAttribute(kbp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D.geo.vsmem)) !=
               cudaSuccess)
             return e;
-          const int32_t nu = (int32_t)P.band_units.size();
-          e = go(kbp, dim3((unsigned)std::min(nu, D.sms)), kPipeThreads, D.geo.vsmem, fp,
-                 (const int32_t*)D.band_units, nu, (int32_t)VB_WAIT_FIRST);
+          e = go(kbp, bgrid, kVThreads, D.geo.vsmem, fp, (int32_t)VB_WAIT_FIRST);
         } else {
           e = go(kfn, bgrid, P.cfg.threads, smem, fp);
         }

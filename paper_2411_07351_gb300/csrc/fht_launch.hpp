@@ -32,9 +32,6 @@ struct DevicePlan {
   AdjTerm* aterms = nullptr;
   int32_t* aptr = nullptr;
   MergeOp* aops = nullptr;
-  int32_t* block_units = nullptr;  // persistent block / band launches (register-tiled path)
-  int32_t* band_units = nullptr;
-  int32_t sms = 1;                 // multiprocessors of the device (persistent grids)
   FusedGeometry geo;
 };
 

@@ -772,13 +772,7 @@ std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
     }
   }
   P.vblock = P.acc_size == 4 && cfg.TW == kVTile && cfg.threads == kVThreads && P.n_by64 > 0;
-  if (P.vblock) {
-    for (size_t k = (size_t)P.n_generic; k < P.fused.size(); k++)
-      for (int32_t t = 0; t < P.fused[k].ntiles; t++)
-        P.block_units.push_back((int32_t)(((k - (size_t)P.n_generic) << 9) | (size_t)t));
-    for (size_t k = 0; k < P.band_items.size(); k++)
-      for (int32_t t = 0; t < P.band_items[k].ntiles; t++) P.band_units.push_back((int32_t)((k << 9) | (size_t)t));
-  }
+
   P.out_elems = out_off;
   P.ws_bytes = kWsHeader + (size_t)ws_off * acc;
   // adjoint: one h x w gradient image per quadrant after the forward buffers

@@ -105,9 +105,6 @@ struct HostPlan {
   int32_t n_generic = 0;
   int32_t max_generic_ntiles = 0, max_by64_ntiles = 0;
   int64_t generic_bytes = 0, by64_bytes = 0;  // model bytes of the two kinds of fused items
-  // work units of the persistent block and band launches: (item << 9) | tile,
-  // item counted from the launch's first item, tiles of one item consecutive
-  std::vector<int32_t> block_units, band_units;
   int64_t adds = 0, model_bytes = 0, ideal_bytes = 0;
   // band schedule (Split_T with 64-row fused blocks): one gathered
   // Brady-Yong pass for every perfect band above the blocks, then one

@@ -127,22 +127,7 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
       }
     }
   }
-  // ---- persistent register-tiled launches: every unit names a real item and tile ----
-  if (P.vblock) {
-    if ((size_t)kPipeBufsHost * 64 * kVPitch * P.acc_size > g.vsmem) return "block launch: shared ring too small";
-    for (size_t k = 0; k < P.block_units.size(); k++) {
-      const int32_t item = P.block_units[k] >> 9, tile = P.block_units[k] & 511;
-      if (item < 0 || item >= P.n_by64 || (size_t)(P.n_generic + item) >= P.fused.size() ||
-          tile >= P.fused[(size_t)P.n_generic + item].ntiles)
-        return at("block unit", (int64_t)k) + "names no 64-row block tile";
-    }
-    for (size_t k = 0; k < P.band_units.size(); k++) {
-      const int32_t item = P.band_units[k] >> 9, tile = P.band_units[k] & 511;
-      if (item < 0 || (size_t)item >= P.band_items.size() || tile >= P.band_items[(size_t)item].ntiles)
-        return at("band unit", (int64_t)k) + "names no band tile";
-      if (P.band_items[(size_t)item].tw != kVTile) return at("band unit", (int64_t)k) + "band tile width";
-    }
-  }
+  if (P.vblock && (size_t)64 * kVPitch * P.acc_size > g.vsmem) return "block launch: shared buffer too small";
   // ---- band schedule ----
   for (size_t k = 0; k < P.band_items.size(); k++) {
     const FusedItem& it = P.band_items[k];
