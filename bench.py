@@ -117,7 +117,7 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-FORWARD_SOURCES = ("fht_desc.h", "fht_device.cuh", "fht_forward.cu", "fht_launch.hpp")
+FORWARD_SOURCES = ("fht_desc.h", "fht_device.cuh", "fht_block.cuh", "fht_forward.cu", "fht_launch.hpp")
 
 
 def _source_hash() -> str:

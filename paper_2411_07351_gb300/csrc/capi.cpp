@@ -137,8 +137,8 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
   cfg.ext = (int32_t)boundary;
   cfg.split = split == FHT_SPLIT_S ? fht::Split::S : fht::Split::T;
   cfg.F = 64;
-  cfg.TW = dtype == FHT_F64_F64 ? 64 : 128;
-  cfg.threads = 512;
+  cfg.TW = 0;       // the planner's default launch shape
+  cfg.threads = 0;
   if (tuning) {
     if (tuning->fused_rows) cfg.F = tuning->fused_rows;
     if (tuning->tile_cols) cfg.TW = tuning->tile_cols;

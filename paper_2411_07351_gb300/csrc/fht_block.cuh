@@ -119,12 +119,11 @@ __device__ __forceinline__ void by_item(const T* S, int32_t row0, int32_t k, int
   by_regs<R, 4, 0, A, T>(c, out);
 }
 
-// Stage the window of the block: block row r = view row a + r, window column
-// z = view column x0 + z.  Untransposed views: warp w stages rows
-// [8 w, 8 w + 8), the rows its first pass merges (no CTA barrier needed
-// before that pass); transposed views need one (see below).  z in
-// [0, kVWin), wrapped (cyclic) or zero outside [0, L) (extended), with the
-// quadrant's transpose / column reversal.
+// Stage the window of rows [8 w, 8 w + 8) of the block (warp w stages the
+// rows its first pass merges, so no CTA barrier is needed before that pass):
+// block row r = view row a + r, window column z = view column x0 + z,
+// z in [0, kVWin), wrapped (cyclic) or zero outside [0, L) (extended), with
+// the quadrant's transpose / column reversal.
 template <typename InT, typename AccT>
 __device__ __forceinline__ void v_stage(const InT* __restrict__ in, int64_t pitch, const QuadDesc& Q, int32_t a,
                                         int32_t x0, AccT* S) {
@@ -155,30 +154,39 @@ __device__ __forceinline__ void v_stage(const InT* __restrict__ in, int64_t pitc
     }
   } else {
     // transposed view: block row r is image column a + r, window column z an
-    // image row.  Lanes run along 32 block rows (one 128-byte stretch of an
-    // image row per load); warp w covers rows 32 (w & 1) + lane and the 64
-    // window columns [64 (w >> 1), + 64), four at a time into one 16-byte
-    // shared store (conflict-free: the rows of a quarter-warp start kVPitch
-    // words apart, 16 bytes apart modulo 128).  The boundary test depends on
-    // the column only, so it is uniform across the warp.
-    const int32_t r = 32 * (warp & 1) + lane;
-    const int32_t zc = 64 * (warp >> 1);
-    const InT* __restrict__ col = in + a + r;
-    AccT v[64];
+    // image row.  Lane = (r & 7) + 8 (z & 3): a warp instruction reads 32
+    // bytes of four image rows and writes 8 rows x 4 columns of shared memory
+    // (distinct banks: kVPitch / 4 is odd).
+    const int32_t rl = lane & 7, zl = lane >> 3;
+    const int32_t r = 8 * warp + rl;
+    const bool inside = x0 >= 0 && x0 + kVWin <= Q.L;
+#pragma unroll 1
+    for (int zb = 0; zb < kVWin; zb += 128) {
+      AccT v[32];
+      if (inside) {
+        // image rows z0, z0 + 4, ... (reversed for the leftward quadrant)
+        const int32_t z0 = x0 + zb + zl;
+        const InT* __restrict__ src = in + (int64_t)(Q.flip ? Q.L - 1 - z0 : z0) * pitch + a + r;
+        const int64_t step = Q.flip ? -4 * pitch : 4 * pitch;
 #pragma unroll
-    for (int c = 0; c < 64; c++) {
-      int32_t z = x0 + zc + c;
-      bool ok = true;
-      if (Q.ext) {
-        ok = z >= 0 && z < Q.L;
-      } else if (z >= Q.L) {
-        z = z < 2 * Q.L ? z - Q.L : z % Q.L;  // cyclic windows start at column >= 0
+        for (int c = 0; c < 32; c++) v[c] = (AccT)__ldg(src + c * step);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 32; c++) {
+          int32_t z = x0 + zb + 4 * c + zl;
+          bool ok = true;
+          if (Q.ext) {
+            ok = z >= 0 && z < Q.L;
+          } else if (z >= Q.L) {
+            z = z < 2 * Q.L ? z - Q.L : z % Q.L;  // cyclic windows start at column >= 0
+          }
+          if (Q.flip) z = Q.L - 1 - z;
+          v[c] = ok ? (AccT)__ldg(in + (int64_t)z * pitch + a + r) : AccT(0);
+        }
       }
-      if (Q.flip) z = Q.L - 1 - z;
-      v[c] = ok ? (AccT)__ldg(col + (int64_t)z * pitch) : AccT(0);
-    }
 #pragma unroll
-    for (int c = 0; c < 64; c += 4) sts4<AccT>(S + r * kVPitch + zc + c, &v[c]);
+      for (int c = 0; c < 32; c++) S[r * kVPitch + zb + 4 * c + zl] = v[c];
+    }
   }
 }
 
@@ -387,11 +395,7 @@ __device__ __forceinline__ void v_block(const FusedParams& p, const FusedItem& i
   } else {
     v_stage<InT, AccT>(static_cast<const InT*>(p.in), p.in_pitch, Q, it.a, x0, S);
   }
-  if (it.kind != FUSED_BAND && Q.transpose) {
-    __syncthreads();  // transposed staging crosses the warps' row groups
-  } else {
-    __syncwarp();
-  }
+  __syncwarp();
   v_merge<AccT>(p, it, Q, tile, S, [] {
     __syncthreads();
     return true;

@@ -267,7 +267,27 @@ static void build_spine_staging(HostPlan& P) {
   }
 }
 
-std::string build_plan(const PlanConfig& cfg, HostPlan& P) {
+// Launch shape of the block passes when the caller sets none (0): the
+// register-tiled path (kVTile columns, kVThreads threads) where it measured
+// faster than the shared-memory radix-4 path on GB300 (4-byte accumulators,
+// Split_T with 64-row blocks, every requested quadrant at least 2048 rows,
+// not a power of two, whose root band would store through the column map
+// element by element, and at least 512 columns); otherwise 128 columns (64
+// for double) x 512 threads.
+static void default_launch_shape(PlanConfig& c) {
+  bool vt = dtype_acc_size(c.dtype) == 4 && c.split == Split::T && c.F == 64;
+  for (int q = 0; q < 4; q++) {
+    if (!(c.quads & (1u << q))) continue;
+    const int32_t n = q < 2 ? c.h : c.w, L = q < 2 ? c.w : c.h;
+    vt = vt && n >= 2048 && (n & (n - 1)) != 0 && L >= 512;
+  }
+  if (c.TW == 0) c.TW = vt ? kVTile : (c.dtype == 3 ? 64 : 128);
+  if (c.threads == 0) c.threads = c.TW == kVTile ? kVThreads : 512;
+}
+
+std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
+  PlanConfig cfg = cfg_in;
+  default_launch_shape(cfg);
   if (cfg.h < 1 || cfg.w < 1 || cfg.h > 65535 || cfg.w > 65535) return "h and w must be in [1, 65535]";
   if (cfg.dtype < 0 || cfg.dtype > 3) return "unknown dtype";
   if (cfg.quads == 0 || (cfg.quads & ~15u)) return "quadrants must be a non-empty subset of FHT_QALL";

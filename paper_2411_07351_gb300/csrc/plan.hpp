@@ -53,8 +53,8 @@ struct PlanConfig {
   int32_t ext = 0;         // boundary
   Split split = Split::T;
   int32_t F = 64;          // fused rows
-  int32_t TW = 128;        // fused column tile
-  int32_t threads = 256;   // fused CTA size
+  int32_t TW = 0;          // fused column tile (0: the planner's default)
+  int32_t threads = 0;     // fused CTA size (0: the planner's default)
   int32_t spine_chunk = 3; // spine nodes merged per spine-sum launch (the lower chunks first)
   bool with_adjoint = false;  // also build the adjoint tables
   int32_t rounding = 0;       // 0: exact half-to-even; 1: rint(t * k) with k = (m_i - 1)/(m - 1) in fp64
