@@ -23,6 +23,7 @@
 #include "fht_desc.h"
 #include "fht_device.cuh"
 #include "fht_launch.hpp"
+#include "fht_nvtx.hpp"
 
 namespace fht {
 
@@ -277,6 +278,7 @@ cudaError_t launch_batch(fht_queue_s* q, int32_t nunits, size_t smem, cudaStream
     return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, q->device)) != cudaSuccess) return e;
   const int grid = std::max(1, std::min<int>(nunits, std::max(1, per_sm) * sms));
+  fht::NvtxRange nv("fht batch kernel");
   kfn<<<grid, fht::kBatchThreads, smem, st>>>(q->d_jobs, q->d_units, nunits, q->d_counters, q->d_status,
                                               q->wait_ns);
   return cudaGetLastError();

@@ -16,6 +16,7 @@
 
 #include "fht_desc.h"
 #include "fht_launch.hpp"
+#include "fht_nvtx.hpp"
 
 namespace fht {
 
@@ -228,6 +229,7 @@ template <typename AccT>
 static cudaError_t launch_adjoint_t(const DevicePlan& D, const void* gout, void* gin, int64_t gin_pitch, void* ws,
                                     cudaStream_t st) {
   const HostPlan& P = *D.host;
+  NvtxRange nv("fht adjoint");
   AccT* wsa = reinterpret_cast<AccT*>(static_cast<unsigned char*>(ws) + kWsHeader);
   cudaError_t e;
   for (size_t p = 0; p + 1 < P.apass_begin.size(); p++) {

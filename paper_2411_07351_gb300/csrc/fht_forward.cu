@@ -18,6 +18,7 @@
 #include "fht_block.cuh"
 #include "fht_device.cuh"
 #include "fht_launch.hpp"
+#include "fht_nvtx.hpp"
 
 namespace fht {
 
@@ -584,17 +585,21 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
   if (e != cudaSuccess) return e;
   if (!P.vblock) {
     dim3 grid((unsigned)P.fused.size(), P.max_ntiles);  // tiles <= 131070 / 32 fit in grid.y
+    nvtxRangePushA("fht fused subtrees");
     mark(0);
     e = go(kfn, grid, P.cfg.threads, smem, fp);
     mark(1);
+    nvtxRangePop();
     launch++;
     if (e != cudaSuccess) return e;
   } else if constexpr (sizeof(AccT) == 4) {
     if (P.n_generic > 0) {
       dim3 grid((unsigned)P.n_generic, P.max_generic_ntiles);
+      nvtxRangePushA("fht generic subtrees");
       mark(0);
       e = go(kfn, grid, P.cfg.threads, D.geo.gsmem, fp);
       mark(1);
+      nvtxRangePop();
       launch++;
       if (e != cudaSuccess) return e;
     }
@@ -604,10 +609,12 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
       return e;
     FusedParams bp = fp;
     bp.items = D.fused + P.n_generic;
+    nvtxRangePushA("fht 64-row blocks");
     mark(0);
     e = go(kbl, dim3((unsigned)P.n_by64, P.max_by64_ntiles), kVThreads, D.geo.vsmem, bp,
            (int32_t)(P.n_generic == 0 ? VB_FIRST : 0));
     mark(1);
+    nvtxRangePop();
     launch++;
     if (e != cudaSuccess) return e;
   } else {
@@ -617,14 +624,17 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
     if (!P.band_items.empty()) {
       fp.items = D.band_items;
       dim3 bgrid((unsigned)P.band_items.size(), P.max_band_ntiles);
+      if constexpr (sizeof(AccT) == 4) {
+        if (P.vblock &&
+            (e = cudaFuncSetAttribute(block_kernel<InT, AccT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)D.geo.vsmem)) != cudaSuccess)
+          return e;
+      }
+      nvtxRangePushA("fht band pass");
       mark(0);
       if constexpr (sizeof(AccT) == 4) {
         if (P.vblock) {
-          auto kbp = block_kernel<InT, AccT>;
-          if ((e = cudaFuncSetAttribute(kbp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D.geo.vsmem)) !=
-              cudaSuccess)
-            return e;
-          e = go(kbp, bgrid, kVThreads, D.geo.vsmem, fp, (int32_t)VB_WAIT_FIRST);
+          e = go(block_kernel<InT, AccT>, bgrid, kVThreads, D.geo.vsmem, fp, (int32_t)VB_WAIT_FIRST);
         } else {
           e = go(kfn, bgrid, P.cfg.threads, smem, fp);
         }
@@ -632,6 +642,7 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
         e = go(kfn, bgrid, P.cfg.threads, smem, fp);
       }
       mark(1);
+      nvtxRangePop();
       launch++;
       if (e != cudaSuccess) return e;
     }
@@ -645,12 +656,16 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
       const int64_t b = P.spine_pass_begin[p], n = P.spine_pass_begin[p + 1] - b;
       if (n <= 0) continue;
       const unsigned groups = (unsigned)((n + kSpineRows - 1) / kSpineRows);
+      const size_t ssmem = (size_t)P.spine_pass_smem[p] * sizeof(AccT);
+      if (ssmem > 0 && (e = cudaFuncSetAttribute(spine_staged_kernel<AccT>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem)) !=
+                           cudaSuccess)
+        return e;
+      nvtxRangePushA("fht spine sum");
       mark(0);
-      if (P.spine_pass_smem[p] > 0) {
-        const size_t smem = (size_t)P.spine_pass_smem[p] * sizeof(AccT);
+      if (ssmem > 0) {
+        const size_t smem = ssmem;
         auto kst = spine_staged_kernel<AccT>;
-        if ((e = cudaFuncSetAttribute(kst, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-          return e;
         dim3 sgrid(groups, (unsigned)((maxW + kStageTile - 1) / kStageTile));
         e = go(kst, sgrid, kStageThreads, smem, (const SpineRow*)(D.spine_rows + b), n,
                (const SpineTerm*)D.spine_terms, (const SpineGrp*)(D.spine_grps + P.spine_grp_begin[p]),
@@ -661,6 +676,7 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
                (const SpineTerm*)D.spine_terms, (const AccT*)wsa, static_cast<AccT*>(out), wsa, qd);
       }
       mark(1);
+      nvtxRangePop();
       launch++;
       if (e != cudaSuccess) return e;
     }
@@ -670,10 +686,12 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
     const int64_t b = P.pass_begin[p], n = P.pass_begin[p + 1] - b;
     if (n <= 0) continue;
     const unsigned blocks = (unsigned)std::min<int64_t>(n, 1 << 30);
+    nvtxRangePushA("fht upper pass");
     mark(0);
     e = go(upper_kernel<AccT>, dim3(blocks), 256, 0, (const RowJob*)(D.rows + b), n, (const AccT*)wsa, wsa,
            static_cast<AccT*>(out));
     mark(1);
+    nvtxRangePop();
     launch++;
     if (e != cudaSuccess) return e;
   }

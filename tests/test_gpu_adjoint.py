@@ -42,6 +42,23 @@ def test_adjoint_matches_oracle(F, orc, boundary, dtype, tol):
         assert (err <= tol * mass + 1e-300).all(), (h, w, float((err / (mass + 1e-300)).max()))
 
 
+@pytest.mark.parametrize("boundary", ["cyclic", "extended"])
+def test_adjoint_large_default_plan(F, orc, boundary):
+    """A float32 plan large enough for the register-tiled forward launch shape
+    (tile 192, 256 threads): the adjoint, which shares the plan's tile width
+    and CTA size, against the oracle element by element."""
+    h, w = 2100, 2050
+    p = F.Plan(h, w, torch.float32, 15, boundary, with_adjoint=True)
+    assert p.info.tile_cols == 192
+    p.check()
+    g = np.random.default_rng(5).standard_normal(p.out_elems).astype(np.float32).astype(np.float64)
+    got = p.adjoint(torch.from_numpy(g).float().cuda()).cpu().double().numpy()
+    ref = orc.adjoint(g, h, w, 15, _ob(orc, boundary))
+    mass = orc.adjoint(np.abs(g), h, w, 15, _ob(orc, boundary))
+    err = np.abs(got - ref)
+    assert (err <= 1e-5 * mass + 1e-300).all(), float((err / (mass + 1e-300)).max())
+
+
 def test_adjoint_integer_exact(F, orc):
     rng = np.random.default_rng(4)
     for h, w, b in [(31, 17, "cyclic"), (70, 66, "extended")]:
