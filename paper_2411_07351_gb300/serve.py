@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import collections
 import concurrent.futures as cf
+import sys
 import threading
 import time
 from dataclasses import dataclass, field
@@ -328,8 +329,14 @@ class PlainServer:
         self.builder.close()
 
 
-def run_stream(server, requests):
+def run_stream(server, requests, switch_interval: float = 1e-4):
     """Feed `requests` (arrival-sorted Request objects) to `server` in real time.
+
+    The serving loop and the plan builders share the interpreter lock: with
+    Python's default switch interval (5 ms) a builder thread waits up to that
+    long for each of its Python steps while the loop spins, which put tens of
+    milliseconds into the tail of the plan stage.  The loop therefore runs
+    with a short switch interval and yields the lock on every turn.
 
     Returns (finished requests, wall seconds from the first arrival to the last completion)."""
     t0 = time.perf_counter()
@@ -339,12 +346,18 @@ def run_stream(server, requests):
 
     i = 0
     n = len(requests)
-    while i < n or not server.idle():
-        t = now()
-        while i < n and requests[i].arrival <= t:
-            server.arrive(requests[i])
-            i += 1
-        server.step(now)
+    old = sys.getswitchinterval()
+    sys.setswitchinterval(switch_interval)
+    try:
+        while i < n or not server.idle():
+            t = now()
+            while i < n and requests[i].arrival <= t:
+                server.arrive(requests[i])
+                i += 1
+            server.step(now)
+            time.sleep(0)  # let a builder thread take the lock now
+    finally:
+        sys.setswitchinterval(old)
     torch.cuda.synchronize()
     end = max(r.done for r in server.finished)
     return server.finished, end - (requests[0].arrival if requests else 0.0)
