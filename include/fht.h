@@ -54,6 +54,7 @@ extern "C" {
 
 typedef struct fht_plan_s* fht_plan_t;
 typedef struct fht_queue_s* fht_queue_t;
+typedef struct fht_builder_s* fht_builder_t;  /* plan builder pool (fht_builder_create) */
 
 typedef enum {
   FHT_OK = 0,
@@ -315,6 +316,30 @@ fht_status fht_plan_table(fht_plan_t plan, fht_table table, const void** data, i
 
 /* Release a plan and its device tables.  NULL is accepted. */
 fht_status fht_plan_destroy(fht_plan_t plan);
+
+/* ---- plan builder pool ----
+ * fht_plan on native worker threads, for callers that meet new image sizes
+ * at run time (a serving loop) and must not block on, or queue behind, plan
+ * building.  The paper has no counterpart: this is runtime of this library.
+ * fht_builder_create starts `threads` (1..256) workers.  fht_builder_submit
+ * queues one fht_plan call with the given arguments (as for fht_plan;
+ * `tuning` may be NULL, and is copied) under the caller's `tag`, and returns
+ * at once.  fht_builder_poll moves up to `cap` finished builds into tags[],
+ * plans[], status[] and sets *n: a plan whose status is FHT_OK is then owned
+ * by the caller (fht_plan_destroy), a failed build has plans[k] = NULL (its
+ * message is not kept).  fht_builder_pending reports the queued and the
+ * finished-but-unpolled builds.  fht_builder_destroy finishes the queued
+ * builds, destroys the plans nobody polled and stops the workers.  All
+ * functions may be called from any thread; one builder's calls are
+ * serialised internally. */
+fht_status fht_builder_create(fht_builder_t* out, int32_t threads);
+fht_status fht_builder_submit(fht_builder_t b, uint64_t tag, int32_t h, int32_t w, fht_dtype dtype,
+                              uint32_t quadrants, fht_boundary boundary, fht_split split, int device,
+                              const fht_tuning_t* tuning);
+fht_status fht_builder_poll(fht_builder_t b, uint64_t* tags, fht_plan_t* plans, fht_status* status, int32_t cap,
+                            int32_t* n);
+fht_status fht_builder_pending(fht_builder_t b, int32_t* queued, int32_t* finished);
+fht_status fht_builder_destroy(fht_builder_t b);
 
 /* Device status word kept at the start of a workspace: FHT_OK or the first
  * device-side error recorded by a kernel that used it.  Every fht_forward

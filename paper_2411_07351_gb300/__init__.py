@@ -6,4 +6,4 @@ package only marshals arguments.
 """
 from ._capi import (FHT_CYCLIC, FHT_EXTENDED, FHT_F32_F32, FHT_F64_F64, FHT_I32_I32, FHT_Q0, FHT_Q1,  # noqa: F401
                     FHT_Q2, FHT_Q3, FHT_QALL, FHT_SPLIT_S, FHT_SPLIT_T, FHT_U8_I32, FHTError)
-from .fht import HostPipeline, Plan, PlanCache, forward  # noqa: F401
+from .fht import HostPipeline, Plan, PlanBuilderPool, PlanCache, forward  # noqa: F401

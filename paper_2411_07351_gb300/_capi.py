@@ -65,6 +65,13 @@ SIGNATURES = {
     "fht_forward_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "fht_noalloc_status": (ctypes.c_int, [ctypes.c_int, _vp]),
     "fht_plan_destroy": (ctypes.c_int, [_vp]),
+    "fht_builder_create": (ctypes.c_int, [ctypes.POINTER(_vp), _i32]),
+    "fht_builder_submit": (ctypes.c_int, [_vp, ctypes.c_uint64, _i32, _i32, ctypes.c_int, _u32, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, ctypes.POINTER(fht_tuning_t)]),
+    "fht_builder_poll": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_vp),
+                                        ctypes.POINTER(ctypes.c_int), _i32, ctypes.POINTER(_i32)]),
+    "fht_builder_pending": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "fht_builder_destroy": (ctypes.c_int, [_vp]),
     "fht_pattern_errors": (ctypes.c_int, [_i32, _i32, ctypes.c_int, _vp, _vp]),
     "fht_queue_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i32, _i64]),
     "fht_queue_set_wait_limit": (ctypes.c_int, [_vp, _i64]),

@@ -71,6 +71,23 @@ class Plan:
             st = self._lib.fht_plan(*args)
         C.check(st, "fht_plan")
         self._h = handle
+        self._read_info()
+
+    @classmethod
+    def adopt(cls, handle, h: int, w: int, dtype, quads: int, boundary: str, split: str, device: int) -> "Plan":
+        """Wrap a plan handle built elsewhere (``PlanBuilderPool``); the Plan owns it from now on."""
+        self = cls.__new__(cls)
+        self._lib = C.load()
+        self.h, self.w = int(h), int(w)
+        self.in_dtype = dtype
+        self.fht_dtype, self.out_dtype = DTYPES[dtype]
+        self.quads, self.boundary, self.split = int(quads), boundary, split
+        self.device_index = int(device)
+        self._h = handle
+        self._read_info()
+        return self
+
+    def _read_info(self):
         info = C.fht_plan_info_t()
         C.check(self._lib.fht_plan_info(self._h, ctypes.byref(info)), "fht_plan_info")
         self.info = info
@@ -187,6 +204,69 @@ class HostPipeline:
             self._lib.fht_pipe_destroy(self._h)
             self._h = None
             self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PlanBuilderPool:
+    """Plans built on the library's native worker threads (``fht_builder_*``):
+    ``submit`` returns at once with a tag, ``poll`` returns the builds that
+    have finished since, as (tag, Plan) or (tag, FHTError).  No interpreter
+    thread takes part in building, so a serving loop keeps the interpreter
+    lock to itself."""
+
+    def __init__(self, threads: int = 8, poll_cap: int = 1024):
+        self._lib = C.load()
+        b = ctypes.c_void_p()
+        C.check(self._lib.fht_builder_create(ctypes.byref(b), int(threads)), "fht_builder_create")
+        self._b = b
+        self._meta: dict = {}
+        self._next = 1
+        self._cap = poll_cap
+        self._tags = (ctypes.c_uint64 * poll_cap)()
+        self._plans = (ctypes.c_void_p * poll_cap)()
+        self._status = (ctypes.c_int * poll_cap)()
+        self._n = ctypes.c_int32()
+
+    def submit(self, h: int, w: int, dtype, quads: int = C.FHT_QALL, boundary: str = "cyclic", split: str = "T",
+               device: int | None = None, tile_cols: int = 0, threads: int = 0) -> int:
+        if device is None:
+            device = torch.cuda.current_device()
+        tag = self._next
+        self._next += 1
+        tun = C.fht_tuning_t(0, int(tile_cols), int(threads), 0, 0, 0)
+        C.check(self._lib.fht_builder_submit(self._b, tag, int(h), int(w), DTYPES[dtype][0], int(quads),
+                                             BOUNDARY[boundary], SPLIT[split], int(device), ctypes.byref(tun)),
+                "fht_builder_submit")
+        self._meta[tag] = (int(h), int(w), dtype, int(quads), boundary, split, int(device))
+        return tag
+
+    def poll(self) -> list:
+        C.check(self._lib.fht_builder_poll(self._b, self._tags, self._plans, self._status, self._cap,
+                                           ctypes.byref(self._n)), "fht_builder_poll")
+        out = []
+        for k in range(self._n.value):
+            tag = int(self._tags[k])
+            meta = self._meta.pop(tag)
+            if self._status[k] == C.FHT_OK:
+                out.append((tag, Plan.adopt(ctypes.c_void_p(self._plans[k]), *meta)))
+            else:
+                out.append((tag, C.FHTError(int(self._status[k]), f"plan build {meta[:2]}")))
+        return out
+
+    def pending(self) -> tuple[int, int]:
+        q, f = ctypes.c_int32(), ctypes.c_int32()
+        C.check(self._lib.fht_builder_pending(self._b, ctypes.byref(q), ctypes.byref(f)), "fht_builder_pending")
+        return q.value, f.value
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.fht_builder_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         try:

@@ -10,9 +10,9 @@ launch (fht_submit) on the least busy of its streams (each stream holds up to
 fills the GPU by itself and runs the per-image kernels instead.  Batches on
 different streams overlap on the device; a request that arrives while others
 run joins the next batch as soon as memory and a stream are free.  Plans are
-built on a thread pool; requests are admitted in arrival order among those
-whose plans are ready, so a plan still being built holds up only its own
-request.  Latency is arrival -> the host seeing the request's completion.
+built on the library's native builder threads; requests are admitted in
+arrival order among those whose plans are ready, so a plan still being built
+holds up only its own request.  Latency is arrival -> the host seeing the request's completion.
 
 ``PlainServer`` is the comparison: one fht_forward per request, launched on
 one stream as soon as the request's plan is ready.
@@ -20,9 +20,7 @@ one stream as soon as the request's plan is ready.
 from __future__ import annotations
 
 import collections
-import concurrent.futures as cf
 import sys
-import threading
 import time
 from dataclasses import dataclass, field
 
@@ -30,7 +28,7 @@ import torch
 
 from . import _capi as C
 from .batch import BATCH_TILE_COLS, BatchQueue
-from .fht import PlanCache
+from .fht import PlanBuilderPool
 
 
 @dataclass
@@ -52,41 +50,75 @@ class Request:
     plan_future: object = None
 
 
+class _PlanSlot:
+    """The plan of one shape, shared by every request of that shape: ready
+    once the loop has polled it from the builder pool."""
+
+    def __init__(self):
+        self.plan = None
+        self.error = None
+        self.t_submit = time.perf_counter()
+        self.times = [self.t_submit, None]  # build submitted / seen finished (perf_counter)
+
+    def done(self) -> bool:
+        return self.plan is not None or self.error is not None
+
+    def result(self):
+        if self.error is not None:
+            raise self.error
+        return self.plan
+
+
 class PlanBuilder:
-    """Builds plans on a thread pool (the C call releases the GIL), one
-    future per distinct shape, so that the serving thread never waits for a
-    plan it does not need yet."""
+    """Plans built on the library's native worker threads (PlanBuilderPool):
+    the serving thread submits a shape the first time it arrives and picks the
+    finished plans up on every turn (`poll`), so it never waits for a plan it
+    does not need yet and no interpreter thread competes with it while plans
+    are built.  Built plans stay in an LRU cache of `capacity` shapes."""
 
     def __init__(self, device: int, quads: int, boundary: str, split: str, workers: int = 8,
-                 batch_below: int = 0):
+                 batch_below: int = 0, capacity: int = 8192):
         self.device, self.quads, self.boundary, self.split = device, quads, boundary, split
         self.batch_below = batch_below
-        self.cache = PlanCache(capacity=8192)
-        self.pool = cf.ThreadPoolExecutor(max_workers=workers)
-        self.futures: dict = {}
-        self.lock = threading.Lock()
-
-    def _build(self, h, w, dtype):
-        torch.cuda.set_device(self.device)
-        # requests that will be batched get the batch tile width
-        tc = BATCH_TILE_COLS if h * w < self.batch_below else 0
-        return self.cache.get(h, w, dtype, self.quads, self.boundary, self.split, self.device, tile_cols=tc)
+        self.capacity = capacity
+        self.pool = PlanBuilderPool(threads=workers)
+        self.cache: collections.OrderedDict = collections.OrderedDict()  # shape -> ready slot
+        self.pending: dict = {}  # build tag -> (shape, slot)
+        self.by_shape: dict = {}  # shape -> slot still being built
 
     def request(self, req: "Request"):
-        k = (req.image.shape[0], req.image.shape[1], req.image.dtype)
-        with self.lock:
-            f = self.futures.get(k)
-            if f is None:
-                f = self.pool.submit(self._build, *k)
-                self.futures[k] = f
-                if len(self.futures) > 16384:  # forget old futures; plans stay in the LRU cache
-                    for old in list(self.futures)[:4096]:
-                        if self.futures[old].done():
-                            del self.futures[old]
-        req.plan_future = f
+        h, w = int(req.image.shape[0]), int(req.image.shape[1])
+        k = (h, w, req.image.dtype)
+        slot = self.cache.get(k)
+        if slot is not None:
+            self.cache.move_to_end(k)
+        else:
+            slot = self.by_shape.get(k)
+            if slot is None:
+                slot = _PlanSlot()
+                # requests that will be batched get the batch tile width
+                tc = BATCH_TILE_COLS if h * w < self.batch_below else 0
+                tag = self.pool.submit(h, w, req.image.dtype, self.quads, self.boundary, self.split, self.device,
+                                       tile_cols=tc)
+                self.pending[tag] = (k, slot)
+                self.by_shape[k] = slot
+        req.plan_future = slot
+
+    def poll(self):
+        for tag, res in self.pool.poll():
+            k, slot = self.pending.pop(tag)
+            del self.by_shape[k]
+            slot.times[1] = time.perf_counter()
+            if isinstance(res, Exception):
+                slot.error = res
+                continue
+            slot.plan = res
+            self.cache[k] = slot
+            while len(self.cache) > self.capacity:
+                self.cache.popitem(last=False)  # dropped: requests still holding the plan keep it alive
 
     def close(self):
-        self.pool.shutdown(wait=True)
+        self.pool.close()
 
 
 def _ready_in_order(waiting, window: int = 256, now_fn=None):
@@ -254,6 +286,7 @@ class Server:
             self.batches += 1
 
     def step(self, now_fn):
+        self.builder.poll()
         self._retire(now_fn)
         self._admit(now_fn)
         self._launch(now_fn)
@@ -312,6 +345,7 @@ class PlainServer:
             self.batches += 1
 
     def step(self, now_fn):
+        self.builder.poll()
         while self.running and self.running[0][0].query():
             ev, r = self.running.popleft()
             r.done = now_fn()
@@ -329,17 +363,17 @@ class PlainServer:
         self.builder.close()
 
 
-def run_stream(server, requests, switch_interval: float = 1e-4):
+def run_stream(server, requests, switch_interval: float | None = None):
     """Feed `requests` (arrival-sorted Request objects) to `server` in real time.
 
-    The serving loop and the plan builders share the interpreter lock: with
-    Python's default switch interval (5 ms) a builder thread waits up to that
-    long for each of its Python steps while the loop spins, which put tens of
-    milliseconds into the tail of the plan stage.  The loop therefore runs
-    with a short switch interval and yields the lock on every turn.
+    The serving loop and the plan builders share the interpreter lock; the
+    loop yields it on every turn, and `switch_interval` (seconds) optionally
+    sets the interpreter's switch interval for the run.  `server.t0` is the
+    perf_counter time of arrival 0.
 
     Returns (finished requests, wall seconds from the first arrival to the last completion)."""
     t0 = time.perf_counter()
+    server.t0 = t0
 
     def now():
         return time.perf_counter() - t0
@@ -347,7 +381,8 @@ def run_stream(server, requests, switch_interval: float = 1e-4):
     i = 0
     n = len(requests)
     old = sys.getswitchinterval()
-    sys.setswitchinterval(switch_interval)
+    if switch_interval is not None:
+        sys.setswitchinterval(switch_interval)
     try:
         while i < n or not server.idle():
             t = now()

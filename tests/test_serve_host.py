@@ -137,3 +137,34 @@ def test_batched_workspace_stays_counted_until_the_launch_ends():
     s._retire(now)
     assert s.used == held() == 0 and not s.running and s.inflight == [0]
     assert [r.rid for r in s.finished] == [0, 1, 2]
+
+
+def test_native_builder_pool_host_plans():
+    # The native builder pool (fht_builder_*) on host-only plans: every
+    # submitted shape comes back once, equal to a plan built directly; a bad
+    # size comes back as an error; unpolled plans are released by close().
+    import time as _t
+
+    import torch
+
+    import paper_2411_07351_gb300 as F
+
+    pool = F.PlanBuilderPool(threads=3)
+    shapes = [(5, 7), (64, 65), (257, 100), (1000, 33), (4095, 17)]
+    tags = {pool.submit(h, w, torch.uint8, 15, "cyclic", "T", device=-1): (h, w) for h, w in shapes}
+    bad = pool.submit(0, 5, torch.uint8, 15, "cyclic", "T", device=-1)
+    got, deadline = {}, _t.time() + 60
+    while len(got) < len(tags) + 1 and _t.time() < deadline:
+        for tag, res in pool.poll():
+            got[tag] = res
+        _t.sleep(0.01)
+    assert sorted(got) == sorted(list(tags) + [bad])
+    assert isinstance(got[bad], F.FHTError)
+    for tag, (h, w) in tags.items():
+        p, ref = got[tag], F.Plan(h, w, torch.uint8, 15, "cyclic", device=-1)
+        assert (p.h, p.w) == (h, w)
+        assert p.out_elems == ref.out_elems and p.workspace_bytes == ref.workspace_bytes
+        assert p.info.model_bytes == ref.info.model_bytes and p.info.adds == ref.info.adds
+    assert pool.pending() == (0, 0)
+    pool.submit(300, 300, torch.uint8, 15, "extended", "T", device=-1)
+    pool.close()  # finishes the queued build and destroys the unclaimed plan
