@@ -88,7 +88,24 @@ cudaError_t upload_tables(fht_plan_s* p) {
   void* buf = nullptr;
   cudaError_t e = cudaMalloc(&buf, std::max<size_t>(tp.host.size(), 256));
   if (e != cudaSuccess) return e;
-  e = cudaMemcpy(buf, tp.host.data(), tp.host.size(), cudaMemcpyHostToDevice);
+  // The copy runs on a non-blocking stream of this thread (one per device),
+  // so that it waits for nothing but itself: a plan built while the device
+  // is busy (a serving loop's builder threads) does not queue behind the
+  // work on the legacy default stream.
+  static thread_local cudaStream_t upload_stream[64] = {};
+  const int dev = p->dev.device;
+  cudaStream_t us = nullptr;
+  if (dev >= 0 && dev < 64) {
+    if (!upload_stream[dev] && cudaStreamCreateWithFlags(&upload_stream[dev], cudaStreamNonBlocking) != cudaSuccess)
+      upload_stream[dev] = nullptr;
+    us = upload_stream[dev];
+  }
+  if (us) {
+    e = cudaMemcpyAsync(buf, tp.host.data(), tp.host.size(), cudaMemcpyHostToDevice, us);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(us);
+  } else {
+    e = cudaMemcpy(buf, tp.host.data(), tp.host.size(), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     cudaFree(buf);
     return e;
