@@ -20,6 +20,7 @@ Multi-GPU runs are independent replicas (weak scaling, no data exchange).
 from __future__ import annotations
 
 import argparse
+import gc
 import ctypes
 import hashlib
 import json
@@ -747,7 +748,15 @@ def measure_c5(args) -> dict:
         srv.finished, srv.batches = [], 0
         return srv
 
+    def fresh():
+        # each measured run starts from the same device state: the previous
+        # run's requests, plans and cached blocks released first
+        gc.collect()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
     for name, mk in makers:
+        fresh()
         reqs = make_requests()
         srv = warmed(mk)
         done, wall = run_stream(srv, reqs)
@@ -757,10 +766,12 @@ def measure_c5(args) -> dict:
                      "p99_ms": _pct(lat, 0.99), "max_ms": max(lat), "launch_groups": srv.batches,
                      "stages": _breakdown(done)}
         srv.close()
+        del done, reqs, srv
     # saturation: the same request mix arriving 10x faster, so that throughput,
     # not the offered load, decides Mpix/s
     nonlocal_rate = rate
     for name, mk in makers:
+        fresh()
         reqs = make_requests()[: int(nonlocal_rate * min(dur, 2.0))]
         for r in reqs:
             r.arrival /= 10.0

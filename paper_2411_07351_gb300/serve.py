@@ -364,7 +364,7 @@ class PlainServer:
         self.builder.close()
 
 
-def run_stream(server, requests, switch_interval: float | None = None):
+def run_stream(server, requests, switch_interval: float | None = None, disable_gc: bool = True):
     """Feed `requests` (arrival-sorted Request objects) to `server` in real time.
 
     The serving loop and the plan builders share the interpreter lock; the
@@ -388,7 +388,8 @@ def run_stream(server, requests, switch_interval: float | None = None):
     # full collection over tens of thousands of live requests stalls the loop
     # for tens of milliseconds (requests hold no reference cycles)
     gc_was_on = gc.isenabled()
-    gc.disable()
+    if disable_gc:
+        gc.disable()
     try:
         while i < n or not server.idle():
             t = now()
