@@ -271,7 +271,7 @@ void queue_free(fht_queue_s* q) {
 template <typename InT, typename AccT>
 cudaError_t launch_batch(fht_queue_s* q, int32_t nunits, size_t smem, cudaStream_t st) {
   auto kfn = fht::batch_kernel<InT, AccT>;
-  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = fht::raise_smem_limit(kfn, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0, sms = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, fht::kBatchThreads, smem)) != cudaSuccess)

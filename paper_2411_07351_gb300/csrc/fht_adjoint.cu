@@ -257,7 +257,7 @@ static cudaError_t launch_adjoint_t(const DevicePlan& D, const void* gout, void*
   fp.PADL = padl;
   fp.Fm = P.max_fused_m;
   auto kfn = adj_fused_kernel<AccT>;
-  if ((e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+  if ((e = raise_smem_limit(kfn, smem)) != cudaSuccess)
     return e;
   dim3 grid((unsigned)P.fused.size(), P.max_antiles);
   kfn<<<grid, P.cfg.threads, smem, st>>>(fp);

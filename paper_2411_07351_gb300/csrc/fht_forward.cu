@@ -13,6 +13,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "../../include/fht.h"
 #include "fht_desc.h"
 #include "fht_block.cuh"
@@ -475,6 +479,20 @@ __global__ void __launch_bounds__(kStageThreads) spine_staged_kernel(const Spine
 // ------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> limit;  // (kernel, device) -> limit set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[{kernel, dev}];
+  if (cur >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
 void fused_geometry(const HostPlan& P, FusedGeometry& g) {
   // generic path: a window of tw + m - 1 columns plus room for the largest shifted read
   g.Fm = std::max(P.max_generic_m, 1);
@@ -581,7 +599,7 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
   fp.RA = D.geo.RA;
   const size_t smem = D.geo.smem;
   auto kfn = fused_kernel<InT, AccT>;
-  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(kfn, smem);
   if (e != cudaSuccess) return e;
   if (!P.vblock) {
     dim3 grid((unsigned)P.fused.size(), P.max_ntiles);  // tiles <= 131070 / 32 fit in grid.y
@@ -604,8 +622,7 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
       if (e != cudaSuccess) return e;
     }
     auto kbl = block_kernel<InT, AccT>;
-    if ((e = cudaFuncSetAttribute(kbl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D.geo.vsmem)) !=
-        cudaSuccess)
+    if ((e = raise_smem_limit(kbl, D.geo.vsmem)) != cudaSuccess)
       return e;
     FusedParams bp = fp;
     bp.items = D.fused + P.n_generic;
@@ -626,8 +643,7 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
       dim3 bgrid((unsigned)P.band_items.size(), P.max_band_ntiles);
       if constexpr (sizeof(AccT) == 4) {
         if (P.vblock &&
-            (e = cudaFuncSetAttribute(block_kernel<InT, AccT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)D.geo.vsmem)) != cudaSuccess)
+            (e = raise_smem_limit(block_kernel<InT, AccT>, D.geo.vsmem)) != cudaSuccess)
           return e;
       }
       nvtxRangePushA("fht band pass");
@@ -657,9 +673,7 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
       if (n <= 0) continue;
       const unsigned groups = (unsigned)((n + kSpineRows - 1) / kSpineRows);
       const size_t ssmem = (size_t)P.spine_pass_smem[p] * sizeof(AccT);
-      if (ssmem > 0 && (e = cudaFuncSetAttribute(spine_staged_kernel<AccT>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem)) !=
-                           cudaSuccess)
+      if (ssmem > 0 && (e = raise_smem_limit(spine_staged_kernel<AccT>, ssmem)) != cudaSuccess)
         return e;
       nvtxRangePushA("fht spine sum");
       mark(0);

@@ -37,6 +37,17 @@ struct DevicePlan {
 
 void fused_geometry(const HostPlan& P, FusedGeometry& g);
 
+// Raises the dynamic shared-memory limit of `kernel` on the current device to
+// at least `bytes`, calling the runtime only when the limit must grow (it is
+// never lowered; occupancy follows the shared memory a launch requests, not
+// the limit).  Setting the attribute on every launch would take the driver's
+// lock on every call, which threads building plans at the same time wait on.
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes);
+template <typename K>
+cudaError_t raise_smem_limit(K* kernel, size_t bytes) {
+  return raise_smem_limit(reinterpret_cast<const void*>(kernel), bytes);
+}
+
 // Enqueues the forward transform.  When `events` is non-null, events[2k] and
 // events[2k + 1] are recorded just before and after the k-th kernel launch.
 cudaError_t launch_forward(const DevicePlan& D, const void* in, int64_t in_pitch, void* out, void* ws,
