@@ -541,8 +541,27 @@ def measure_c1(args) -> dict:
     return line
 
 
+def _extra_dist(fn, args):
+    """Run an extra workload on this rank's GPU (torchrun: one process per GPU,
+    NCCL only for the timing reductions) and print rank 0's line."""
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    line = fn(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def run_c3(args):
-    print(json.dumps(measure_c3(args)), flush=True)
+    _extra_dist(measure_c3, args)
 
 
 def measure_c3(args) -> dict:
@@ -554,10 +573,13 @@ def measure_c3(args) -> dict:
     from paper_2411_07351_gb300 import inputs
     from paper_2411_07351_gb300.batch import BatchQueue
 
-    torch.cuda.set_device(0)
+    from paper_2411_07351_gb300 import parallel
+
+    world, _ = parallel.world_rank()
     imgs = inputs.c3_batch()
+    mpix = sum(im.size for im in imgs) / 1e6  # the whole batch, over all ranks
+    imgs = [imgs[i] for i in parallel.my_shard([im.shape for im in imgs])]  # all of them at world 1
     xs = [torch.from_numpy(im).cuda() for im in imgs]
-    mpix = sum(im.size for im in imgs) / 1e6
     q = BatchQueue(max_jobs=len(xs), max_units=1 << 23)
     plans = [q.plan_for(x, F.FHT_QALL, "cyclic", "T") for x in xs]
     outs = [p.new_output() for p in plans]
@@ -599,7 +621,12 @@ def measure_c3(args) -> dict:
             q.submit(xs, F.FHT_QALL, "cyclic", "T", outs=outs, workspaces=wss, stream=s, plans=plans)
     torch.cuda.synchronize()
     t_graph = timed(g.replay, reps)
-    line = {"metric": METRIC, "value": mpix / (t_batch * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": reps,
+    # the batch's time is its slowest rank's (no exchange on the data path)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t_plain, t_batch, t_graph = (parallel.max_over_ranks(t, dev) for t in (t_plain, t_batch, t_graph))
+    model = int(parallel.sum_over_ranks(float(model), dev))
+    line = {"metric": METRIC, "value": mpix / (t_batch * 1e-3), "unit": UNIT, "n_gpus": world, "steps": reps,
+            "scaling": "strong",
             "higher_is_better": True, "dtype": "u8->i32", "data": "synthetic",
             "config": {"workload": "c3: 4096 binary edge maps, h, w ~ U{17..511} seed 3, 4 quadrants, cyclic",
                        "mpix": mpix, "l2": "256 MiB buffer written before every timed run"},
@@ -607,7 +634,8 @@ def measure_c3(args) -> dict:
             "plain_value": mpix / (t_plain * 1e-3), "graph_value": mpix / (t_graph * 1e-3),
             "speedup_vs_plain": t_plain / t_batch, "model_bytes": model,
             "model_gbs_batched": model / (t_batch * 1e-3) / 1e9,
-            "gpu_launches": {"plain": sum(_launches(p) for p in plans), "batched": 1}}
+            "gpu_launches": {"plain": sum(_launches(p) for p in plans), "batched": 1},
+            "sharding": "size-balanced shard of the batch per rank, slowest rank's time" if world > 1 else None}
     q.close()
     return line
 
@@ -620,7 +648,6 @@ def run_c4(args):
     from paper_2411_07351_gb300 import inputs
     from paper_2411_07351_gb300.autograd import fht
 
-    torch.cuda.set_device(0)
     imgs = inputs.c4_batch()
     ys = [torch.from_numpy(y).cuda() for y in inputs.c4_targets(imgs)]
     xs = [torch.from_numpy(im).cuda().requires_grad_(True) for im in imgs]
@@ -692,22 +719,44 @@ def run_c4(args):
 
 
 def run_c5(args):
-    print(json.dumps(measure_c5(args)), flush=True)
+    _extra_dist(measure_c5, args)
 
 
-def _breakdown(done) -> dict:
-    """p50 / p99 (ms) of each stage of a served request: arrival -> plan built
-    (seen by the serving loop), -> admitted under the memory budget, ->
-    launch enqueued, -> completion seen by the host."""
-    stages = {"plan": [], "admit": [], "launch": [], "device": []}
+def _records(done) -> list:
+    """Per served request: (latency, plan, admit, launch, device) in ms and its
+    pixels.  Stages: arrival -> plan built (seen by the serving loop), ->
+    admitted under the memory budget, -> launch enqueued, -> completion seen
+    by the host."""
+    out = []
     for r in done:
-        if None in (r.t_ready, r.t_admit, r.t_launch):
-            continue
-        stages["plan"].append((r.t_ready - r.arrival) * 1e3)
-        stages["admit"].append((r.t_admit - r.t_ready) * 1e3)
-        stages["launch"].append((r.t_launch - r.t_admit) * 1e3)
-        stages["device"].append((r.done - r.t_launch) * 1e3)
-    return {k: {"p50_ms": _pct(v, 0.5), "p99_ms": _pct(v, 0.99)} for k, v in stages.items()}
+        st = None
+        if None not in (r.t_ready, r.t_admit, r.t_launch):
+            st = ((r.t_ready - r.arrival) * 1e3, (r.t_admit - r.t_ready) * 1e3, (r.t_launch - r.t_admit) * 1e3,
+                  (r.done - r.t_launch) * 1e3)
+        out.append(((r.done - r.arrival) * 1e3, st, int(r.image.numel())))
+    return out
+
+
+def _gathered(records: list, wall: float) -> tuple[list, float]:
+    """Every rank's records and the slowest rank's wall time (one rank: as given)."""
+    from paper_2411_07351_gb300 import parallel
+
+    world, rank = parallel.world_rank()
+    if world == 1:
+        return records, wall
+    merged = parallel.gather_by_index({rank: records})
+    return [x for k in sorted(merged) for x in merged[k]], parallel.max_over_ranks(wall)
+
+
+def _summary(records: list, wall: float) -> dict:
+    lat = [x[0] for x in records]
+    mp = sum(x[2] for x in records) / 1e6
+    stages = {}
+    for k, name in enumerate(("plan", "admit", "launch", "device")):
+        v = [x[1][k] for x in records if x[1] is not None]
+        stages[name] = {"p50_ms": _pct(v, 0.5), "p99_ms": _pct(v, 0.99)}
+    return {"requests": len(records), "wall_s": wall, "mpix_per_s": mp / wall, "p50_ms": _pct(lat, 0.5),
+            "p99_ms": _pct(lat, 0.99), "max_ms": max(lat), "stages": stages}
 
 
 def measure_c5(args) -> dict:
@@ -716,9 +765,10 @@ def measure_c5(args) -> dict:
     vs plain per-request launches on the same arrival sequence."""
     import torch
 
+    from paper_2411_07351_gb300 import parallel
     from paper_2411_07351_gb300.serve import PlainServer, Request, Server, run_stream
 
-    torch.cuda.set_device(0)
+    world, rank = parallel.world_rank()
     rate, dur, lo, hi = 2000.0, args.serve_seconds, 64, 4096
     g = np.random.Generator(np.random.PCG64(6))
     # one seeded 4096 x 4096 noise field; each request is a window of it (10 % non-zero, values U{1..255})
@@ -736,6 +786,14 @@ def measure_c5(args) -> dict:
             w = int(round(math.exp(gg.uniform(math.log(lo), math.log(hi)))))
             y0, x0 = int(gg.integers(0, hi - h + 1)), int(gg.integers(0, hi - w + 1))
             out.append(Request(len(out), t, dfield[y0:y0 + h, x0:x0 + w]))
+
+    def my_requests(reqs):
+        # several GPUs: each arrival is routed to one rank (least work so far;
+        # every rank routes the same stream identically, nothing is exchanged)
+        if world == 1:
+            return reqs
+        to = parallel.route([tuple(r.image.shape) for r in reqs], world)
+        return [r for r, k in zip(reqs, to) if k == rank]
 
     res = {}
     makers = (("served", lambda: Server(budget_bytes=16 << 30, streams=4, keep_outputs=False)),
@@ -757,14 +815,11 @@ def measure_c5(args) -> dict:
 
     for name, mk in makers:
         fresh()
-        reqs = make_requests()
+        reqs = my_requests(make_requests())
         srv = warmed(mk)
         done, wall = run_stream(srv, reqs)
-        lat = [(r.done - r.arrival) * 1e3 for r in done]
-        mp = sum(r.image.numel() for r in done) / 1e6
-        res[name] = {"requests": len(done), "wall_s": wall, "mpix_per_s": mp / wall, "p50_ms": _pct(lat, 0.5),
-                     "p99_ms": _pct(lat, 0.99), "max_ms": max(lat), "launch_groups": srv.batches,
-                     "stages": _breakdown(done)}
+        res[name] = _summary(*_gathered(_records(done), wall))
+        res[name]["launch_groups"] = int(parallel.sum_over_ranks(float(srv.batches)))
         srv.close()
         del done, reqs, srv
     # saturation: the same request mix arriving 10x faster, so that throughput,
@@ -772,21 +827,22 @@ def measure_c5(args) -> dict:
     nonlocal_rate = rate
     for name, mk in makers:
         fresh()
-        reqs = make_requests()[: int(nonlocal_rate * min(dur, 2.0))]
+        reqs = my_requests(make_requests()[: int(nonlocal_rate * min(dur, 2.0))])
         for r in reqs:
             r.arrival /= 10.0
         srv = warmed(mk)
         done, wall = run_stream(srv, reqs)
-        lat = [(r.done - r.arrival) * 1e3 for r in done]
-        mp = sum(r.image.numel() for r in done) / 1e6
-        res[name]["saturated"] = {"requests": len(done), "offered_req_per_s": rate * 10, "wall_s": wall,
-                                  "mpix_per_s": mp / wall, "p50_ms": _pct(lat, 0.5), "p99_ms": _pct(lat, 0.99)}
+        sat = _summary(*_gathered(_records(done), wall))
+        res[name]["saturated"] = {k: sat[k] for k in ("requests", "wall_s", "mpix_per_s", "p50_ms", "p99_ms")}
+        res[name]["saturated"]["offered_req_per_s"] = rate * 10
         srv.close()
-    line = {"metric": METRIC + " served", "value": res["served"]["mpix_per_s"], "unit": UNIT, "n_gpus": 1,
+    line = {"metric": METRIC + " served", "value": res["served"]["mpix_per_s"], "unit": UNIT, "n_gpus": world,
+            "scaling": "strong",
             "higher_is_better": True, "dtype": "u8->i32", "data": "synthetic",
             "config": {"workload": f"c5: Poisson {rate:.0f} req/s for {dur} s, h, w log-uniform [64, 4096], "
                                    "10% non-zero uint8 windows of a seeded field, 4 quadrants cyclic, 16 GB budget",
-                       "warm_up": "0.5 s of requests from another seed through each server before its measured run"},
+                       "warm_up": "0.5 s of requests from another seed through each server before its measured run",
+                       "routing": "each arrival to the rank with the least work so far" if world > 1 else None},
             "served": res["served"], "plain": res["plain"]}
     return line
 

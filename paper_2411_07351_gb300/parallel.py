@@ -39,6 +39,51 @@ def shard(sizes: list[tuple[int, int]], world: int, quads: int = 15) -> list[lis
     return out
 
 
+def world_rank() -> tuple[int, int]:
+    """(world size, rank) of the initialised process group, else (1, 0)."""
+    if dist.is_available() and dist.is_initialized():
+        return dist.get_world_size(), dist.get_rank()
+    return 1, 0
+
+
+def my_shard(sizes: list[tuple[int, int]], quads: int = 15) -> list[int]:
+    """This rank's images (indices) of a batch: every rank computes the same
+    assignment from the sizes alone, so no exchange is needed."""
+    world, rank = world_rank()
+    return shard(sizes, world, quads)[rank]
+
+
+def route(sizes: list[tuple[int, int]], world: int, quads: int = 15) -> list[int]:
+    """Rank of every request of a stream, in arrival order: each goes to the
+    rank with the least work routed so far (ties to the lowest rank).  The
+    rule depends only on the requests seen so far, so every rank routes the
+    same stream identically without exchanging anything."""
+    load = [0.0] * world
+    out = []
+    for h, w in sizes:
+        r = min(range(world), key=lambda k: (load[k], k))
+        out.append(r)
+        load[r] += cost(h, w, quads)
+    return out
+
+
+def gather_by_index(local: dict) -> dict:
+    """Merge {index: object} dictionaries from every rank (host objects; for
+    checking or collecting results, not a step of the transform)."""
+    world, _ = world_rank()
+    if world == 1:
+        return dict(local)
+    parts = [None] * world
+    dist.all_gather_object(parts, local)
+    merged: dict = {}
+    for p in parts:
+        dup = merged.keys() & p.keys()
+        if dup:
+            raise ValueError(f"indices on more than one rank: {sorted(dup)[:5]}")
+        merged.update(p)
+    return merged
+
+
 def max_over_ranks(value: float, device: torch.device | None = None) -> float:
     """The largest `value` over all ranks (the job's time is its slowest rank's)."""
     if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
