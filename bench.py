@@ -492,7 +492,6 @@ def measure_c1(args) -> dict:
     import paper_2411_07351_gb300 as F
     from paper_2411_07351_gb300 import inputs
 
-    torch.cuda.set_device(0)
     img = inputs.c1_image()
     x = torch.from_numpy(img).cuda()
     plan = F.Plan(257, 257, torch.uint8, F.FHT_Q0, "cyclic", tuning="auto")
