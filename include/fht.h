@@ -94,7 +94,9 @@ typedef struct {
   int32_t spine_chunk; /* Split_T roots taller than 64 rows: spine nodes summed per spine launch (default 3);
                           the lower chunks' top nodes are summed first and become single parts of the
                           chunk above.  A value >= the spine length gives one spine launch. */
-  int32_t reserved[2];
+  int32_t generic_cols;/* column tile of the subtrees under 64 rows that take the generic shared-memory
+                          path (multiple of 32; default: half of tile_cols rounded down to 32, at least 32) */
+  int32_t reserved;
 } fht_tuning_t;
 
 typedef struct {

@@ -26,7 +26,7 @@ FHT_TABLE_QUADS, FHT_TABLE_FUSED, FHT_TABLE_OPS, FHT_TABLE_ROWS, FHT_TABLE_PASS_
 class fht_tuning_t(ctypes.Structure):
     _fields_ = [("fused_rows", ctypes.c_int32), ("tile_cols", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("with_adjoint", ctypes.c_int32), ("rounding", ctypes.c_int32),
-                ("spine_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("spine_chunk", ctypes.c_int32), ("generic_cols", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class fht_plan_info_t(ctypes.Structure):

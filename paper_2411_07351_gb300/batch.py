@@ -12,10 +12,13 @@ from . import _capi as C
 from .fht import Plan, PlanCache
 
 
-# Column tile of plans made for batched launches: 64-column tiles keep the
-# persistent kernel at 3 CTAs per SM (<= 64 KB of shared memory per CTA) and
-# fit the small images batches are for.
-BATCH_TILE_COLS = 64
+# Launch shape of plans made for batched launches: the register-tiled block
+# path (192-column tiles, 256 threads: the persistent kernel's CTA size) for
+# the 64-row blocks and bands, and 32-column tiles for the generic subtrees,
+# so that every unit fits one 66.5 KB shared buffer (3 CTAs per SM).
+BATCH_TILE_COLS = 192
+BATCH_THREADS = 256
+BATCH_GENERIC_COLS = 32
 
 # numpy layout of fht_job (include/fht.h): 64 bytes, naturally aligned fields
 _JOB_DTYPE = np.dtype([("plan", np.uint64), ("d_in", np.uint64), ("in_pitch", np.int64), ("d_out", np.uint64),
@@ -42,7 +45,7 @@ class BatchQueue:
 
     def plan_for(self, x: torch.Tensor, quads: int, boundary: str, split: str) -> Plan:
         return self.plans.get(x.shape[0], x.shape[1], x.dtype, quads, boundary, split, self.device_index,
-                              tile_cols=BATCH_TILE_COLS)
+                              tile_cols=BATCH_TILE_COLS, threads=BATCH_THREADS, generic_cols=BATCH_GENERIC_COLS)
 
     def submit(self, images, quads: int = C.FHT_QALL, boundary: str = "cyclic", split: str = "T",
                outs=None, workspaces=None, stream=None, flags=None, tags=None, plans=None):

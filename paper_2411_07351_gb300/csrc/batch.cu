@@ -21,6 +21,7 @@
 
 #include "../../include/fht.h"
 #include "fht_desc.h"
+#include "fht_block.cuh"
 #include "fht_device.cuh"
 #include "fht_launch.hpp"
 #include "fht_nvtx.hpp"
@@ -64,6 +65,13 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
   int32_t v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+// One register-tiled block or band tile of a job, out of line: its own
+// register allocation instead of one shared with every other unit kind.
+template <typename InT, typename AccT>
+__device__ __noinline__ void batch_vblock(const FusedParams& fp, const FusedItem& it, int32_t tile, AccT* sm) {
+  v_block<true, InT, AccT>(fp, it, fp.quad[it.q], tile, sm);
 }
 
 template <typename AccT>
@@ -171,7 +179,9 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchJob*
           const QuadDesc& Q = jb.fp.quad[it.q];
           for (int32_t tile = U.tile; tile < U.tile + U.ntiles && tile < it.ntiles; tile++) {
             if (tile > U.tile) __syncthreads();  // the previous tile's shared reads are done
-            if (it.kind != FUSED_GENERIC) {
+            if (it.kind != FUSED_GENERIC && jb.fp.vblock) {
+              if constexpr (sizeof(AccT) == 4) batch_vblock<InT, AccT>(jb.fp, it, tile, sm);
+            } else if (it.kind != FUSED_GENERIC) {
               fused_block_any<true, InT, AccT>(jb.fp, it, Q, tile, sm, sm + (size_t)64 * jb.fp.RS);
             } else {
               fused_generic<InT, AccT>(jb.fp, it, Q, tile, sm, sm + (size_t)jb.fp.Fm * jb.fp.RP);
@@ -379,11 +389,14 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
     B.fp.Fm = D->geo.Fm;
     B.fp.RS = D->geo.RS;
     B.fp.RA = D->geo.RA;
+    B.fp.vblock = P.vblock ? 1 : 0;
     B.band_items = D->band_items;
     B.spine_rows = D->spine_rows;
     B.spine_terms = D->spine_terms;
     B.rows = D->rows;
-    smem = std::max(smem, D->geo.smem);
+    // the register-tiled path stages into one 64 x kVPitch buffer; the generic
+    // subtrees of such a plan use their own (smaller) layout
+    smem = std::max(smem, P.vblock ? std::max(D->geo.vsmem, D->geo.gsmem) : D->geo.smem);
   }
   // pass 2: units, phase by phase across all jobs
   std::vector<int32_t> done_before(njobs, 0);

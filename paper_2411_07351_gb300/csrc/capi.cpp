@@ -163,6 +163,7 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
     cfg.with_adjoint = tuning->with_adjoint != 0;
     cfg.rounding = tuning->rounding;
     if (tuning->spine_chunk) cfg.spine_chunk = tuning->spine_chunk;
+    cfg.generic_cols = tuning->generic_cols;
     if (cfg.spine_chunk < 1) return fail(FHT_ERR_INVALID, "fht_plan: spine_chunk must be >= 1");
     if (cfg.threads > 512) return fail(FHT_ERR_INVALID, "fht_plan: threads must be <= 512");
   }

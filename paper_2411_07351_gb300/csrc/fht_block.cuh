@@ -194,7 +194,9 @@ __device__ __forceinline__ void v_stage(const InT* __restrict__ in, int64_t pitc
 // b, pre-shifted by K b (window column z reads block column x0 + K b + c_src
 // + z), so that each group of B rows is then a B-row Brady-Yong transform.
 // Warp w stages rows [8 w, 8 w + 8).
-template <typename AccT>
+// kC: the block rows were written earlier in the same launch by other CTAs
+// (persistent batched kernel): read them at L2, past L1.
+template <bool kC, typename AccT>
 __device__ __forceinline__ void v_stage_band(const AccT* __restrict__ ws, const FusedItem& it, const QuadDesc& Q,
                                              int32_t x0, AccT* S) {
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -209,7 +211,7 @@ __device__ __forceinline__ void v_stage_band(const AccT* __restrict__ ws, const 
     const int32_t base = x0 + K * b + it.c_src;  // >= 0 in the cyclic case
     if (base >= 0 && base + kVWin <= lim) {
 #pragma unroll
-      for (int c = 0; c < kVWin / 32; c++) v[rr][c] = __ldg(row + base + 32 * c + lane);
+      for (int c = 0; c < kVWin / 32; c++) v[rr][c] = ld_ws<kC>(row + base + 32 * c + lane);
     } else {
 #pragma unroll
       for (int c = 0; c < kVWin / 32; c++) {
@@ -220,7 +222,7 @@ __device__ __forceinline__ void v_stage_band(const AccT* __restrict__ ws, const 
         } else if (z >= Q.W) {
           z = z < 2 * Q.W ? z - Q.W : z % Q.W;
         }
-        v[rr][c] = ok ? __ldg(row + z) : AccT(0);
+        v[rr][c] = ok ? ld_ws<kC>(row + z) : AccT(0);
       }
     }
   }
@@ -386,12 +388,12 @@ __device__ __forceinline__ bool v_merge(const FusedParams& p, const FusedItem& i
 
 // One item x one tile, staged by the merging warps themselves (each stages
 // the rows its first pass merges).
-template <typename InT, typename AccT>
+template <bool kC, typename InT, typename AccT>
 __device__ __forceinline__ void v_block(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile,
                                         AccT* S) {
   const int32_t x0 = tile * kVTile - it.c;
   if (it.kind == FUSED_BAND) {
-    v_stage_band<AccT>(static_cast<const AccT*>(p.ws), it, Q, x0, S);
+    v_stage_band<kC, AccT>(static_cast<const AccT*>(p.ws), it, Q, x0, S);
   } else {
     v_stage<InT, AccT>(static_cast<const InT*>(p.in), p.in_pitch, Q, it.a, x0, S);
   }

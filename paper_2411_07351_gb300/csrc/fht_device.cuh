@@ -33,6 +33,7 @@ struct FusedParams {
   int32_t Fm;  // generic path: rows per shared buffer
   int32_t RS;  // fast path: pitch of the staged input / level-4 rows
   int32_t RA;  // fast path: pitch of the level-2 rows
+  int32_t vblock;  // the plan's 64-row blocks and bands take the register-tiled path (batched launch)
 };
 
 template <typename InT, typename AccT>

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kVThreads, 3) block_kernel(FusedParams p, int3
   const int32_t tile = blockIdx.y;
   if (tile < it.ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    v_block<InT, AccT>(p, it, p.quad[it.q], tile, reinterpret_cast<AccT*>(smem_raw));
+    v_block<false, InT, AccT>(p, it, p.quad[it.q], tile, reinterpret_cast<AccT*>(smem_raw));
   }
   if (!(flags & VB_WAIT_FIRST)) pdl_wait();
 }
@@ -597,6 +597,7 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
   fp.Fm = D.geo.Fm;
   fp.RS = D.geo.RS;
   fp.RA = D.geo.RA;
+  fp.vblock = 0;  // the plain launches pick their kernels on the host
   const size_t smem = D.geo.smem;
   auto kfn = fused_kernel<InT, AccT>;
   cudaError_t e = raise_smem_limit(kfn, smem);

@@ -295,6 +295,8 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
   if (cfg.F < 1 || cfg.F > 64 || (cfg.F & (cfg.F - 1))) return "fused_rows must be a power of two in [1, 64]";
   if (cfg.TW < 32 || cfg.TW % 32 || cfg.TW > 1024) return "tile_cols must be a multiple of 32 in [32, 1024]";
   if (cfg.threads < 32 || cfg.threads % 32 || cfg.threads > 1024) return "threads must be a multiple of 32";
+  if (cfg.generic_cols < 0 || cfg.generic_cols % 32 || cfg.generic_cols > 1024)
+    return "generic_cols must be 0 or a multiple of 32 in [32, 1024]";
   if (cfg.rounding != 0 && cfg.rounding != 1) return "unknown rounding rule";
   set_rounding_rule(cfg.rounding);
   P = HostPlan();
@@ -763,7 +765,7 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
   // buffers of up to 63 rows) use half of it, so their shared windows stay
   // no larger than the fast path's
   for (const FusedItem& fi : P.fused) P.n_by64 += fi.kind == FUSED_BY64;
-  P.generic_tw = std::max(32, cfg.TW / 64 * 32);
+  P.generic_tw = cfg.generic_cols > 0 ? cfg.generic_cols : std::max(32, cfg.TW / 64 * 32);
   for (FusedItem& fi : P.fused) {
     fi.tw = fi.kind == FUSED_BY64 ? cfg.TW : P.generic_tw;
     fi.ntiles = (fi.wn + fi.tw - 1) / fi.tw;

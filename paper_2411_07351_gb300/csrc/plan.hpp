@@ -56,6 +56,7 @@ struct PlanConfig {
   int32_t TW = 0;          // fused column tile (0: the planner's default)
   int32_t threads = 0;     // fused CTA size (0: the planner's default)
   int32_t spine_chunk = 3; // spine nodes merged per spine-sum launch (the lower chunks first)
+  int32_t generic_cols = 0; // column tile of generic subtrees (0: half of TW, at least 32)
   bool with_adjoint = false;  // also build the adjoint tables
   int32_t rounding = 0;       // 0: exact half-to-even; 1: rint(t * k) with k = (m_i - 1)/(m - 1) in fp64
 };

@@ -38,7 +38,7 @@ class Plan:
     def __init__(self, h: int, w: int, dtype=torch.float32, quads: int = C.FHT_QALL,
                  boundary: str = "cyclic", split: str = "T", device: int | None = None,
                  fused_rows: int = 0, tile_cols: int = 0, threads: int = 0, with_adjoint: bool = False,
-                 tuning: str | None = None, rounding: str = "exact", spine_chunk: int = 0):
+                 tuning: str | None = None, rounding: str = "exact", spine_chunk: int = 0, generic_cols: int = 0):
         self._lib = C.load()
         if tuning == "auto" and not (tile_cols or threads):
             from .tune import lookup
@@ -60,7 +60,7 @@ class Plan:
         if rounding not in ("exact", "float"):
             raise ValueError("rounding is 'exact' or 'float'")
         tun = C.fht_tuning_t(fused_rows, tile_cols, threads, int(with_adjoint), 1 if rounding == "float" else 0,
-                             int(spine_chunk))
+                             int(spine_chunk), int(generic_cols))
         handle = ctypes.c_void_p()
         args = (ctypes.byref(handle), self.h, self.w, self.fht_dtype, self.quads, BOUNDARY[boundary], SPLIT[split],
                 self.device_index, ctypes.byref(tun))
@@ -233,12 +233,12 @@ class PlanBuilderPool:
         self._n = ctypes.c_int32()
 
     def submit(self, h: int, w: int, dtype, quads: int = C.FHT_QALL, boundary: str = "cyclic", split: str = "T",
-               device: int | None = None, tile_cols: int = 0, threads: int = 0) -> int:
+               device: int | None = None, tile_cols: int = 0, threads: int = 0, generic_cols: int = 0) -> int:
         if device is None:
             device = torch.cuda.current_device()
         tag = self._next
         self._next += 1
-        tun = C.fht_tuning_t(0, int(tile_cols), int(threads), 0, 0, 0)
+        tun = C.fht_tuning_t(0, int(tile_cols), int(threads), 0, 0, 0, int(generic_cols))
         C.check(self._lib.fht_builder_submit(self._b, tag, int(h), int(w), DTYPES[dtype][0], int(quads),
                                              BOUNDARY[boundary], SPLIT[split], int(device), ctypes.byref(tun)),
                 "fht_builder_submit")
@@ -283,14 +283,16 @@ class PlanCache:
         self._d: OrderedDict = OrderedDict()
         self._lock = threading.Lock()
 
-    def get(self, h, w, dtype, quads, boundary, split, device, tile_cols: int = 0) -> Plan:
-        key = (h, w, dtype, quads, boundary, split, device, tile_cols)
+    def get(self, h, w, dtype, quads, boundary, split, device, tile_cols: int = 0, threads: int = 0,
+            generic_cols: int = 0) -> Plan:
+        key = (h, w, dtype, quads, boundary, split, device, tile_cols, threads, generic_cols)
         with self._lock:
             p = self._d.get(key)
             if p is not None:
                 self._d.move_to_end(key)
                 return p
-        p = Plan(h, w, dtype, quads, boundary, split, device, tile_cols=tile_cols)
+        p = Plan(h, w, dtype, quads, boundary, split, device, tile_cols=tile_cols, threads=threads,
+                 generic_cols=generic_cols)
         with self._lock:
             self._d[key] = p
             while len(self._d) > self.capacity:

@@ -28,7 +28,7 @@ from dataclasses import dataclass, field
 import torch
 
 from . import _capi as C
-from .batch import BATCH_TILE_COLS, BatchQueue
+from .batch import BATCH_GENERIC_COLS, BATCH_THREADS, BATCH_TILE_COLS, BatchQueue
 from .fht import PlanBuilderPool
 
 
@@ -98,9 +98,11 @@ class PlanBuilder:
             if slot is None:
                 slot = _PlanSlot()
                 # requests that will be batched get the batch tile width
-                tc = BATCH_TILE_COLS if h * w < self.batch_below else 0
+                batched = h * w < self.batch_below
                 tag = self.pool.submit(h, w, req.image.dtype, self.quads, self.boundary, self.split, self.device,
-                                       tile_cols=tc)
+                                       tile_cols=BATCH_TILE_COLS if batched else 0,
+                                       threads=BATCH_THREADS if batched else 0,
+                                       generic_cols=BATCH_GENERIC_COLS if batched else 0)
                 self.pending[tag] = (k, slot)
                 self.by_shape[k] = slot
         req.plan_future = slot
