@@ -12,13 +12,16 @@ from . import _capi as C
 from .fht import Plan, PlanCache
 
 
-# Launch shape of plans made for batched launches: the register-tiled block
-# path (192-column tiles, 256 threads: the persistent kernel's CTA size) for
-# the 64-row blocks and bands, and 32-column tiles for the generic subtrees,
-# so that every unit fits one 66.5 KB shared buffer (3 CTAs per SM).
-BATCH_TILE_COLS = 192
-BATCH_THREADS = 256
-BATCH_GENERIC_COLS = 32
+# Launch shape of plans made for batched launches: 64-column tiles keep the
+# persistent kernel at 3 CTAs per SM (<= 64 KB of shared memory per CTA) and
+# fit the small images batches are for.  (Plans with the register-tiled shape,
+# tile 192 x 256 threads with 32-column generic tiles, also run in a batch;
+# measured on the 4096-map batch they were slower: graph replay 26.2 vs
+# 23.5 ms, a 192-column register tile costing the same however few of its
+# columns a narrow image fills.)
+BATCH_TILE_COLS = 64
+BATCH_THREADS = 0
+BATCH_GENERIC_COLS = 0
 
 # numpy layout of fht_job (include/fht.h): 64 bytes, naturally aligned fields
 _JOB_DTYPE = np.dtype([("plan", np.uint64), ("d_in", np.uint64), ("in_pitch", np.int64), ("d_out", np.uint64),

@@ -181,3 +181,26 @@ def test_batch_c3_full_size(F, orc):
     for x, o, p in zip(xs, outs, plans):
         assert torch.equal(o, p.forward(x))
     q.close()
+
+
+def test_batch_register_tiled_plans(F, orc):
+    """Plans with the register-tiled launch shape (tile 192, 256 threads,
+    32-column generic tiles) submitted to the batched launch: its 64-row block
+    and band units take the register-tiled path, bit-exact against the oracle."""
+    from paper_2411_07351_gb300.batch import BatchQueue
+
+    g = np.random.default_rng(17)
+    sizes = [(64, 300), (200, 511), (300, 90), (511, 200), (1100, 40), (65, 17)]
+    imgs = [g.integers(0, 256, s, dtype=np.uint8) for s in sizes]
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    q = BatchQueue(max_jobs=16, max_units=1 << 18)
+    for boundary in ("cyclic", "extended"):
+        plans = [F.Plan(h, w, torch.uint8, 15, boundary, tile_cols=192, threads=256, generic_cols=32)
+                 for h, w in sizes]
+        outs, _, _ = q.submit(xs, 15, boundary, plans=plans)
+        torch.cuda.synchronize()
+        assert q.status() == 0
+        b = orc.EXTENDED if boundary == "extended" else orc.CYCLIC
+        for im, o in zip(imgs, outs):
+            assert np.array_equal(o.cpu().numpy(), orc.fht(im.astype(np.int64), 15, b))
+    q.close()
