@@ -517,35 +517,6 @@ def measure_c1(args) -> dict:
         b.synchronize()
         if i >= 50:
             gdev.append(a.elapsed_time(b) * 1e3)
-    # the same transform as ONE persistent launch: a one-job batch (fht_submit),
-    # its fused, band and spine phases ordered inside the launch; replayed
-    # from a CUDA graph (staging copies, counter reset and the launch)
-    from paper_2411_07351_gb300.batch import BatchQueue
-
-    bq = BatchQueue(max_jobs=1, max_units=4096)
-    bplan = bq.plan_for(x, F.FHT_Q0, "cyclic", "T")
-    bout, bws = bplan.new_output(), bplan.new_workspace()
-    for _ in range(20):
-        bq.submit([x], F.FHT_Q0, "cyclic", "T", outs=[bout], workspaces=[bws], plans=[bplan])
-    torch.cuda.synchronize()
-    assert torch.equal(bout, out), "one-launch c1 result differs from the chained launches"
-    bside = torch.cuda.Stream()
-    bside.wait_stream(torch.cuda.current_stream())
-    bgraph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(bside):
-        with torch.cuda.graph(bgraph, stream=bside, capture_error_mode="relaxed"):
-            bq.submit([x], F.FHT_Q0, "cyclic", "T", outs=[bout], workspaces=[bws], stream=bside, plans=[bplan])
-    torch.cuda.synchronize()
-    bdev = []
-    for i in range(max(args.steps, 1000) + 50):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        bgraph.replay()
-        b.record()
-        b.synchronize()
-        if i >= 50:
-            bdev.append(a.elapsed_time(b) * 1e3)
-    bq.close()
     n = max(args.steps, 1000)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
     host = []
@@ -563,9 +534,7 @@ def measure_c1(args) -> dict:
             "config": {"workload": "c1: 257x257 uint8 U{0..255} seed 1, quadrant Q0, cyclic"},
             "latency_us": {"device_p50": _pct(dev, 0.5), "device_p99": _pct(dev, 0.99),
                            "host_p50": _pct(host, 0.5), "host_p99": _pct(host, 0.99),
-                           "graph_device_p50": _pct(gdev, 0.5), "graph_device_p99": _pct(gdev, 0.99),
-                           "one_launch_graph_device_p50": _pct(bdev, 0.5),
-                           "one_launch_graph_device_p99": _pct(bdev, 0.99)},
+                           "graph_device_p50": _pct(gdev, 0.5), "graph_device_p99": _pct(gdev, 0.99)},
             "tile_cols": int(plan.info.tile_cols),
             "gpu_launches_per_call": _launches(plan)}
     return line
