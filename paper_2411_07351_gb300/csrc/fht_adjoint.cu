@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fht_block.cuh"
 #include "fht_desc.h"
 #include "fht_launch.hpp"
 #include "fht_nvtx.hpp"
@@ -168,7 +169,35 @@ __global__ void __launch_bounds__(256) adj_upper_kernel(const AdjRow* __restrict
     const bool neg = R.flags & ROW_NEG;
     const AccT* src = (fin ? gout : ws_in) + R.src;
     AccT* dst = ws_out + R.dst;
-    for (int32_t i0 = 0; i0 < R.wdst; i0 += (int32_t)blockDim.x * U) {
+    int32_t i0 = 0;
+    if constexpr (sizeof(AccT) == 4) {
+      // 16-byte path: four consecutive columns per thread, for chunks where the
+      // parent rows are read without the root's column map and every term's
+      // columns lie inside its row with 8 elements to spare; the terms are
+      // added in the same order as below, so the results are identical
+      const int32_t C = (int32_t)blockDim.x * 4;
+      const bool vec = !fin && (R.dst & 3) == 0;
+      for (; vec && i0 + C <= R.wdst; i0 += C) {
+        bool inside = true;
+        for (int32_t c = 0; c < R.term_count && inside; c++) {
+          const int32_t e = terms[R.term_begin + c].e;
+          inside = ext ? (i0 + e >= 0 && i0 + C + e + 8 <= R.wsrc) : (i0 + C + e + 8 <= R.W);
+        }
+        if (!inside) break;
+        const int32_t i = i0 + 4 * (int32_t)threadIdx.x;
+        AccT acc[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
+        for (int32_t c = 0; c < R.term_count; c++) {
+          const AdjTerm T = terms[R.term_begin + c];
+          const int64_t off = R.src + (int64_t)T.t * R.src_pitch + T.e;  // element offset of column 0's term
+          AccT v[4];
+          ldg4_shifted<false, AccT>(src + (int64_t)T.t * R.src_pitch + T.e + i, (int32_t)(off & 3), v);
+#pragma unroll
+          for (int q = 0; q < 4; q++) acc[q] += v[q];
+        }
+        sts4<AccT>(dst + i, acc);
+      }
+    }
+    for (; i0 < R.wdst; i0 += (int32_t)blockDim.x * U) {
       AccT acc[U];
 #pragma unroll
       for (int q = 0; q < U; q++) acc[q] = AccT(0);

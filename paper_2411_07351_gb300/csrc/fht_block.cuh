@@ -105,6 +105,34 @@ __device__ __forceinline__ void sts4(T* p, const T* s) {
   *reinterpret_cast<typename Vec4<T>::type*>(p) = v;
 }
 
+// Four consecutive elements p[0..3] of global memory whose first one sits
+// `a` (= its element offset mod 4) past a 16-byte boundary: one or two
+// aligned 16-byte loads and a selection.  `a` must be the same in every
+// thread of a warp for the selection not to diverge; the caller makes sure
+// that the aligned span [p - a, p - a + 8) is readable.
+template <bool kC, typename T>
+__device__ __forceinline__ void ldg4_shifted(const T* p, int32_t a, T (&o)[4]) {
+  using V = typename Vec4<T>::type;
+  const V* q = reinterpret_cast<const V*>(p - a);
+  const V v0 = kC ? __ldcg(q) : __ldg(q);
+  if (a == 0) {
+    o[0] = v0.x, o[1] = v0.y, o[2] = v0.z, o[3] = v0.w;
+    return;
+  }
+  const V v1 = kC ? __ldcg(q + 1) : __ldg(q + 1);
+  switch (a) {
+    case 1:
+      o[0] = v0.y, o[1] = v0.z, o[2] = v0.w, o[3] = v1.x;
+      break;
+    case 2:
+      o[0] = v0.z, o[1] = v0.w, o[2] = v1.x, o[3] = v1.y;
+      break;
+    default:
+      o[0] = v0.w, o[1] = v1.x, o[2] = v1.y, o[3] = v1.z;
+      break;
+  }
+}
+
 // The R slopes of one (group, k) at columns j .. j + 3: child e is shared
 // row `row0 + e * M` (row0 = group * R * M + k), read from column j + e k.
 template <int R, int M, int A, typename T>

@@ -86,7 +86,30 @@ __global__ void __launch_bounds__(256) upper_kernel(const RowJob* __restrict__ r
     const bool fin = J.flags & ROW_FINAL;
     const bool ext = J.flags & ROW_EXT;
     AccT* dst = (fin ? out : ws_out) + J.dst;
-    for (int32_t u0 = 0; u0 < J.wout; u0 += (int32_t)blockDim.x * U) {
+    int32_t u0 = 0;
+    if constexpr (sizeof(AccT) == 4) {
+      // 16-byte path: every thread four consecutive columns; a chunk runs it
+      // when the row is not a root row (no column map) and all of its reads
+      // lie inside both child rows with 8 elements to spare (the aligned
+      // vector loads read up to 7 past the first wanted element)
+      const int32_t C = (int32_t)blockDim.x * 4;
+      const int32_t at = (int32_t)((J.top + (ext ? J.dtop : 0)) & 3), ab = (int32_t)((J.bot + J.dbot) & 3);
+      const bool vec = !fin && (J.dst & 3) == 0;
+      for (; vec && u0 + C <= J.wout; u0 += C) {
+        const bool inside = ext ? (u0 + J.dtop >= 0 && u0 + C + J.dtop + 8 <= J.wtop && u0 + J.dbot >= 0 &&
+                                   u0 + C + J.dbot + 8 <= J.wbot)
+                                : (u0 + C + 8 <= J.W && u0 + C + J.dbot + 8 <= J.W);
+        if (!inside) break;
+        const int32_t u = u0 + 4 * (int32_t)threadIdx.x;
+        AccT a[4], b[4], o[4];
+        ldg4_shifted<false, AccT>(top + u + (ext ? J.dtop : 0), at, a);
+        ldg4_shifted<false, AccT>(bot + u + J.dbot, ab, b);
+#pragma unroll
+        for (int q = 0; q < 4; q++) o[q] = a[q] + b[q];
+        sts4<AccT>(dst + u, o);
+      }
+    }
+    for (; u0 < J.wout; u0 += (int32_t)blockDim.x * U) {
       AccT a[U], b[U];
 #pragma unroll
       for (int q = 0; q < U; q++) {
