@@ -249,7 +249,7 @@ __global__ void adj_sum_kernel(const AccT* __restrict__ ws, int64_t g0, int64_t 
 void adjoint_geometry(const HostPlan& P, int32_t& rp, int32_t& padl, size_t& smem) {
   const int32_t Fm = P.max_fused_m;
   padl = P.max_fused_shift;
-  rp = padl + P.cfg.TW + Fm - 1;
+  rp = padl + P.adj_tw + Fm - 1;
   if (rp % 2 == 0) rp++;
   smem = (size_t)2 * Fm * rp * P.acc_size;
 }
@@ -278,7 +278,7 @@ static cudaError_t launch_adjoint_t(const DevicePlan& D, const void* gout, void*
   for (int q = 0; q < 4; q++) fp.quad[q] = P.quad[q];
   fp.h = P.cfg.h;
   fp.w = P.cfg.w;
-  fp.TW = P.cfg.TW;
+  fp.TW = P.adj_tw;
   int32_t rp, padl;
   size_t smem;
   adjoint_geometry(P, rp, padl, smem);
@@ -289,7 +289,7 @@ static cudaError_t launch_adjoint_t(const DevicePlan& D, const void* gout, void*
   if ((e = raise_smem_limit(kfn, smem)) != cudaSuccess)
     return e;
   dim3 grid((unsigned)P.fused.size(), P.max_antiles);
-  kfn<<<grid, P.cfg.threads, smem, st>>>(fp);
+  kfn<<<grid, P.adj_threads, smem, st>>>(fp);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int64_t g[4] = {0, 0, 0, 0};
   int32_t nq = 0;

@@ -301,6 +301,8 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
   set_rounding_rule(cfg.rounding);
   P = HostPlan();
   P.cfg = cfg;
+  P.adj_tw = cfg.TW == kVTile ? 128 : cfg.TW;
+  P.adj_threads = cfg.TW == kVTile ? 512 : cfg.threads;
   P.in_size = dtype_in_size(cfg.dtype);
   P.acc_size = dtype_acc_size(cfg.dtype);
   const int32_t acc = P.acc_size;
@@ -487,7 +489,7 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
         }
         fi.aprog = ait->second;
       }
-      fi.antiles = (Q.L + cfg.TW - 1) / cfg.TW;
+      fi.antiles = (Q.L + P.adj_tw - 1) / P.adj_tw;
       P.max_antiles = std::max(P.max_antiles, fi.antiles);
       fi.q = q;
       fi.a = nd.a;

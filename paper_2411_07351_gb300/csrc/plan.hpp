@@ -103,6 +103,9 @@ struct HostPlan {
   // threads): the 64-row blocks run in a launch of their own, after one for
   // the generic subtrees (fused[0 .. n_generic) sorts first)
   bool vblock = false;
+  // adjoint fused kernel: its own column tile and CTA size (the forward's
+  // register-tiled shape does not suit its shared-memory radix-2 path)
+  int32_t adj_tw = 0, adj_threads = 0;
   int32_t n_generic = 0;
   int32_t max_generic_ntiles = 0, max_by64_ntiles = 0;
   int64_t generic_bytes = 0, by64_bytes = 0;  // model bytes of the two kinds of fused items

@@ -270,10 +270,11 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
   for (size_t k = 0; k < P.fused.size(); k++) {
     const FusedItem& it = P.fused[k];
     const QuadDesc& Q = P.quad[it.q];
-    if (it.antiles < 1 || (int64_t)(it.antiles - 1) * TW >= Q.L || (int64_t)it.antiles * TW < Q.L)
+    const int32_t ATW = P.adj_tw;
+    if (it.antiles < 1 || (int64_t)(it.antiles - 1) * ATW >= Q.L || (int64_t)it.antiles * ATW < Q.L)
       return at("adjoint fused", k) + "tiles do not cover the view length";
     if (it.antiles > P.max_antiles) return at("adjoint fused", k) + "more tiles than the grid";
-    const int32_t TZin = TW + it.m - 1;
+    const int32_t TZin = ATW + it.m - 1;
     if (adj_padl + TZin > adj_rp) return at("adjoint fused", k) + "window wider than the shared row";
     if (it.aprog < 0 || (size_t)it.aprog + (size_t)it.nlev * (it.m + 1) > P.aptr.size())
       return at("adjoint fused", k) + "program pointers";
