@@ -171,28 +171,57 @@ __global__ void __launch_bounds__(256) adj_upper_kernel(const AdjRow* __restrict
     AccT* dst = ws_out + R.dst;
     int32_t i0 = 0;
     if constexpr (sizeof(AccT) == 4) {
-      // 16-byte path: four consecutive columns per thread, for chunks where the
-      // parent rows are read without the root's column map and every term's
-      // columns lie inside its row with 8 elements to spare; the terms are
-      // added in the same order as below, so the results are identical
+      // 16-byte path: four consecutive columns per thread, for chunks where
+      // every term's columns lie inside its parent row (no cyclic wrap) and,
+      // for a root row read through the column map X = (sigma u + kappa) mod W,
+      // the chunk's X are one contiguous run (ascending for sigma = +1,
+      // descending for sigma = -1) at least 8 elements from either end of the
+      // row; the terms are added in the same order as below, so the results
+      // are identical
       const int32_t C = (int32_t)blockDim.x * 4;
-      const bool vec = !fin && (R.dst & 3) == 0;
+      const bool vec = (R.dst & 3) == 0;
       for (; vec && i0 + C <= R.wdst; i0 += C) {
         bool inside = true;
         for (int32_t c = 0; c < R.term_count && inside; c++) {
           const int32_t e = terms[R.term_begin + c].e;
-          inside = ext ? (i0 + e >= 0 && i0 + C + e + 8 <= R.wsrc) : (i0 + C + e + 8 <= R.W);
+          if (ext) {
+            inside = i0 + e >= 0 && i0 + C + e + (fin ? 0 : 8) <= R.wsrc;
+          } else {
+            inside = i0 + C + e + (fin ? 0 : 8) <= R.W;
+          }
+          if (inside && fin) {
+            // X over u in [i0 + e, i0 + e + C): one run shifted by a multiple of W
+            const int32_t lo = neg ? R.kappa - (i0 + e + C - 1) : i0 + e + R.kappa;
+            const int32_t sh = lo >= R.W ? -R.W : lo < 0 ? R.W : 0;
+            inside = lo + sh >= 8 && lo + sh + C + 8 <= R.W;
+          }
         }
         if (!inside) break;
         const int32_t i = i0 + 4 * (int32_t)threadIdx.x;
         AccT acc[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
         for (int32_t c = 0; c < R.term_count; c++) {
           const AdjTerm T = terms[R.term_begin + c];
-          const int64_t off = R.src + (int64_t)T.t * R.src_pitch + T.e;  // element offset of column 0's term
+          const int64_t row = R.src + (int64_t)T.t * R.src_pitch;  // element offset of the parent row
           AccT v[4];
-          ldg4_shifted<false, AccT>(src + (int64_t)T.t * R.src_pitch + T.e + i, (int32_t)(off & 3), v);
+          if (!fin) {
+            ldg4_shifted<false, AccT>(src - R.src + row + T.e + i, (int32_t)((row + T.e) & 3), v);
 #pragma unroll
-          for (int q = 0; q < 4; q++) acc[q] += v[q];
+            for (int q = 0; q < 4; q++) acc[q] += v[q];
+          } else {
+            const int32_t lo = neg ? R.kappa - (i0 + T.e + C - 1) : i0 + T.e + R.kappa;
+            const int32_t sh = lo >= R.W ? -R.W : lo < 0 ? R.W : 0;
+            if (!neg) {
+              const int32_t X = i + T.e + R.kappa + sh;  // columns X .. X + 3
+              ldg4_shifted<false, AccT>(src - R.src + row + X, (int32_t)((row + R.kappa + sh + T.e) & 3), v);
+#pragma unroll
+              for (int q = 0; q < 4; q++) acc[q] += v[q];
+            } else {
+              const int32_t X = R.kappa - (i + T.e) + sh - 3;  // columns X .. X + 3, read backwards
+              ldg4_shifted<false, AccT>(src - R.src + row + X, (int32_t)((row + R.kappa + sh - T.e - 3) & 3), v);
+#pragma unroll
+              for (int q = 0; q < 4; q++) acc[q] += v[3 - q];
+            }
+          }
         }
         sts4<AccT>(dst + i, acc);
       }
