@@ -155,6 +155,92 @@ __global__ void __launch_bounds__(512, 1) adj_fused_kernel(AdjFusedParams p) {
   }
 }
 
+// Adjoint of a 64-row Brady-Yong block on the register-tiled path.  The
+// forward block is H[t][u] = sum_y V[a + y][u - c + p_t(y)]; its transpose is
+// gV[a + y][z] = sum_t g[t][z + c - p_t(y)].  The power-of-two pattern matrix
+// is symmetric (p_t(y) = p_y(t)), so with the tile's columns reversed,
+// z' = z0 + kVTile - 1 - z and g~[t][v] = g[t][c + z0 + kVTile - 1 - v],
+//     gV[a + y][z] = sum_t g~[t][z' + p_y(t)],
+// the forward block transform of g~ read at slope y.  One CTA = one block x
+// one tile of kVTile view columns: the 64 gradient rows are staged reversed,
+// merged exactly as the forward merges its window, and stored back reversed
+// into the quadrant's view gradient.
+template <typename AccT>
+__device__ __forceinline__ void adj_stage_rev(const AdjFusedParams& p, const FusedItem& it, const QuadDesc& Q,
+                                              int32_t z0, AccT* S) {
+  const AccT* __restrict__ gout = static_cast<const AccT*>(p.gout);
+  const AccT* __restrict__ ws = static_cast<const AccT*>(p.ws);
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t K = it.c + z0 + kVTile - 1;  // u of window column 0
+  AccT v[8][kVWin / 32];
+#pragma unroll
+  for (int rr = 0; rr < 8; rr++) {
+    const int32_t t = 8 * warp + rr;
+#pragma unroll
+    for (int c = 0; c < kVWin / 32; c++) {
+      int32_t u = K - (32 * c + lane);
+      bool ok = true;
+      if (Q.ext) {
+        ok = u >= 0 && u < it.wn;
+      } else {
+        u = wrap_mod(u, Q.W);
+      }
+      AccT x = AccT(0);
+      if (ok) {
+        if (it.final_) {
+          int32_t X = Q.sigma * u + Q.kappa;
+          if (X < 0) X += Q.W;
+          if (X >= Q.W) X -= Q.W;
+          x = gout[it.dst + (int64_t)t * Q.W + X];
+        } else {
+          x = ws[it.dst + (int64_t)t * it.dst_pitch + u];
+        }
+      }
+      v[rr][c] = x;
+    }
+  }
+#pragma unroll
+  for (int rr = 0; rr < 8; rr++) {
+    AccT* dst = S + (8 * warp + rr) * kVPitch + lane;
+#pragma unroll
+    for (int c = 0; c < kVWin / 32; c++) dst[32 * c] = v[rr][c];
+  }
+}
+
+template <typename AccT>
+__global__ void __launch_bounds__(kVThreads, 3) adj_block_kernel(AdjFusedParams p) {
+  const FusedItem it = p.items[blockIdx.x];
+  const QuadDesc& Q = p.quad[it.q];
+  const int32_t z0 = blockIdx.y * kVTile;
+  if (z0 >= Q.L) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AccT* S = reinterpret_cast<AccT*>(smem_raw);
+  adj_stage_rev<AccT>(p, it, Q, z0, S);
+  __syncwarp();
+  AccT* __restrict__ gq = static_cast<AccT*>(p.ws) + Q.grad_off;
+  v_merge_groups<AccT>(S, 6, kVTile, [] {
+    __syncthreads();
+    return true;
+  }, [&](int32_t row0, int32_t j, const auto& o) {
+    constexpr int R = sizeof(o) / sizeof(o[0]);
+#pragma unroll
+    for (int x = 0; x < 4; x++) {
+      const int32_t z = z0 + kVTile - 1 - (j + x);  // view column of tile column j + x
+      if (z >= Q.L) continue;
+      const int32_t zz = Q.flip ? Q.L - 1 - z : z;
+#pragma unroll
+      for (int i = 0; i < R; i++) {
+        const int32_t r = it.a + row0 + i;  // view row
+        if (Q.transpose) {
+          gq[(int64_t)zz * p.w + r] = o[i][x];
+        } else {
+          gq[(int64_t)r * p.w + zz] = o[i][x];
+        }
+      }
+    }
+  });
+}
+
 template <typename AccT>
 __global__ void __launch_bounds__(256) adj_upper_kernel(const AdjRow* __restrict__ rows, int64_t nrows,
                                                        const AdjTerm* __restrict__ terms, const AccT* ws_in,
@@ -317,9 +403,29 @@ static cudaError_t launch_adjoint_t(const DevicePlan& D, const void* gout, void*
   auto kfn = adj_fused_kernel<AccT>;
   if ((e = raise_smem_limit(kfn, smem)) != cudaSuccess)
     return e;
-  dim3 grid((unsigned)P.fused.size(), P.max_antiles);
-  kfn<<<grid, P.adj_threads, smem, st>>>(fp);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // 4-byte accumulators: the 64-row blocks on the register-tiled path, the
+  // generic subtrees (sorted first) on the shared-memory path
+  const bool vblocks = sizeof(AccT) == 4 && P.n_by64 > 0;
+  const unsigned nfused = vblocks ? (unsigned)P.n_generic : (unsigned)P.fused.size();
+  if (nfused > 0) {
+    dim3 grid(nfused, P.max_antiles);
+    kfn<<<grid, P.adj_threads, smem, st>>>(fp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if constexpr (sizeof(AccT) == 4) {
+    if (vblocks) {
+      int32_t maxL = 1;
+      for (int q = 0; q < 4; q++)
+        if (P.cfg.quads & (1u << q)) maxL = std::max(maxL, P.quad[q].L);
+      const size_t vsmem = (size_t)64 * kVPitch * sizeof(AccT);
+      auto kbl = adj_block_kernel<AccT>;
+      if ((e = raise_smem_limit(kbl, vsmem)) != cudaSuccess) return e;
+      AdjFusedParams bp = fp;
+      bp.items = D.fused + P.n_generic;
+      kbl<<<dim3((unsigned)P.n_by64, (unsigned)((maxL + kVTile - 1) / kVTile)), kVThreads, vsmem, st>>>(bp);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
   int64_t g[4] = {0, 0, 0, 0};
   int32_t nq = 0;
   for (int q = 0; q < 4; q++)

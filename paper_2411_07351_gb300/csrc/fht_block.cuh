@@ -312,10 +312,10 @@ __device__ __forceinline__ void v_pass1(AccT* S) {
   }
 }
 
-// Groups of B = R1 <= 8 rows: one pass, straight to global memory.
-template <int R1, typename AccT>
-__device__ __forceinline__ void v_pass1_out(const AccT* S, const FusedItem& it, const QuadDesc& Q,
-                                            AccT* __restrict__ base, int32_t u0, int32_t ncols, bool vec_ok) {
+// Groups of B = R1 <= 8 rows: one pass, straight to global memory through
+// `st(row0, j, o)` (rows row0 .. row0 + R1 - 1, tile columns j .. j + 3).
+template <int R1, typename AccT, typename Store>
+__device__ __forceinline__ void v_pass1_out(const AccT* S, int32_t ncols, Store st) {
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int32_t j0 = 0; j0 < kVTile; j0 += 128) {
@@ -325,7 +325,7 @@ __device__ __forceinline__ void v_pass1_out(const AccT* S, const FusedItem& it, 
     for (int32_t sg = 0; sg < 8; sg += R1) {
       AccT o[R1][4];
       by_item<R1, 1, 0, AccT>(S, 8 * warp + sg, 0, j, o);
-      v_store<R1, AccT>(it, Q, base, 8 * warp + sg, u0, j, ncols, vec_ok, o);
+      st(8 * warp + sg, j, o);
     }
   }
 }
@@ -333,9 +333,8 @@ __device__ __forceinline__ void v_pass1_out(const AccT* S, const FusedItem& it, 
 // Second pass: in each group g of B = 8 R2 rows the R2 8-row blocks become
 // the B-row block; slope R2 k + i reads child e at shared row g B + 8 e + k.
 // Warp w computes k = w of every group.
-template <int R2, int A, typename AccT>
-__device__ __forceinline__ void v_pass2_k(const AccT* S, int32_t k, const FusedItem& it, const QuadDesc& Q,
-                                          AccT* __restrict__ base, int32_t u0, int32_t ncols, bool vec_ok) {
+template <int R2, int A, typename AccT, typename Store>
+__device__ __forceinline__ void v_pass2_k(const AccT* S, int32_t k, int32_t ncols, Store& st) {
   const int32_t lane = threadIdx.x & 31;
   constexpr int B = 8 * R2;
 #pragma unroll 1
@@ -346,36 +345,70 @@ __device__ __forceinline__ void v_pass2_k(const AccT* S, int32_t k, const FusedI
       if (j >= ncols) break;
       AccT o[R2][4];
       by_item<R2, 8, A, AccT>(S, g * B + k, k, j, o);
-      v_store<R2, AccT>(it, Q, base, g * B + R2 * k, u0, j, ncols, vec_ok, o);
+      st(g * B + R2 * k, j, o);
     }
   }
 }
 
-template <int R2, typename AccT>
-__device__ __forceinline__ void v_pass2(const AccT* S, const FusedItem& it, const QuadDesc& Q, AccT* __restrict__ base,
-                                        int32_t u0, int32_t ncols, bool vec_ok) {
+template <int R2, typename AccT, typename Store>
+__device__ __forceinline__ void v_pass2(const AccT* S, int32_t ncols, Store st) {
   const int32_t k = threadIdx.x >> 5;
   switch (k & 3) {
     case 0:
-      v_pass2_k<R2, 0, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      v_pass2_k<R2, 0, AccT>(S, k, ncols, st);
       break;
     case 1:
-      v_pass2_k<R2, 1, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      v_pass2_k<R2, 1, AccT>(S, k, ncols, st);
       break;
     case 2:
-      v_pass2_k<R2, 2, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      v_pass2_k<R2, 2, AccT>(S, k, ncols, st);
       break;
     default:
-      v_pass2_k<R2, 3, AccT>(S, k, it, Q, base, u0, ncols, vec_ok);
+      v_pass2_k<R2, 3, AccT>(S, k, ncols, st);
       break;
   }
 }
 
-// The merges of one staged 64-row block (FUSED_BY64) or band item
-// (FUSED_BAND: groups of 2^L rows) x one tile of kVTile columns, run by
-// kVThreads threads (warps 0 .. 7 of the CTA); results go to global memory.
-// `bar` synchronises the merging warps between the two passes; it returns
-// false if its wait gave up, and then the second pass is skipped.
+// The merges of a staged window whose groups are 2^L-row Brady-Yong blocks
+// (L = 6: one 64-row block), over tile columns [0, ncols), run by kVThreads
+// threads (warps 0 .. 7 of the CTA); the results leave through `st`.  `bar`
+// synchronises the merging warps between the two passes; it returns false
+// if its wait gave up, and then the second pass is skipped.
+template <typename AccT, typename Bar, typename Store>
+__device__ __forceinline__ bool v_merge_groups(AccT* S, int32_t L, int32_t ncols, Bar bar, Store st) {
+  switch (L) {
+    case 6:
+      v_pass1<kVTile + 56, AccT>(S);
+      if (!bar()) return false;
+      v_pass2<8, AccT>(S, ncols, st);
+      break;
+    case 5:
+      v_pass1<kVTile + 24, AccT>(S);
+      if (!bar()) return false;
+      v_pass2<4, AccT>(S, ncols, st);
+      break;
+    case 4:
+      v_pass1<kVTile + 8, AccT>(S);
+      if (!bar()) return false;
+      v_pass2<2, AccT>(S, ncols, st);
+      break;
+    case 3:
+      v_pass1_out<8, AccT>(S, ncols, st);
+      break;
+    case 2:
+      v_pass1_out<4, AccT>(S, ncols, st);
+      break;
+    default:
+      v_pass1_out<2, AccT>(S, ncols, st);
+      break;
+  }
+  return true;
+}
+
+// The forward merges of one staged 64-row block (FUSED_BY64) or band item
+// (FUSED_BAND: groups of 2^L rows) x one tile of kVTile columns, stored as
+// the item's Hough rows (node-local workspace columns, or the output through
+// the quadrant's column map).
 template <typename AccT, typename Bar>
 __device__ __forceinline__ bool v_merge(const FusedParams& p, const FusedItem& it, const QuadDesc& Q, int32_t tile,
                                         AccT* S, Bar bar) {
@@ -385,33 +418,10 @@ __device__ __forceinline__ bool v_merge(const FusedParams& p, const FusedItem& i
   // 16-byte stores need node-local columns (no output map) on 16-byte aligned rows
   const bool vec_ok = !it.final_ && ((it.dst | (int64_t)it.dst_pitch) & 3) == 0 &&
                       (reinterpret_cast<uintptr_t>(p.ws) & 15) == 0;
-  switch (it.L) {
-    case 6:
-      v_pass1<kVTile + 56, AccT>(S);
-      if (!bar()) return false;
-      v_pass2<8, AccT>(S, it, Q, base, u0, ncols, vec_ok);
-      break;
-    case 5:
-      v_pass1<kVTile + 24, AccT>(S);
-      if (!bar()) return false;
-      v_pass2<4, AccT>(S, it, Q, base, u0, ncols, vec_ok);
-      break;
-    case 4:
-      v_pass1<kVTile + 8, AccT>(S);
-      if (!bar()) return false;
-      v_pass2<2, AccT>(S, it, Q, base, u0, ncols, vec_ok);
-      break;
-    case 3:
-      v_pass1_out<8, AccT>(S, it, Q, base, u0, ncols, vec_ok);
-      break;
-    case 2:
-      v_pass1_out<4, AccT>(S, it, Q, base, u0, ncols, vec_ok);
-      break;
-    default:
-      v_pass1_out<2, AccT>(S, it, Q, base, u0, ncols, vec_ok);
-      break;
-  }
-  return true;
+  return v_merge_groups<AccT>(S, it.L, ncols, bar, [&](int32_t row0, int32_t j, const auto& o) {
+    constexpr int R = sizeof(o) / sizeof(o[0]);
+    v_store<R, AccT>(it, Q, base, row0, u0, j, ncols, vec_ok, o);
+  });
 }
 
 // One item x one tile, staged by the merging warps themselves (each stages
