@@ -46,6 +46,8 @@ class Plan:
             best = lookup(h, w, dtype, quads, boundary, split)
             if best:
                 tile_cols, threads = int(best["tile_cols"]), int(best["threads"])
+                if not fused_rows:
+                    fused_rows = int(best.get("fused_rows", 0))
         if dtype not in DTYPES:
             raise ValueError(f"unsupported dtype {dtype}")
         self.h, self.w = int(h), int(w)

@@ -1,9 +1,12 @@
 """Autotuner for the forward transform's launch shape.
 
 For a size bucket it times ``fht_forward`` with each candidate (column tile
-of the fused / band passes x threads per CTA) using CUDA events, keeps the
-fastest and records it in a JSON cache keyed by (h bucket, w bucket, dtype,
-quadrants, boundary, split).  ``Plan(..., tuning="auto")`` reads the cache.
+of the fused / band passes x threads per CTA x the height of the subtrees
+merged in shared memory: 64-row blocks with the band + spine schedule, or 32-
+and 16-row subtrees with one HBM pass per tree height above them) using CUDA
+events, keeps the fastest and records it in a JSON cache keyed by (h bucket,
+w bucket, dtype, quadrants, boundary, split).  The candidate (192, 256, 64) is
+the register-tiled block path.  ``Plan(..., tuning="auto")`` reads the cache.
 Every candidate computes the same result (the tests check this); only speed
 differs.
 
@@ -21,7 +24,9 @@ import torch
 
 from . import _capi as C
 
-CANDIDATES = [(tc, th) for tc in (64, 96, 128, 192, 256) for th in (256, 512)]
+# (tile_cols, threads, fused_rows)
+CANDIDATES = [(tc, th, 64) for tc in (64, 96, 128, 192, 256) for th in (256, 512)] + \
+    [(128, 512, 32), (64, 512, 32), (128, 512, 16)]
 _lock = threading.Lock()
 
 
@@ -82,7 +87,8 @@ def sweep(sizes=(64, 128, 256, 512, 1024, 2048, 4096), dtypes=(torch.uint8, torc
             for b in boundaries:
                 e = tune(n, n, dt, q, b, "T", reps=reps, save=False)
                 table[key(n, n, dt, q, b, "T")] = e
-                print(key(n, n, dt, q, b, "T"), e["tile_cols"], e["threads"], f"{e['ms']:.4f} ms", flush=True)
+                print(key(n, n, dt, q, b, "T"), e["tile_cols"], e["threads"], e["fused_rows"], f"{e['ms']:.4f} ms",
+                      flush=True)
     path = out or PACKAGED
     with open(path, "w") as f:
         json.dump(table, f, indent=1, sort_keys=True)
@@ -120,16 +126,17 @@ def tune(h: int, w: int, dtype=torch.float32, quads: int = C.FHT_QALL, boundary:
     else:
         x = torch.randn((h, w), generator=g, device=f"cuda:{dev}", dtype=dtype)
     results = []
-    for tc, th in candidates or CANDIDATES:
+    for tc, th, fr in candidates or CANDIDATES:
         try:
-            p = Plan(h, w, dtype, quads, boundary, split, dev, tile_cols=tc, threads=th)
+            p = Plan(h, w, dtype, quads, boundary, split, dev, tile_cols=tc, threads=th, fused_rows=fr)
         except C.FHTError:
             continue  # e.g. too much shared memory for this dtype
-        results.append((_time_plan(p, x, reps), tc, th))
+        results.append((_time_plan(p, x, reps), tc, th, fr))
         p.close()
     results.sort()
-    ms, tc, th = results[0]
-    entry = {"tile_cols": tc, "threads": th, "ms": ms, "candidates": [[r[1], r[2], r[0]] for r in results]}
+    ms, tc, th, fr = results[0]
+    entry = {"tile_cols": tc, "threads": th, "fused_rows": fr, "ms": ms,
+             "candidates": [[r[1], r[2], r[3], r[0]] for r in results]}
     if save:
         with _lock:
             d = load_cache()

@@ -26,15 +26,15 @@ def test_candidates_agree_and_cache(F, tmp_path, monkeypatch):
     g = np.random.default_rng(1)
     img = torch.from_numpy(g.integers(0, 256, (300, 200), dtype=np.uint8)).cuda()
     ref = None
-    for tc, th in tune.CANDIDATES:
-        p = F.Plan(300, 200, torch.uint8, 15, "extended", tile_cols=tc, threads=th)
+    for tc, th, fr in tune.CANDIDATES:
+        p = F.Plan(300, 200, torch.uint8, 15, "extended", tile_cols=tc, threads=th, fused_rows=fr)
         p.check()
         out = p.forward(img)
         if ref is None:
             ref = out.clone()
-        assert torch.equal(out, ref), (tc, th)
+        assert torch.equal(out, ref), (tc, th, fr)
     best = tune.tune(300, 200, torch.uint8, 15, "extended", "T", reps=3)
-    assert (best["tile_cols"], best["threads"]) in [tuple(c) for c in tune.CANDIDATES]
+    assert (best["tile_cols"], best["threads"], best["fused_rows"]) in [tuple(c) for c in tune.CANDIDATES]
     p = F.Plan(300, 200, torch.uint8, 15, "extended", tuning="auto")
-    assert p.info.tile_cols == best["tile_cols"]
+    assert p.info.tile_cols == best["tile_cols"] and p.info.fused_rows == best["fused_rows"]
     assert torch.equal(p.forward(img), ref)

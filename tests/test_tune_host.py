@@ -39,7 +39,7 @@ def test_user_cache_wins_over_packaged_table(tmp_path, monkeypatch):
     k = tune.key(1024, 1024, torch.float32, 15, "cyclic", "T")
     packaged = tune.lookup(1024, 1024, torch.float32, 15, "cyclic", "T")
     assert packaged is not None  # shipped with the package
-    tune.save_cache({k: {"tile_cols": 64, "threads": 256, "ms": 1.0}})
+    tune.save_cache({k: {"tile_cols": 64, "threads": 256, "fused_rows": 64, "ms": 1.0}})
     hit = tune.lookup(1024, 1024, torch.float32, 15, "cyclic", "T")
     assert hit["tile_cols"] == 64 and hit["threads"] == 256
 
@@ -61,9 +61,10 @@ def test_packaged_entries_are_candidates():
     table = _packaged()
     assert len(table) >= 40
     for k, v in table.items():
-        assert (v["tile_cols"], v["threads"]) in tune.CANDIDATES, k
+        assert (v["tile_cols"], v["threads"], v["fused_rows"]) in tune.CANDIDATES, k
         # the kept choice is the fastest candidate measured
-        assert v["ms"] == min(c[2] for c in v["candidates"]), k
+        assert v["ms"] == min(c[3] for c in v["candidates"]), k
+        assert len(v["candidates"]) == len(tune.CANDIDATES), k
 
 
 @pytest.mark.parametrize("entry", sorted(_packaged())[::4])
@@ -75,5 +76,5 @@ def test_packaged_choice_builds_a_verified_plan(F, entry):
     boundary, split = entry.split(":")[3], entry.split(":")[4]
     for h, w in ((hb, wb), (hb - 1, wb + 3)):
         p = F.Plan(h, w, dtype, quads, boundary, split=split, tile_cols=v["tile_cols"], threads=v["threads"],
-                   device=-1)
+                   fused_rows=v["fused_rows"], device=-1)
         p.check()
