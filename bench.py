@@ -579,7 +579,11 @@ def measure_c3(args) -> dict:
     mpix = sum(im.size for im in imgs) / 1e6  # the whole batch, over all ranks
     imgs = [imgs[i] for i in parallel.my_shard([im.shape for im in imgs])]  # all of them at world 1
     xs = [torch.from_numpy(im).cuda() for im in imgs]
-    q = BatchQueue(max_jobs=len(xs), max_units=1 << 23)
+    # the plans' launch shape chosen by measurement on this batch (autotuned tiles)
+    from paper_2411_07351_gb300.tune import tune_batch
+
+    tuned = tune_batch(xs, F.FHT_QALL, "cyclic", "T")
+    q = BatchQueue(max_jobs=len(xs), max_units=1 << 23, shape=tuned["shape"])
     plans = [q.plan_for(x, F.FHT_QALL, "cyclic", "T") for x in xs]
     outs = [p.new_output() for p in plans]
     wss = [p.new_workspace() for p in plans]
@@ -634,6 +638,8 @@ def measure_c3(args) -> dict:
             "speedup_vs_plain": t_plain / t_batch, "model_bytes": model,
             "model_gbs_batched": model / (t_batch * 1e-3) / 1e9,
             "gpu_launches": {"plain": sum(_launches(p) for p in plans), "batched": 1},
+            "tuned_shape": {"tile_cols_threads_generic_cols": list(tuned["shape"]),
+                            "candidates_ms": tuned["candidates"]},
             "sharding": "size-balanced shard of the batch per rank, slowest rank's time" if world > 1 else None}
     q.close()
     return line

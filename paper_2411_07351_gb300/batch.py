@@ -33,7 +33,12 @@ assert _JOB_DTYPE.itemsize == ctypes.sizeof(C.fht_job)
 class BatchQueue:
     """One fht_queue_t: device tables for up to max_jobs jobs / max_units units per submit."""
 
-    def __init__(self, device: int | None = None, max_jobs: int = 8192, max_units: int = 1 << 22):
+    def __init__(self, device: int | None = None, max_jobs: int = 8192, max_units: int = 1 << 22,
+                 shape: tuple[int, int, int] | None = None):
+        """`shape` = (tile_cols, threads, generic_cols) of the plans this queue
+        makes (0 = default); None takes the batch defaults above (see
+        ``tune.tune_batch`` for choosing one by measurement)."""
+        self.shape = tuple(shape) if shape is not None else (BATCH_TILE_COLS, BATCH_THREADS, BATCH_GENERIC_COLS)
         self._lib = C.load()
         self.device_index = torch.cuda.current_device() if device is None else int(device)
         h = ctypes.c_void_p()
@@ -47,8 +52,9 @@ class BatchQueue:
         C.check(self._lib.fht_queue_set_wait_limit(self._q, int(seconds * 1e9)), "fht_queue_set_wait_limit")
 
     def plan_for(self, x: torch.Tensor, quads: int, boundary: str, split: str) -> Plan:
+        tc, th, gc = self.shape
         return self.plans.get(x.shape[0], x.shape[1], x.dtype, quads, boundary, split, self.device_index,
-                              tile_cols=BATCH_TILE_COLS, threads=BATCH_THREADS, generic_cols=BATCH_GENERIC_COLS)
+                              tile_cols=tc, threads=th, generic_cols=gc)
 
     def submit(self, images, quads: int = C.FHT_QALL, boundary: str = "cyclic", split: str = "T",
                outs=None, workspaces=None, stream=None, flags=None, tags=None, plans=None):

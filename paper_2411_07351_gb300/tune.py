@@ -145,6 +145,41 @@ def tune(h: int, w: int, dtype=torch.float32, quads: int = C.FHT_QALL, boundary:
     return entry
 
 
+# launch shapes of the plans of a batched launch: (tile_cols, threads, generic_cols)
+BATCH_CANDIDATES = [(64, 0, 0), (96, 0, 0), (128, 0, 0), (192, 256, 32)]
+
+
+def tune_batch(images, quads: int = C.FHT_QALL, boundary: str = "cyclic", split: str = "T", reps: int = 5,
+               candidates=None) -> dict:
+    """Time one persistent batched launch (fht_submit) over `images` with each
+    candidate plan shape and return the fastest, with every candidate's time.
+    The batch's own images are the workload, so the choice fits their sizes."""
+    from .batch import BatchQueue
+
+    results = []
+    for shape in candidates or BATCH_CANDIDATES:
+        q = BatchQueue(max_jobs=len(images), max_units=1 << 23, shape=shape)
+        plans = [q.plan_for(x, quads, boundary, split) for x in images]
+        outs = [p.new_output() for p in plans]
+        wss = [p.new_workspace() for p in plans]
+        for _ in range(2):
+            q.submit(images, quads, boundary, split, outs=outs, workspaces=wss, plans=plans)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            q.submit(images, quads, boundary, split, outs=outs, workspaces=wss, plans=plans)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        results.append((statistics.median(ts), tuple(shape)))
+        q.close()
+        del plans, outs, wss
+    results.sort()
+    return {"shape": results[0][1], "ms": results[0][0], "candidates": [[list(r[1]), r[0]] for r in results]}
+
+
 if __name__ == "__main__":
     import sys
 

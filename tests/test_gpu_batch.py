@@ -204,3 +204,22 @@ def test_batch_register_tiled_plans(F, orc):
         for im, o in zip(imgs, outs):
             assert np.array_equal(o.cpu().numpy(), orc.fht(im.astype(np.int64), 15, b))
     q.close()
+
+
+def test_batch_tuner_picks_a_measured_shape(F, orc):
+    """tune.tune_batch times every candidate plan shape on the batch itself
+    and returns the fastest; a queue with that shape gives the oracle's result."""
+    from paper_2411_07351_gb300 import tune
+    from paper_2411_07351_gb300.batch import BatchQueue
+
+    imgs = inputs.c3_batch(seed=5, count=24)
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    best = tune.tune_batch(xs, 15, "cyclic", "T", reps=2)
+    assert best["shape"] in [tuple(c) for c in tune.BATCH_CANDIDATES]
+    assert best["ms"] == min(c[1] for c in best["candidates"])
+    q = BatchQueue(max_jobs=len(xs), shape=best["shape"])
+    outs, _, _ = q.submit(xs, 15, "cyclic")
+    torch.cuda.synchronize()
+    for im, o in zip(imgs, outs):
+        assert np.array_equal(o.cpu().numpy(), orc.fht(im.astype(np.int64), 15, orc.CYCLIC))
+    q.close()
