@@ -95,7 +95,8 @@ typedef struct {
                           the lower chunks' top nodes are summed first and become single parts of the
                           chunk above.  A value >= the spine length gives one spine launch. */
   int32_t generic_cols;/* column tile of the subtrees under 64 rows that take the generic shared-memory
-                          path (multiple of 32; default: half of tile_cols rounded down to 32, at least 32) */
+                          path (multiple of 32; default: 128 with tile_cols 192 and 256 threads, else half
+                          of tile_cols rounded down to 32, at least 32) */
   int32_t reserved;
 } fht_tuning_t;
 
