@@ -136,22 +136,12 @@ __global__ void __launch_bounds__(512, 1) adj_fused_kernel(AdjFusedParams p) {
 
   // ---- leaf gradients: window columns [m - 1, TZin) are view columns [z0, z0 + TW) ----
   AccT* __restrict__ gq = ws + Q.grad_off;
-  if (!Q.transpose) {
-    for (int32_t r = warp; r < m; r += nwarps) {
-      const AccT* s = src + (size_t)r * p.RP + p.PADL + (m - 1);
-      AccT* o = gq + (int64_t)(it.a + r) * p.w;
-      for (int32_t jj = lane; jj < p.TW; jj += 32) {
-        const int32_t z = z0 + jj;
-        if (z < Q.L) o[Q.flip ? Q.L - 1 - z : z] = s[jj];
-      }
-    }
-  } else {
-    for (int32_t jj = warp; jj < p.TW; jj += nwarps) {
-      const int32_t z = z0 + jj;
-      if (z >= Q.L) continue;
-      AccT* o = gq + (int64_t)(Q.flip ? Q.L - 1 - z : z) * p.w + it.a;
-      for (int32_t r = lane; r < m; r += 32) o[r] = src[(size_t)r * p.RP + p.PADL + (m - 1) + jj];
-    }
+  const int64_t gp = grad_pitch(Q.L);
+  for (int32_t r = warp; r < m; r += nwarps) {
+    const AccT* s = src + (size_t)r * p.RP + p.PADL + (m - 1);
+    AccT* o = gq + (int64_t)(it.a + r) * gp + z0;
+    for (int32_t jj = lane; jj < p.TW; jj += 32)
+      if (z0 + jj < Q.L) o[jj] = s[jj];
   }
 }
 
@@ -164,7 +154,9 @@ __global__ void __launch_bounds__(512, 1) adj_fused_kernel(AdjFusedParams p) {
 // the forward block transform of g~ read at slope y.  One CTA = one block x
 // one tile of kVTile view columns: the 64 gradient rows are staged reversed,
 // merged exactly as the forward merges its window, and stored back reversed
-// into the quadrant's view gradient.
+// into the quadrant's view gradient (a thread's four tile columns j .. j + 3
+// are the view columns z0 + kVTile - 4 - j .. z0 + kVTile - 1 - j, one
+// 16-byte aligned run of a row).
 template <typename AccT>
 __device__ __forceinline__ void adj_stage_rev(const AdjFusedParams& p, const FusedItem& it, const QuadDesc& Q,
                                               int32_t z0, AccT* S) {
@@ -218,25 +210,20 @@ __global__ void __launch_bounds__(kVThreads, 3) adj_block_kernel(AdjFusedParams 
   adj_stage_rev<AccT>(p, it, Q, z0, S);
   __syncwarp();
   AccT* __restrict__ gq = static_cast<AccT*>(p.ws) + Q.grad_off;
+  const int64_t gp = grad_pitch(Q.L);
   v_merge_groups<AccT>(S, 6, kVTile, [] {
     __syncthreads();
     return true;
   }, [&](int32_t row0, int32_t j, const auto& o) {
     constexpr int R = sizeof(o) / sizeof(o[0]);
+    // z0, kVTile and j are multiples of 4, so zs is; zs < L keeps the run
+    // inside the row's grad_pitch(L) elements (a run past L writes slack)
+    const int32_t zs = z0 + kVTile - 4 - j;
+    if (zs >= Q.L) return;
 #pragma unroll
-    for (int x = 0; x < 4; x++) {
-      const int32_t z = z0 + kVTile - 1 - (j + x);  // view column of tile column j + x
-      if (z >= Q.L) continue;
-      const int32_t zz = Q.flip ? Q.L - 1 - z : z;
-#pragma unroll
-      for (int i = 0; i < R; i++) {
-        const int32_t r = it.a + row0 + i;  // view row
-        if (Q.transpose) {
-          gq[(int64_t)zz * p.w + r] = o[i][x];
-        } else {
-          gq[(int64_t)r * p.w + zz] = o[i][x];
-        }
-      }
+    for (int i = 0; i < R; i++) {
+      const AccT v[4] = {o[i][3], o[i][2], o[i][1], o[i][0]};
+      sts4<AccT>(gq + (int64_t)(it.a + row0 + i) * gp + zs, v);
     }
   });
 }
@@ -347,17 +334,62 @@ __global__ void __launch_bounds__(256) adj_upper_kernel(const AdjRow* __restrict
   }
 }
 
+// The quadrants' view gradients summed into the image gradient.  Quadrant q
+// holds gV_q[r][z] (n rows of pitch grad_pitch(L)); image element (y, x) is
+// view element (y, x~) of the untransposed quadrants and (x, y~) of the
+// transposed ones, with ~ the column reversal of the leftward quadrants.  One
+// CTA = one 32 x 32 image tile: untransposed views are read along image rows,
+// transposed ones along image columns (coalesced view rows) and turned
+// through shared memory.  Every element adds its quadrants in order q = 0..3.
+struct AdjSumQuad {
+  int64_t off;  // element offset of the view gradient in the workspace
+  int32_t pitch, L, transpose, flip;
+};
+struct AdjSumParams {
+  AdjSumQuad q[4];
+  int32_t nq, h, w;
+  int64_t pitch;  // elements between image rows of gin
+};
+
 template <typename AccT>
-__global__ void adj_sum_kernel(const AccT* __restrict__ ws, int64_t g0, int64_t g1, int64_t g2, int64_t g3,
-                               int32_t nq, int32_t h, int32_t w, AccT* __restrict__ gin, int64_t pitch) {
-  const int64_t total = (int64_t)h * w;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    AccT v = ws[g0 + i];
-    if (nq > 1) v += ws[g1 + i];
-    if (nq > 2) v += ws[g2 + i];
-    if (nq > 3) v += ws[g3 + i];
-    const int64_t y = i / w, x = i - y * w;
-    gin[y * pitch + x] = v;
+__global__ void __launch_bounds__(256) adj_sum_kernel(const AccT* __restrict__ ws, AdjSumParams sp,
+                                                      AccT* __restrict__ gin) {
+  __shared__ AccT T[32][33];
+  const int32_t tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int32_t x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, x = x0 + tx;
+  AccT acc[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
+  for (int32_t k = 0; k < sp.nq; k++) {
+    const AdjSumQuad Q = sp.q[k];
+    const AccT* __restrict__ g = ws + Q.off;
+    if (!Q.transpose) {
+      if (x < sp.w) {
+        const int32_t z = Q.flip ? Q.L - 1 - x : x;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          const int32_t y = y0 + ty + 8 * i;
+          if (y < sp.h) acc[i] += g[(int64_t)y * Q.pitch + z];
+        }
+      }
+    } else {
+      // T[a][b] = view row x0 + a at the column of image row y0 + b
+      const int32_t yb = y0 + tx;
+      const int32_t z = Q.flip ? Q.L - 1 - yb : yb;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const int32_t xr = x0 + ty + 8 * i;
+        T[ty + 8 * i][tx] = (xr < sp.w && yb < sp.h) ? g[(int64_t)xr * Q.pitch + z] : AccT(0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 4; i++) acc[i] += T[tx][ty + 8 * i];
+      __syncthreads();
+    }
+  }
+  if (x >= sp.w) return;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int32_t y = y0 + ty + 8 * i;
+    if (y < sp.h) gin[(int64_t)y * sp.pitch + x] = acc[i];
   }
 }
 
@@ -426,14 +458,17 @@ static cudaError_t launch_adjoint_t(const DevicePlan& D, const void* gout, void*
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }
-  int64_t g[4] = {0, 0, 0, 0};
-  int32_t nq = 0;
-  for (int q = 0; q < 4; q++)
-    if (P.cfg.quads & (1u << q)) g[nq++] = P.quad[q].grad_off;
-  const int64_t total = (int64_t)P.cfg.h * P.cfg.w;
-  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
-  adj_sum_kernel<AccT><<<blocks, 256, 0, st>>>(wsa, g[0], g[1], g[2], g[3], nq, P.cfg.h, P.cfg.w,
-                                               static_cast<AccT*>(gin), gin_pitch);
+  AdjSumParams sp{};
+  for (int q = 0; q < 4; q++) {
+    if (!(P.cfg.quads & (1u << q))) continue;
+    const QuadDesc& Q = P.quad[q];
+    sp.q[sp.nq++] = AdjSumQuad{Q.grad_off, grad_pitch(Q.L), Q.L, Q.transpose, Q.flip};
+  }
+  sp.h = P.cfg.h;
+  sp.w = P.cfg.w;
+  sp.pitch = gin_pitch;
+  const dim3 grid((unsigned)((P.cfg.w + 31) / 32), (unsigned)((P.cfg.h + 31) / 32));
+  adj_sum_kernel<AccT><<<grid, 256, 0, st>>>(wsa, sp, static_cast<AccT*>(gin));
   return cudaGetLastError();
 }
 

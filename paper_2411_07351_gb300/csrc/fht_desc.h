@@ -20,8 +20,16 @@ struct QuadDesc {
   int32_t sigma;      // +1 or -1
   int32_t kappa;      // see above
   int64_t out_off;    // element offset of the quadrant in the output
-  int64_t grad_off;   // adjoint: workspace offset of this quadrant's h x w image gradient
+  int64_t grad_off;   // adjoint: workspace offset of this quadrant's view gradient, n rows of
+                      // grad_pitch(L) elements (columns [L, grad_pitch(L)) are slack)
 };
+
+// Row pitch of a quadrant's view gradient: L rounded up to 4 elements, so that
+// every row starts 16-byte aligned for 4-byte accumulators.
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline int32_t grad_pitch(int32_t L) { return (L + 3) & ~3; }
 
 // A subtree of at most F rows, merged entirely in shared memory.
 struct FusedItem {

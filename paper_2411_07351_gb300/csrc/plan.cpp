@@ -803,12 +803,13 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
 
   P.out_elems = out_off;
   P.ws_bytes = kWsHeader + (size_t)ws_off * acc;
-  // adjoint: one h x w gradient image per quadrant after the forward buffers
-  int64_t goff = ws_off;
+  // adjoint: one view gradient per quadrant (n rows of grad_pitch(L)) after
+  // the forward buffers, each starting 16-byte aligned
+  int64_t goff = (ws_off + 3) & ~(int64_t)3;
   for (int q = 0; q < 4; q++) {
     if (!(cfg.quads & (1u << q))) continue;
     P.quad[q].grad_off = goff;
-    goff += (int64_t)cfg.h * cfg.w;
+    goff += (int64_t)P.quad[q].n * grad_pitch(P.quad[q].L);
   }
   P.adj_ws_bytes = kWsHeader + (size_t)goff * acc;
   // adjoint passes: highest tree height first

@@ -260,12 +260,20 @@ std::string check_plan(const HostPlan& P, const FusedGeometry& g, int32_t adj_rp
   // ---- adjoint ----
   if (!P.has_adjoint) return "";
   const int64_t adj_elems = (int64_t)((P.adj_ws_bytes - kWsHeader) / P.acc_size);
-  const int64_t img = (int64_t)P.cfg.h * P.cfg.w;
   for (int q = 0; q < 4; q++) {
     if (!(P.cfg.quads & (1u << q))) continue;
-    // gradient images sit after the forward buffers
-    if (P.quad[q].grad_off < ws_elems) return "adjoint gradient image overlaps the forward buffers";
-    if (P.quad[q].grad_off + img > adj_elems) return "adjoint gradient image outside the workspace";
+    // view gradients sit after the forward buffers, 16-byte aligned rows
+    const QuadDesc& Q = P.quad[q];
+    const int64_t img = (int64_t)Q.n * grad_pitch(Q.L);
+    if (Q.grad_off < ws_elems) return "adjoint gradient image overlaps the forward buffers";
+    if (Q.grad_off + img > adj_elems) return "adjoint gradient image outside the workspace";
+    if (Q.grad_off % 4 != 0) return "adjoint gradient image not 4-element aligned";
+    if ((int64_t)Q.n * Q.L != (int64_t)P.cfg.h * P.cfg.w) return "adjoint gradient view is not the image's size";
+    for (int r = 0; r < q; r++) {
+      if (!(P.cfg.quads & (1u << r))) continue;
+      const int64_t o = P.quad[r].grad_off, e = o + (int64_t)P.quad[r].n * grad_pitch(P.quad[r].L);
+      if (Q.grad_off < e && o < Q.grad_off + img) return "adjoint gradient images overlap";
+    }
   }
   for (size_t k = 0; k < P.fused.size(); k++) {
     const FusedItem& it = P.fused[k];

@@ -361,8 +361,8 @@ def _adjoint_tables(F, plan):
 
 def _execute_adjoint(F, plan, gout):
     """The adjoint schedule from the tables: per-height gather passes (highest
-    first), then every fused subtree's levels in reverse, then the sum of the
-    quadrants' image gradients."""
+    first), then every fused subtree's levels in reverse into the quadrants'
+    view gradients, then their sum mapped back onto the image."""
     T = _adjoint_tables(F, plan)
     h, w = plan.h, plan.w
     ws = np.zeros((plan.adjoint_workspace_bytes - 256) // 4, dtype=np.int64)
@@ -407,18 +407,20 @@ def _execute_adjoint(F, plan, gout):
                     nxt[k, s:] += cur[op["top"], : len(x) - s]  # g[k][j] += g'[top][j - s]
             cur = nxt
         z = np.arange(L)
-        zz = L - 1 - z if Q["flip"] else z
+        gp = (L + 3) // 4 * 4  # view gradient rows: L elements padded to a multiple of 4
         for r in range(m):
-            leaf = cur[r, z + m - 1]
-            if Q["transpose"]:
-                ws[Q["grad_off"] + zz * w + it["a"] + r] = leaf
-            else:
-                ws[Q["grad_off"] + (it["a"] + r) * w + zz] = leaf
+            ws[Q["grad_off"] + (it["a"] + r) * gp + z] = cur[r, z + m - 1]
     gin = np.zeros((h, w), dtype=np.int64)
     for q in range(4):
         if plan.quads & (1 << q):
-            off = int(T["quads"][q]["grad_off"])
-            gin += ws[off: off + h * w].reshape(h, w)
+            Q = T["quads"][q]
+            off, n, L = int(Q["grad_off"]), int(Q["n"]), int(Q["L"])
+            gp = (L + 3) // 4 * 4
+            assert off % 4 == 0
+            g = ws[off: off + n * gp].reshape(n, gp)[:, :L]  # view gradient gV[r][z]
+            if Q["flip"]:
+                g = g[:, ::-1]
+            gin += g.T if Q["transpose"] else g
     return gin
 
 
