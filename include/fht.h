@@ -258,8 +258,17 @@ typedef struct {
 fht_status fht_queue_create(fht_queue_t* q, int device, int32_t max_jobs, int64_t max_units);
 fht_status fht_queue_set_wait_limit(fht_queue_t q, int64_t wait_ns);
 /* Enqueue one persistent launch over all jobs on `stream` (cudaStream_t).
- * FHT_ERR_BUSY when the jobs or their units exceed the queue's capacity. */
+ * FHT_ERR_BUSY when the jobs or their units exceed the queue's capacity.
+ * The job tables are staged in the queue's pinned host buffers and copied in
+ * stream order, so a submit first waits on the host until the previous
+ * submit's copies have run, which is after every launch queued before them
+ * on that stream (see fht_queue_ready). */
 fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* stream);
+/* Non-blocking: *ready = 1 when the queue's staging buffers are free, so
+ * that fht_submit will not wait on the host; 0 while the previous submit's
+ * table copies are still queued behind earlier work.  A serving loop that
+ * submits only to ready queues never stalls on a busy stream. */
+fht_status fht_queue_ready(fht_queue_t q, int32_t* ready);
 /* Non-blocking: copies up to `cap` tags of finished jobs.  Each job is
  * reported once, as soon as its own last unit has finished (the kernel sets
  * the job's host-mapped completion flag), so early jobs of a batch are seen

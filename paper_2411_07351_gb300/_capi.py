@@ -78,6 +78,7 @@ SIGNATURES = {
     "fht_submit": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(fht_job), _vp]),
     "fht_queue_poll": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), _i32, ctypes.POINTER(_i32)]),
     "fht_queue_status": (ctypes.c_int, [_vp, _vp]),
+    "fht_queue_ready": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "fht_queue_reset_status": (ctypes.c_int, [_vp, _vp]),
     "fht_queue_destroy": (ctypes.c_int, [_vp]),
     "fht_pipe_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, _i32, _i32]),

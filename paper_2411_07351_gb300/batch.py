@@ -89,6 +89,13 @@ class BatchQueue:
         self._keep = [images, outs, workspaces, plans]
         return outs, plans, workspaces
 
+    def ready(self) -> bool:
+        """True when a submit would not wait on the host for this queue's
+        staging buffers (the previous submit's table copies have run)."""
+        r = ctypes.c_int32()
+        C.check(self._lib.fht_queue_ready(self._q, ctypes.byref(r)), "fht_queue_ready")
+        return bool(r.value)
+
     def status(self, stream=None) -> int:
         s = stream if stream is not None else torch.cuda.current_stream(torch.device("cuda", self.device_index))
         return int(self._lib.fht_queue_status(self._q, int(s.cuda_stream)))

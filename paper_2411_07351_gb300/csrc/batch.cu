@@ -500,6 +500,22 @@ fht_status fht_submit(fht_queue_t q, int32_t njobs, const fht_job* jobs, void* s
   return FHT_OK;
 }
 
+fht_status fht_queue_ready(fht_queue_t q, int32_t* ready) {
+  if (!q || !ready) return fht_capi_fail(FHT_ERR_INVALID, "fht_queue_ready: NULL argument");
+  *ready = 1;
+  if (!q->staged_pending) return FHT_OK;
+  QueueDeviceGuard g(q->device);
+  if (!g.ok) return fht_capi_fail(FHT_ERR_CUDA, "fht_queue_ready: cannot select the queue's device");
+  const cudaError_t e = cudaEventQuery(q->staged);
+  if (e == cudaErrorNotReady) {
+    *ready = 0;
+    return FHT_OK;
+  }
+  if (e != cudaSuccess) return fht_capi_fail(FHT_ERR_CUDA, std::string("fht_queue_ready: ") + cudaGetErrorString(e));
+  q->staged_pending = false;
+  return FHT_OK;
+}
+
 fht_status fht_queue_poll(fht_queue_t q, uint64_t* done_tags, int32_t cap, int32_t* ndone) {
   if (!q || !ndone || (cap > 0 && !done_tags)) return fht_capi_fail(FHT_ERR_INVALID, "fht_queue_poll: bad argument");
   *ndone = 0;

@@ -6,7 +6,9 @@ only while the device-memory budget (output + workspace of every admitted,
 unfinished request) has room, and on every turn of its loop submits the
 admitted small requests that are not yet running as ONE persistent batched
 launch (fht_submit) on the least busy of its streams (each stream holds up to
-``max_inflight`` launches); a large request (at least ``plain_pixels``)
+``max_inflight`` launches, and a batched launch goes only to a stream whose
+queue can take it without the host waiting: the loop itself never blocks on
+the device); a large request (at least ``plain_pixels``)
 fills the GPU by itself and runs the per-image kernels instead.  Batches on
 different streams overlap on the device; a request that arrives while others
 run joins the next batch as soon as memory and a stream are free.  Plans are
@@ -235,17 +237,29 @@ class Server:
                 still.append(b)
         self.running = still
 
-    def _pick_stream(self):
-        k = min(range(len(self.streams)), key=lambda i: self.inflight[i])
-        return k if self.inflight[k] < self.max_inflight else None
+    def _pick_stream(self, batched: bool):
+        """The least-loaded stream with room for another launch; for a batched
+        launch also one whose queue can take a submit without the host waiting
+        (its previous table copies have run).  None: launch nothing this turn,
+        the loop goes on retiring, polling plans and admitting."""
+        best = None
+        for k in range(len(self.streams)):
+            if self.inflight[k] >= self.max_inflight:
+                continue
+            if best is not None and self.inflight[k] >= self.inflight[best]:
+                continue
+            if batched and not self.queues[k].ready():
+                continue
+            best = k
+        return best
 
     def _launch(self, now_fn=None):
         while self.admitted:
-            slot = self._pick_stream()
+            head = self.admitted[0]
+            slot = self._pick_stream(batched=head.image.numel() < self.plain_pixels)
             if slot is None:
                 return
             s = self.streams[slot]
-            head = self.admitted[0]
             if head.image.numel() >= self.plain_pixels:
                 # a large request fills the GPU by itself: the per-image kernels,
                 # no persistent batch

@@ -133,6 +133,27 @@ def test_batch_poll_tags(F, queue):
     assert sorted(got) == [21, 22, 23, 24]
 
 
+def test_queue_ready_tracks_the_staging_copies(F, queue):
+    # fht_queue_ready: 0 while a submit's table copies wait behind earlier
+    # work on the stream, 1 once they have run; a submit to a ready queue
+    # does not wait on the host
+    torch.cuda.synchronize()
+    assert queue.ready()
+    s = torch.cuda.Stream()
+    xs = _edge_maps(5, 3)
+    with torch.cuda.stream(s):
+        torch.cuda._sleep(50_000_000)  # tens of milliseconds of device work ahead of the copies
+        queue.submit(xs, 15, "cyclic", stream=s)
+    assert not queue.ready()
+    s.synchronize()
+    assert queue.ready()
+    with torch.cuda.stream(s):
+        outs, plans, _ = queue.submit(xs, 15, "cyclic", stream=s)
+    s.synchronize()
+    for x, o, p in zip(xs, outs, plans):
+        assert torch.equal(o, p.forward(x))
+
+
 def test_batch_graph_replay(F, queue):
     """A fixed batch captured in a CUDA graph replays to the same results."""
     xs = _edge_maps(10, 16)

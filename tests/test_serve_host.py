@@ -168,3 +168,33 @@ def test_native_builder_pool_host_plans():
     assert pool.pending() == (0, 0)
     pool.submit(300, 300, torch.uint8, 15, "extended", "T", device=-1)
     pool.close()  # finishes the queued build and destroys the unclaimed plan
+
+
+class _ReadyQueue:
+    def __init__(self, ready):
+        self._ready = ready
+        self.asked = 0
+
+    def ready(self):
+        self.asked += 1
+        return self._ready
+
+
+def test_batched_launch_only_on_a_queue_that_does_not_block():
+    # A batched submit to a queue whose previous table copies are still queued
+    # behind earlier launches would make the host wait; the loop picks the
+    # least-loaded stream among those with room AND a ready queue, and launches
+    # nothing this turn when there is none.  Plain launches need no queue.
+    s = serve.Server.__new__(serve.Server)
+    s.streams = [None] * 4
+    s.max_inflight = 2
+    s.inflight = [0, 1, 2, 0]
+    s.queues = [_ReadyQueue(False), _ReadyQueue(True), _ReadyQueue(True), _ReadyQueue(True)]
+    assert s._pick_stream(batched=False) == 0
+    assert s._pick_stream(batched=True) == 3
+    s.inflight = [0, 1, 2, 2]
+    assert s._pick_stream(batched=True) == 1
+    s.queues[1]._ready = False
+    assert s._pick_stream(batched=True) is None
+    assert s._pick_stream(batched=False) == 0
+    assert s.queues[2].asked == 0  # a full stream's queue is not even asked
