@@ -291,7 +291,9 @@ fht_status fht_pattern_errors(int32_t n_lo, int32_t n_hi, fht_split split, int64
 
 /* Host-side verification of a plan: walks every table entry and checks that
  * each input, workspace, output and shared-memory index the kernels derive
- * from it lies inside its buffer.  No device access; works on host-only plans.
+ * from it lies inside its buffer.  Works on host-only plans; on a device plan
+ * its first call copies the tables the host does not keep back from the
+ * device (see fht_plan_table), nothing else touches the device.
  * FHT_OK, or FHT_ERR_INVALID with the first violation in fht_last_error(). */
 fht_status fht_plan_check(fht_plan_t plan);
 
@@ -305,8 +307,12 @@ fht_status fht_plan_check(fht_plan_t plan);
  * stable interface.  Offsets in the tables are element offsets into the
  * output, or into the workspace after its 256-byte header.  The adjoint
  * tables are empty until the plan has them (with_adjoint = 1, or after a
- * first fht_adjoint).
- * FHT_ERR_INVALID for a NULL argument or an unknown table. */
+ * first fht_adjoint).  A plan built for a device keeps on the host only the
+ * tables its launches read there; the first fht_plan_table (or
+ * fht_plan_check) on it copies the others back from the device (a
+ * synchronous copy) and keeps them for the plan's lifetime.
+ * FHT_ERR_INVALID for a NULL argument or an unknown table; FHT_ERR_CUDA if
+ * that copy fails. */
 typedef enum {
   FHT_TABLE_QUADS = 0,        /* QuadDesc[4] (entries of absent quadrants are unused) */
   FHT_TABLE_FUSED = 1,        /* FusedItem: fused subtrees (64-row blocks and the rest) */

@@ -16,7 +16,15 @@ struct fht_plan_s {
   fht::HostPlan host;
   fht::DevicePlan dev;
   void* d_tables = nullptr;  // one device allocation holding every table of the plan
-  std::mutex mu;             // serialises the lazy adjoint build
+  std::mutex mu;             // serialises the lazy adjoint build and the host-table restore
+  // Once uploaded, a device plan keeps on the host only what launches read
+  // there (work lists and pass boundaries): the merge programs, row jobs,
+  // spine and adjoint tables live on the device alone, so that a server
+  // holding thousands of plans does not hold their tables twice.  Their
+  // lengths are kept for fht_plan_table and fht_plan_check, which copy them
+  // back on demand.
+  bool host_released = false;
+  int64_t released[10] = {};
 };
 
 namespace {
@@ -133,6 +141,57 @@ void free_dev(fht_plan_s* p) {
   d.spine_grps = nullptr;
 }
 
+template <typename T>
+void drop_table(std::vector<T>& v, int64_t& n) {
+  n = (int64_t)v.size();
+  std::vector<T>().swap(v);
+}
+
+void release_host_tables(fht_plan_s* p) {
+  fht::HostPlan& h = p->host;
+  int64_t* n = p->released;
+  drop_table(h.ops, n[0]);
+  drop_table(h.rows, n[1]);
+  drop_table(h.spine_rows, n[2]);
+  drop_table(h.spine_terms, n[3]);
+  drop_table(h.spine_segs, n[4]);
+  drop_table(h.spine_grps, n[5]);
+  drop_table(h.arows, n[6]);
+  drop_table(h.aterms, n[7]);
+  drop_table(h.aptr, n[8]);
+  drop_table(h.aops, n[9]);
+  p->host_released = true;
+}
+
+template <typename T>
+cudaError_t fetch_table(std::vector<T>& v, const T* d, int64_t n) {
+  v.resize((size_t)n);
+  if (n == 0) return cudaSuccess;
+  return cudaMemcpy(v.data(), d, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost);
+}
+
+// The released host tables copied back from the device (caller holds p->mu).
+cudaError_t restore_host_tables(fht_plan_s* p) {
+  if (!p->host_released) return cudaSuccess;
+  DeviceGuard g(p->dev.device);
+  if (!g.ok) return cudaErrorInvalidDevice;
+  fht::HostPlan& h = p->host;
+  const fht::DevicePlan& d = p->dev;
+  const int64_t* n = p->released;
+  cudaError_t e;
+  if ((e = fetch_table(h.ops, d.ops, n[0])) != cudaSuccess || (e = fetch_table(h.rows, d.rows, n[1])) != cudaSuccess ||
+      (e = fetch_table(h.spine_rows, d.spine_rows, n[2])) != cudaSuccess ||
+      (e = fetch_table(h.spine_terms, d.spine_terms, n[3])) != cudaSuccess ||
+      (e = fetch_table(h.spine_segs, d.spine_segs, n[4])) != cudaSuccess ||
+      (e = fetch_table(h.spine_grps, d.spine_grps, n[5])) != cudaSuccess ||
+      (e = fetch_table(h.arows, d.arows, n[6])) != cudaSuccess ||
+      (e = fetch_table(h.aterms, d.aterms, n[7])) != cudaSuccess ||
+      (e = fetch_table(h.aptr, d.aptr, n[8])) != cudaSuccess || (e = fetch_table(h.aops, d.aops, n[9])) != cudaSuccess)
+    return e;
+  p->host_released = false;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 // Shared with noalloc.cu.
@@ -214,6 +273,7 @@ fht_status fht_plan(fht_plan_t* out, int32_t h, int32_t w, fht_dtype dtype, uint
       if (e == cudaErrorMemoryAllocation) return fail(FHT_ERR_NOMEM, "fht_plan: device allocation failed");
       return cuda_fail(e, "fht_plan: upload");
     }
+    release_host_tables(p);
   }
   *out = p;
   return FHT_OK;
@@ -321,9 +381,11 @@ fht_status fht_adjoint(fht_plan_t plan, const void* d_gout, void* d_gin, int64_t
       if (!err.empty()) return fail(FHT_ERR_INVALID, "fht_adjoint: " + err);
       free_dev(plan);
       plan->host = std::move(hp);
+      plan->host_released = false;
       fht::fused_geometry(plan->host, plan->dev.geo);
       cudaError_t e = upload_tables(plan);
       if (e != cudaSuccess) return cuda_fail(e, "fht_adjoint: table upload");
+      release_host_tables(plan);
     }
   }
   if (ws_bytes < P.adj_ws_bytes)
@@ -336,6 +398,8 @@ fht_status fht_adjoint(fht_plan_t plan, const void* d_gout, void* d_gin, int64_t
 
 fht_status fht_plan_check(fht_plan_t plan) {
   if (!plan) return fail(FHT_ERR_INVALID, "fht_plan_check: plan is NULL");
+  std::lock_guard<std::mutex> lock(plan->mu);
+  if (cudaError_t e = restore_host_tables(plan); e != cudaSuccess) return cuda_fail(e, "fht_plan_check: table copy");
   int32_t arp = 0, apad = 0;
   size_t asmem = 0;
   fht::adjoint_geometry(plan->host, arp, apad, asmem);
@@ -346,6 +410,10 @@ fht_status fht_plan_check(fht_plan_t plan) {
 
 fht_status fht_plan_table(fht_plan_t plan, fht_table table, const void** data, int64_t* count, int32_t* elem_size) {
   if (!plan || !data || !count || !elem_size) return fail(FHT_ERR_INVALID, "fht_plan_table: NULL argument");
+  {
+    std::lock_guard<std::mutex> lock(plan->mu);
+    if (cudaError_t e = restore_host_tables(plan); e != cudaSuccess) return cuda_fail(e, "fht_plan_table: table copy");
+  }
   const fht::HostPlan& P = plan->host;
   auto give = [&](const auto& v) {
     *data = v.data();

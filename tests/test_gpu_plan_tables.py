@@ -1,0 +1,58 @@
+"""Device plans keep on the host only the tables their launches read there;
+fht_plan_table and fht_plan_check copy the rest back from the device.  The
+copies must equal the tables of a host-only plan of the same configuration,
+before and after the lazy adjoint build, and the plans must still run."""
+import ctypes
+
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_07351_gb300 import build as B
+
+    B.build()
+    import paper_2411_07351_gb300 as F
+
+    return F
+
+
+def _tables(F, plan):
+    from paper_2411_07351_gb300 import _capi as C
+
+    lib, out = C.load(), {}
+    for k in range(14):
+        data, count, esz = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int32()
+        C.check(lib.fht_plan_table(plan._h, k, ctypes.byref(data), ctypes.byref(count), ctypes.byref(esz)),
+                "fht_plan_table")
+        n = count.value * esz.value
+        out[k] = ctypes.string_at(data.value, n) if n else b""
+    return out
+
+
+@pytest.mark.parametrize("h,w,boundary,dtype", [(131, 45, "extended", torch.uint8), (300, 700, "cyclic", torch.float32),
+                                                (1000, 257, "extended", torch.float32)])
+def test_device_plan_tables_come_back_equal(F, h, w, boundary, dtype):
+    dev = F.Plan(h, w, dtype, F.FHT_QALL, boundary)
+    host = F.Plan(h, w, dtype, F.FHT_QALL, boundary, device=-1)
+    x = (torch.rand(h, w, device="cuda") * 100).to(dtype)
+    ref = dev.forward(x)
+    assert _tables(F, dev) == _tables(F, host)
+    dev.check()
+    assert torch.equal(dev.forward(x), ref)
+    # the lazy adjoint build replaces the tables; they are released and restored again
+    out = dev.forward(x)
+    gin = torch.empty((h, w), dtype=dev.out_dtype, device="cuda")
+    ws = dev.new_workspace(adjoint=True)
+    dev.adjoint(out, gin, ws)
+    host_adj = F.Plan(h, w, dtype, F.FHT_QALL, boundary, device=-1, with_adjoint=True)
+    assert _tables(F, dev) == _tables(F, host_adj)
+    dev.check()
+    gin2 = torch.empty_like(gin)
+    dev.adjoint(out, gin2, ws)
+    assert torch.equal(gin, gin2)
