@@ -141,30 +141,39 @@ void free_dev(fht_plan_s* p) {
   d.spine_grps = nullptr;
 }
 
+// A table is released only where the device holds a copy (n = its length);
+// a table that was not uploaded (the adjoint tables of a forward-only plan)
+// stays on the host (n = -1).
 template <typename T>
-void drop_table(std::vector<T>& v, int64_t& n) {
+void drop_table(std::vector<T>& v, const T* d, int64_t& n) {
+  if (!d) {
+    n = -1;
+    return;
+  }
   n = (int64_t)v.size();
   std::vector<T>().swap(v);
 }
 
 void release_host_tables(fht_plan_s* p) {
   fht::HostPlan& h = p->host;
+  const fht::DevicePlan& d = p->dev;
   int64_t* n = p->released;
-  drop_table(h.ops, n[0]);
-  drop_table(h.rows, n[1]);
-  drop_table(h.spine_rows, n[2]);
-  drop_table(h.spine_terms, n[3]);
-  drop_table(h.spine_segs, n[4]);
-  drop_table(h.spine_grps, n[5]);
-  drop_table(h.arows, n[6]);
-  drop_table(h.aterms, n[7]);
-  drop_table(h.aptr, n[8]);
-  drop_table(h.aops, n[9]);
+  drop_table(h.ops, d.ops, n[0]);
+  drop_table(h.rows, d.rows, n[1]);
+  drop_table(h.spine_rows, d.spine_rows, n[2]);
+  drop_table(h.spine_terms, d.spine_terms, n[3]);
+  drop_table(h.spine_segs, d.spine_segs, n[4]);
+  drop_table(h.spine_grps, d.spine_grps, n[5]);
+  drop_table(h.arows, d.arows, n[6]);
+  drop_table(h.aterms, d.aterms, n[7]);
+  drop_table(h.aptr, d.aptr, n[8]);
+  drop_table(h.aops, d.aops, n[9]);
   p->host_released = true;
 }
 
 template <typename T>
 cudaError_t fetch_table(std::vector<T>& v, const T* d, int64_t n) {
+  if (n < 0) return cudaSuccess;  // kept on the host
   v.resize((size_t)n);
   if (n == 0) return cudaSuccess;
   return cudaMemcpy(v.data(), d, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost);
