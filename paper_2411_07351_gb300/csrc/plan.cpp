@@ -587,7 +587,7 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
               stack.pop_back();
               const TreeNode& nd = tr.nodes[z.v];
               if (nd.m <= kMaxBandRows) {
-                SpineTerm st;
+                SpineTerm st{};
                 st.row = node_row(z.v, z.t);
                 st.wpart = node_w(z.v);
                 st.off = cfg.ext ? (int32_t)(z.off + nd.m - N.m) : (int32_t)z.off;
@@ -631,7 +631,7 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
             int64_t off = 0;  // accumulated shift in window (x) coordinates
             auto add_term = [&](int32_t pi, int32_t row) {
               const TreeNode& pt = tr.nodes[pi];
-              SpineTerm st;
+              SpineTerm st{};
               st.row = node_row(pi, row);
               st.wpart = node_w(pi);
               st.off = cfg.ext ? (int32_t)(off + pt.m - N.m) : (int32_t)off;  // off kept reduced mod W
