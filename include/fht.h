@@ -332,7 +332,11 @@ typedef enum {
 
 fht_status fht_plan_table(fht_plan_t plan, fht_table table, const void** data, int64_t* count, int32_t* elem_size);
 
-/* Release a plan and its device tables.  NULL is accepted. */
+/* Release a plan and its device tables.  NULL is accepted.  Device tables
+ * live in ranges of large per-device chunks that the library allocates once
+ * and keeps until the process exits (no driver allocation per plan); the
+ * destroy waits for the device's outstanding work, as a cudaFree would, and
+ * returns the range for reuse by later plans. */
 fht_status fht_plan_destroy(fht_plan_t plan);
 
 /* ---- plan builder pool ----

@@ -11,11 +11,13 @@
 #include "../../include/fht.h"
 #include "fht_launch.hpp"
 #include "plan.hpp"
+#include "table_arena.hpp"
 
 struct fht_plan_s {
   fht::HostPlan host;
   fht::DevicePlan dev;
-  void* d_tables = nullptr;  // one device allocation holding every table of the plan
+  void* d_tables = nullptr;  // one device range (table arena) holding every table of the plan
+  size_t d_tables_bytes = 0;
   std::mutex mu;             // serialises the lazy adjoint build and the host-table restore
   // Once uploaded, a device plan keeps on the host only what launches read
   // there (work lists and pass boundaries): the merge programs, row jobs,
@@ -93,39 +95,73 @@ cudaError_t upload_tables(fht_plan_s* p) {
     d.aptr = nullptr;
     d.aops = nullptr;
   }
+  const int dev = p->dev.device;
   void* buf = nullptr;
-  cudaError_t e = cudaMalloc(&buf, std::max<size_t>(tp.host.size(), 256));
+  const size_t bytes = std::max<size_t>(tp.host.size(), 256);
+  cudaError_t e = fht::table_arena_alloc(dev, bytes, &buf);
   if (e != cudaSuccess) return e;
   // The copy runs on a non-blocking stream of this thread (one per device),
   // so that it waits for nothing but itself: a plan built while the device
   // is busy (a serving loop's builder threads) does not queue behind the
-  // work on the legacy default stream.
+  // work on the legacy default stream.  It leaves from this thread's pinned
+  // staging buffer (grown when a plan needs more, freed at thread exit).
   static thread_local cudaStream_t upload_stream[64] = {};
-  const int dev = p->dev.device;
+  struct Staging {
+    void* p = nullptr;
+    size_t n = 0;
+    ~Staging() {
+      if (p) cudaFreeHost(p);
+    }
+  };
+  static thread_local Staging staging;
   cudaStream_t us = nullptr;
   if (dev >= 0 && dev < 64) {
     if (!upload_stream[dev] && cudaStreamCreateWithFlags(&upload_stream[dev], cudaStreamNonBlocking) != cudaSuccess)
       upload_stream[dev] = nullptr;
     us = upload_stream[dev];
   }
+  if (us && staging.n < tp.host.size()) {
+    if (staging.p) cudaFreeHost(staging.p);
+    staging.p = nullptr;
+    staging.n = 0;
+    const size_t want = std::max<size_t>(tp.host.size(), size_t(1) << 20);
+    if (cudaMallocHost(&staging.p, want) == cudaSuccess) {
+      staging.n = want;
+    } else {
+      staging.p = nullptr;
+      cudaGetLastError();  // clear the failed allocation; the copy below goes from pageable memory
+    }
+  }
   if (us) {
-    e = cudaMemcpyAsync(buf, tp.host.data(), tp.host.size(), cudaMemcpyHostToDevice, us);
+    const void* src = tp.host.data();
+    if (staging.n >= tp.host.size()) {
+      memcpy(staging.p, tp.host.data(), tp.host.size());
+      src = staging.p;
+    }
+    e = cudaMemcpyAsync(buf, src, tp.host.size(), cudaMemcpyHostToDevice, us);
     if (e == cudaSuccess) e = cudaStreamSynchronize(us);
   } else {
     e = cudaMemcpy(buf, tp.host.data(), tp.host.size(), cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) {
-    cudaFree(buf);
+    fht::table_arena_free(dev, buf, bytes);
     return e;
   }
   for (auto& f : tp.fix) *f.first = static_cast<unsigned char*>(buf) + f.second;
   p->d_tables = buf;
+  p->d_tables_bytes = bytes;
   return cudaSuccess;
 }
 
 void free_dev(fht_plan_s* p) {
-  if (p->d_tables) cudaFree(p->d_tables);  // cudaFree waits for work that may still read the tables
+  if (p->d_tables) {
+    // launches that may still read the tables end first (as a cudaFree
+    // would wait for them): the range can be handed to another plan at once
+    cudaDeviceSynchronize();
+    fht::table_arena_free(p->dev.device, p->d_tables, p->d_tables_bytes);
+  }
   p->d_tables = nullptr;
+  p->d_tables_bytes = 0;
   fht::DevicePlan& d = p->dev;
   d.fused = nullptr;
   d.ops = nullptr;

@@ -75,3 +75,28 @@ def test_device_plan_tables_come_back_equal(F, h, w, boundary, dtype):
     gin2 = torch.empty_like(gin)
     dev.adjoint(out, gin2, ws)
     assert torch.equal(gin, gin2)
+
+
+def test_table_ranges_reused_after_destroy(F, orc):
+    # Plans take their device tables from ranges of shared chunks; a destroyed
+    # plan's range goes to later plans.  Many plans built and destroyed in an
+    # interleaved order, then every surviving plan (old ones and ones on
+    # recycled ranges, small and large) still
+    # gives the oracle's transform bit for bit.
+    rng = np.random.default_rng(17)
+    shapes = [(int(rng.integers(1, 90)), int(rng.integers(1, 90))) for _ in range(300)]
+    shapes += [(2000, 1900), (1500, 64)]
+    plans = {k: F.Plan(h, w, torch.uint8, 15, "cyclic") for k, (h, w) in enumerate(shapes)}
+    for k in list(plans)[::2]:
+        plans.pop(k).close()
+    more = [(int(rng.integers(1, 90)), int(rng.integers(1, 90))) for _ in range(150)]
+    for j, (h, w) in enumerate(more):
+        plans[len(shapes) + j] = F.Plan(h, w, torch.uint8, 15, "extended")
+    shapes += more
+    for k in sorted(plans)[::7] + [len(shapes) - len(more) - 1]:
+        p = plans[k]
+        img = rng.integers(0, 256, size=(p.h, p.w)).astype(np.uint8)
+        got = p.forward(torch.from_numpy(img).cuda()).cpu().numpy().astype(np.int64)
+        b = orc.EXTENDED if p.boundary == "extended" else orc.CYCLIC
+        ref = orc.fht(img.astype(np.int64), 15, b, orc.SPLIT_T)
+        assert np.array_equal(got, ref), (k, p.h, p.w, p.boundary)
