@@ -340,7 +340,9 @@ __global__ void __launch_bounds__(256) adj_upper_kernel(const AdjRow* __restrict
 // transposed ones, with ~ the column reversal of the leftward quadrants.  One
 // CTA = one 32 x 32 image tile: untransposed views are read along image rows,
 // transposed ones along image columns (coalesced view rows) and turned
-// through shared memory.  Every element adds its quadrants in order q = 0..3.
+// through shared memory.  Every thread issues all its quadrants' loads before
+// the one barrier (up to 16 in flight), then every element adds its quadrants
+// in order q = 0..3.
 struct AdjSumQuad {
   int64_t off;  // element offset of the view gradient in the workspace
   int32_t pitch, L, transpose, flip;
@@ -354,36 +356,40 @@ struct AdjSumParams {
 template <typename AccT>
 __global__ void __launch_bounds__(256) adj_sum_kernel(const AccT* __restrict__ ws, AdjSumParams sp,
                                                       AccT* __restrict__ gin) {
-  __shared__ AccT T[32][33];
+  __shared__ AccT T[4][32][33];
   const int32_t tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int32_t x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, x = x0 + tx;
-  AccT acc[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
-  for (int32_t k = 0; k < sp.nq; k++) {
+  AccT v[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    if (k >= sp.nq) break;
     const AdjSumQuad Q = sp.q[k];
     const AccT* __restrict__ g = ws + Q.off;
     if (!Q.transpose) {
-      if (x < sp.w) {
-        const int32_t z = Q.flip ? Q.L - 1 - x : x;
+      const int32_t z = Q.flip ? Q.L - 1 - x : x;
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-          const int32_t y = y0 + ty + 8 * i;
-          if (y < sp.h) acc[i] += g[(int64_t)y * Q.pitch + z];
-        }
+      for (int i = 0; i < 4; i++) {
+        const int32_t y = y0 + ty + 8 * i;
+        v[k][i] = (x < sp.w && y < sp.h) ? g[(int64_t)y * Q.pitch + z] : AccT(0);
       }
     } else {
-      // T[a][b] = view row x0 + a at the column of image row y0 + b
+      // T[k][a][b] = view row x0 + a at the column of image row y0 + b
       const int32_t yb = y0 + tx;
       const int32_t z = Q.flip ? Q.L - 1 - yb : yb;
 #pragma unroll
       for (int i = 0; i < 4; i++) {
         const int32_t xr = x0 + ty + 8 * i;
-        T[ty + 8 * i][tx] = (xr < sp.w && yb < sp.h) ? g[(int64_t)xr * Q.pitch + z] : AccT(0);
+        T[k][ty + 8 * i][tx] = (xr < sp.w && yb < sp.h) ? g[(int64_t)xr * Q.pitch + z] : AccT(0);
       }
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < 4; i++) acc[i] += T[tx][ty + 8 * i];
-      __syncthreads();
     }
+  }
+  __syncthreads();
+  AccT acc[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    if (k >= sp.nq) break;
+#pragma unroll
+    for (int i = 0; i < 4; i++) acc[i] += sp.q[k].transpose ? T[k][tx][ty + 8 * i] : v[k][i];
   }
   if (x >= sp.w) return;
 #pragma unroll

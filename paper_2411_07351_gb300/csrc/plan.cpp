@@ -128,9 +128,14 @@ static void build_program(const Tree& tr, int32_t r, std::vector<MergeOp>& ops, 
   const TreeNode& root = tr.nodes[r];
   nlev = root.height;
   const int32_t m = root.m, base = root.a;
-  // collect the subtree's internal nodes by height
-  std::vector<std::vector<int32_t>> by_h(nlev + 1);
-  std::vector<int32_t> stack{r};
+  // collect the subtree's internal nodes by height (the lists and the merge
+  // table are this thread's scratch, reused from one subtree to the next)
+  static thread_local std::vector<std::vector<int32_t>> by_h;
+  static thread_local std::vector<int32_t> stack;
+  static thread_local std::vector<MergeRow> mtab;
+  if ((int32_t)by_h.size() < nlev + 1) by_h.resize(nlev + 1);
+  for (int32_t lev = 0; lev <= nlev; lev++) by_h[lev].clear();
+  stack.assign(1, r);
   while (!stack.empty()) {
     int32_t i = stack.back();
     stack.pop_back();
@@ -149,7 +154,6 @@ static void build_program(const Tree& tr, int32_t r, std::vector<MergeOp>& ops, 
       const TreeNode& nd = tr.nodes[i];
       const TreeNode& c0 = tr.nodes[nd.child[0]];
       const TreeNode& c1 = tr.nodes[nd.child[1]];
-      std::vector<MergeRow> mtab;
       merge_table(nd.m, c0.m, c1.m, mtab);
       for (int32_t t = 0; t < nd.m; t++) {
         const int32_t t1 = mtab[t].t1, t2 = mtab[t].t2, s = mtab[t].s;
@@ -206,6 +210,18 @@ static void build_spine_staging(HostPlan& P) {
   const int32_t epc = 16 / acc;  // elements per 16-byte chunk
   auto floor_to = [](int64_t a, int64_t m) { return a >= 0 ? a / m * m : -((-a + m - 1) / m) * m; };
   auto ceil_to = [](int64_t a, int64_t m) { return (a + m - 1) / m * m; };
+  struct Seg {
+    int64_t row;
+    int32_t wpart, lo, hi;
+  };
+  std::vector<Seg> segs;                             // reused by every group
+  std::vector<std::pair<int64_t, int32_t>> member;  // term index -> segment
+  // A group's segments of one part row are chained in index order (next[])
+  // from a hash of the row (open addressing over kHash slots), so a term looks
+  // only at its own row's segments and still takes the first that fits.
+  constexpr int32_t kHash = 2048;
+  std::vector<int64_t> hkey(kHash);
+  std::vector<int32_t> hhead(kHash, -1), htail(kHash, -1), hused, next;
   P.spine_grp_begin.push_back(0);
   for (size_t p = 0; p + 1 < P.spine_pass_begin.size(); p++) {
     const int64_t b = P.spine_pass_begin[p], e = P.spine_pass_begin[p + 1];
@@ -213,12 +229,11 @@ static void build_spine_staging(HostPlan& P) {
     bool ok = true;
     for (int64_t g0 = b; g0 < e; g0 += kSpineRows) {
       const int64_t g1 = std::min<int64_t>(e, g0 + kSpineRows);
-      struct Seg {
-        int64_t row;
-        int32_t wpart, lo, hi;
-      };
-      std::vector<Seg> segs;
-      std::vector<std::pair<int64_t, int32_t>> member;  // term index -> segment
+      segs.clear();
+      member.clear();
+      next.clear();
+      for (int32_t s : hused) hhead[s] = -1;
+      hused.clear();
       for (int64_t r = g0; r < g1; r++) {
         const SpineRow& R = P.spine_rows[r];
         const QuadDesc& Q = P.quad[R.q];
@@ -226,16 +241,31 @@ static void build_spine_staging(HostPlan& P) {
         for (int32_t c = 0; c < R.term_count; c++) {
           const int64_t ti = R.term_begin + c;
           const SpineTerm& T = P.spine_terms[ti];
-          int32_t k = 0;
-          for (; k < (int32_t)segs.size(); k++) {
-            Seg& S = segs[k];
-            if (S.row == T.row && T.off >= S.hi - kStageMaxSpan && T.off <= S.lo + kStageMaxSpan) {
+          int32_t slot = (int32_t)(((uint64_t)T.row * 0x9E3779B97F4A7C15ull) >> 53);  // 11 bits
+          while (hhead[slot] != -1 && hkey[slot] != T.row) slot = (slot + 1) & (kHash - 1);
+          int32_t k = -1;
+          for (int32_t j = hhead[slot]; j != -1; j = next[j]) {
+            Seg& S = segs[j];
+            if (T.off >= S.hi - kStageMaxSpan && T.off <= S.lo + kStageMaxSpan) {
               S.lo = std::min(S.lo, T.off);
               S.hi = std::max(S.hi, T.off);
+              k = j;
               break;
             }
           }
-          if (k == (int32_t)segs.size()) segs.push_back({T.row, T.wpart, T.off, T.off});
+          if (k < 0) {
+            k = (int32_t)segs.size();
+            segs.push_back({T.row, T.wpart, T.off, T.off});
+            next.push_back(-1);
+            if (hhead[slot] == -1) {
+              hkey[slot] = T.row;
+              hhead[slot] = k;
+              hused.push_back(slot);
+            } else {
+              next[htail[slot]] = k;
+            }
+            htail[slot] = k;
+          }
           member.emplace_back(ti, k);
         }
       }
