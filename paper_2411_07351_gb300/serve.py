@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import collections
 import gc
+import os
 import sys
 import time
 from dataclasses import dataclass, field
@@ -79,8 +80,12 @@ class PlanBuilder:
     does not need yet and no interpreter thread competes with it while plans
     are built.  Built plans stay in an LRU cache of `capacity` shapes."""
 
-    def __init__(self, device: int, quads: int, boundary: str, split: str, workers: int = 8,
+    def __init__(self, device: int, quads: int, boundary: str, split: str, workers: int | None = None,
                  batch_below: int = 0, capacity: int = 8192):
+        # plan building is the serving loop's largest stage: every core but
+        # the loop's own and one spare builds plans (at most 16 threads)
+        if workers is None:
+            workers = max(2, min(16, (os.cpu_count() or 4) - 2))
         self.device, self.quads, self.boundary, self.split = device, quads, boundary, split
         self.batch_below = batch_below
         self.capacity = capacity
