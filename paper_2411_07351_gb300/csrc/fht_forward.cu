@@ -174,16 +174,18 @@ template <typename AccT>
 __global__ void __launch_bounds__(256, sizeof(AccT) > 4 ? 1 : 3) spine_kernel(const SpineRow* __restrict__ rows,
                                                    int64_t nrows, const SpineTerm* __restrict__ terms,
                                                    const AccT* __restrict__ ws, AccT* __restrict__ out, AccT* inner,
-                                                   QuadDescs quads) {
+                                                   QuadDescs quads, int32_t rpc) {
+  // rpc (<= kSpineRows) rows per CTA: a CTA sums its rows one after another,
+  // so a short spine takes fewer rows per CTA and more CTAs
   __shared__ SpineTerm st[kSpineRows][kMaxSpineTerms];
   __shared__ SpineRow sr[kSpineRows];
   __shared__ const AccT* tp[kSpineRows][kMaxSpineTerms];
   __shared__ int32_t s_straddle;
   pdl_launch_dependents();
   pdl_wait();
-  const int64_t r0 = (int64_t)blockIdx.x * kSpineRows;
+  const int64_t r0 = (int64_t)blockIdx.x * rpc;
   const int32_t u0 = blockIdx.y * kSpineTilePlain;
-  const int32_t nr = (int32_t)(nrows - r0 < kSpineRows ? nrows - r0 : kSpineRows);
+  const int32_t nr = (int32_t)(nrows - r0 < rpc ? nrows - r0 : rpc);
   if (threadIdx.x < nr) sr[threadIdx.x] = rows[r0 + threadIdx.x];
   if (threadIdx.x == 0) s_straddle = 0;
   __syncthreads();
@@ -709,9 +711,14 @@ static cudaError_t launch_forward_t(const DevicePlan& D, const void* in, int64_t
                (const SpineTerm*)D.spine_terms, (const SpineGrp*)(D.spine_grps + P.spine_grp_begin[p]),
                (const SpineSeg*)D.spine_segs, (const AccT*)wsa, static_cast<AccT*>(out), wsa, qd);
       } else {
-        dim3 sgrid(groups, (unsigned)((maxW + kSpineTilePlain - 1) / kSpineTilePlain));
+        // rows per CTA: 16, halved (to 2 at least) while the grid would hold
+        // fewer than two CTAs per SM (a 257-row spine: 129 CTAs of 2 rows)
+        const unsigned tiles = (unsigned)((maxW + kSpineTilePlain - 1) / kSpineTilePlain);
+        int32_t rpc = kSpineRows;
+        while (rpc > 2 && (unsigned)((n + rpc - 1) / rpc) * tiles < 2u * 152u) rpc /= 2;
+        dim3 sgrid((unsigned)((n + rpc - 1) / rpc), tiles);
         e = go(spine_kernel<AccT>, sgrid, 256, 0, (const SpineRow*)(D.spine_rows + b), n,
-               (const SpineTerm*)D.spine_terms, (const AccT*)wsa, static_cast<AccT*>(out), wsa, qd);
+               (const SpineTerm*)D.spine_terms, (const AccT*)wsa, static_cast<AccT*>(out), wsa, qd, rpc);
       }
       mark(1);
       nvtxRangePop();
