@@ -214,14 +214,18 @@ static void build_spine_staging(HostPlan& P) {
     int64_t row;
     int32_t wpart, lo, hi;
   };
-  std::vector<Seg> segs;                             // reused by every group
-  std::vector<std::pair<int64_t, int32_t>> member;  // term index -> segment
+  // this thread's scratch, reused by every group and every plan
+  static thread_local std::vector<Seg> segs;
+  static thread_local std::vector<std::pair<int64_t, int32_t>> member;  // term index -> segment
   // A group's segments of one part row are chained in index order (next[])
   // from a hash of the row (open addressing over kHash slots), so a term looks
   // only at its own row's segments and still takes the first that fits.
   constexpr int32_t kHash = 2048;
-  std::vector<int64_t> hkey(kHash);
-  std::vector<int32_t> hhead(kHash, -1), htail(kHash, -1), hused, next;
+  static thread_local std::vector<int64_t> hkey(kHash);
+  static thread_local std::vector<int32_t> hhead(kHash, -1), htail(kHash, -1), hused, next;
+  for (int32_t s : hused) hhead[s] = -1;  // an earlier plan's last group
+  hused.clear();
+  P.spine_grps.reserve(P.spine_rows.size() / kSpineRows + P.spine_pass_begin.size());
   P.spine_grp_begin.push_back(0);
   for (size_t p = 0; p + 1 < P.spine_pass_begin.size(); p++) {
     const int64_t b = P.spine_pass_begin[p], e = P.spine_pass_begin[p + 1];
@@ -356,11 +360,20 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
   int64_t ws_off = 0;  // elements of the accumulator type after the header
   std::vector<std::vector<RowJob>> passes;
   std::vector<int64_t> bytes_by_height;
-  std::vector<SpineRow> pre_rows;                          // big parts (n > 8192), before the spine
-  std::vector<SpineTerm> pre_terms;
+  // spine rows and terms by chunk level from the bottom, and the big parts'
+  // (n > 8192) pre-pass: this thread's scratch, emptied here and reused from
+  // one plan to the next (a serving process builds thousands of plans a
+  // second, and fresh vectors of this size cost a page fault per 4 KB)
+  static thread_local std::vector<SpineRow> pre_rows;
+  static thread_local std::vector<SpineTerm> pre_terms;
+  static thread_local std::vector<std::vector<SpineRow>> spine_levels_rows;
+  static thread_local std::vector<std::vector<SpineTerm>> spine_levels_terms;
+  pre_rows.clear();
+  pre_terms.clear();
+  for (auto& v : spine_levels_rows) v.clear();
+  for (auto& v : spine_levels_terms) v.clear();
+  size_t nlevels = 0;  // levels in use this plan (the scratch may hold more, empty)
   int64_t pre_bytes = 0;
-  std::vector<std::vector<SpineRow>> spine_levels_rows;    // by chunk level from the bottom
-  std::vector<std::vector<SpineTerm>> spine_levels_terms;
   std::vector<int64_t> spine_levels_bytes;
   std::set<int32_t> heights_seen;
 
@@ -641,6 +654,7 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
         if ((int32_t)spine_levels_rows.size() < (int32_t)chunks.size()) spine_levels_rows.resize(chunks.size());
         if ((int32_t)spine_levels_terms.size() < (int32_t)chunks.size()) spine_levels_terms.resize(chunks.size());
         if ((int32_t)spine_levels_bytes.size() < (int32_t)chunks.size()) spine_levels_bytes.resize(chunks.size(), 0);
+        nlevels = std::max(nlevels, chunks.size());
         for (size_t c = 0; c < chunks.size(); c++) {
           const int32_t ktop = chunks[c].first, kbot = chunks[c].second;
           const int32_t top = spine[ktop];
@@ -776,22 +790,28 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
   }
   // spine launches: the big parts, then the lowest chunk level of every quadrant first
   P.spine_pass_begin.push_back(0);
-  if (!pre_rows.empty()) {
-    spine_levels_rows.insert(spine_levels_rows.begin(), pre_rows);
-    spine_levels_terms.insert(spine_levels_terms.begin(), pre_terms);
-    spine_levels_bytes.insert(spine_levels_bytes.begin(), pre_bytes);
+  {
+    size_t nrows = pre_rows.size(), nterms = pre_terms.size();
+    for (size_t c = 0; c < nlevels; c++) {
+      nrows += spine_levels_rows[c].size();
+      nterms += spine_levels_terms[c].size();
+    }
+    P.spine_rows.reserve(nrows);
+    P.spine_terms.reserve(nterms);
   }
-  for (size_t c = 0; c < spine_levels_rows.size(); c++) {
+  auto flatten = [&](const std::vector<SpineRow>& rows, const std::vector<SpineTerm>& terms, int64_t bytes) {
     const int32_t base = (int32_t)P.spine_terms.size();
-    for (SpineRow sr : spine_levels_rows[c]) {
+    for (SpineRow sr : rows) {
       sr.term_begin += base;
       P.spine_rows.push_back(sr);
     }
-    P.spine_terms.insert(P.spine_terms.end(), spine_levels_terms[c].begin(), spine_levels_terms[c].end());
+    P.spine_terms.insert(P.spine_terms.end(), terms.begin(), terms.end());
     P.spine_pass_begin.push_back((int64_t)P.spine_rows.size());
-    P.spine_pass_bytes.push_back(spine_levels_bytes[c]);
-    P.spine_bytes += spine_levels_bytes[c];
-  }
+    P.spine_pass_bytes.push_back(bytes);
+    P.spine_bytes += bytes;
+  };
+  if (!pre_rows.empty()) flatten(pre_rows, pre_terms, pre_bytes);
+  for (size_t c = 0; c < nlevels; c++) flatten(spine_levels_rows[c], spine_levels_terms[c], spine_levels_bytes[c]);
   build_spine_staging(P);
   // tiles: fast-path items use tile_cols; generic items (two ping-pong
   // buffers of up to 63 rows) use half of it, so their shared windows stay
