@@ -373,6 +373,8 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
   for (auto& v : spine_levels_rows) v.clear();
   for (auto& v : spine_levels_terms) v.clear();
   size_t nlevels = 0;  // levels in use this plan (the scratch may hold more, empty)
+  std::vector<int64_t> chunk_row0;  // per spine chunk: first row, width, height of each part
+  std::vector<int32_t> chunk_w, chunk_m;
   int64_t pre_bytes = 0;
   std::vector<int64_t> spine_levels_bytes;
   std::set<int32_t> heights_seen;
@@ -663,7 +665,21 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
           std::vector<SpineRow>& rows_out = spine_levels_rows[c];
           std::vector<SpineTerm>& terms_out = spine_levels_terms[c];
           // every slope t of the chunk's top node: follow the spine down to the
-          // chunk's lower boundary, collecting (part, row, offset)
+          // chunk's lower boundary, collecting (part, row, offset).  A part's
+          // row r lives at node_row(pi, 0) + r * pitch; its first row, width
+          // and height are taken once per chunk.
+          const int32_t nk = kbot - ktop + 2;  // the chunk's left parts, then its lowest node
+          chunk_row0.resize(nk);
+          chunk_w.resize(nk);
+          chunk_m.resize(nk);
+          for (int32_t j = 0; j < nk; j++) {
+            const int32_t pi = j + 1 < nk ? tr.nodes[spine[ktop + j]].child[0] : tr.nodes[spine[kbot]].child[1];
+            chunk_row0[j] = node_row(pi, 0);
+            chunk_w[j] = node_w(pi);
+            chunk_m[j] = tr.nodes[pi].m;
+          }
+          rows_out.reserve(rows_out.size() + N.m);
+          terms_out.reserve(terms_out.size() + (size_t)N.m * nk);
           for (int32_t t = 0; t < N.m; t++) {
             SpineRow sr{};
             sr.dst = fin ? Q.out_off + (int64_t)t * Q.W : node_row(top, t);
@@ -673,22 +689,20 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
             sr.term_begin = (int32_t)terms_out.size();  // rebased when the launches are flattened
             int32_t tn = t;
             int64_t off = 0;  // accumulated shift in window (x) coordinates
-            auto add_term = [&](int32_t pi, int32_t row) {
-              const TreeNode& pt = tr.nodes[pi];
+            auto add_term = [&](int32_t j, int32_t row) {
               SpineTerm st{};
-              st.row = node_row(pi, row);
-              st.wpart = node_w(pi);
-              st.off = cfg.ext ? (int32_t)(off + pt.m - N.m) : (int32_t)off;  // off kept reduced mod W
+              st.row = chunk_row0[j] + (int64_t)row * pitch;
+              st.wpart = chunk_w[j];
+              st.off = cfg.ext ? (int32_t)(off + chunk_m[j] - N.m) : (int32_t)off;  // off kept reduced mod W
               terms_out.push_back(st);
             };
             for (int32_t k = ktop; k <= kbot; k++) {
-              const TreeNode& nd = tr.nodes[spine[k]];
               const MergeRow& mr = stab[k][tn];
-              add_term(nd.child[0], mr.t1);
+              add_term(k - ktop, mr.t1);
               off += mr.s;
               if (!cfg.ext && off >= Q.W) off = off < 2 * (int64_t)Q.W ? off - Q.W : off % Q.W;
               tn = mr.t2;
-              if (k == kbot) add_term(nd.child[1], mr.t2);
+              if (k == kbot) add_term(nk - 1, mr.t2);
             }
             sr.term_count = (int32_t)terms_out.size() - sr.term_begin;
             P.max_spine_terms = std::max(P.max_spine_terms, sr.term_count);
