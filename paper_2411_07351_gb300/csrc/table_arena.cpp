@@ -2,7 +2,7 @@
 //
 // A serving process builds a plan for nearly every request (image sizes
 // rarely repeat), thousands per second on builder threads.  One cudaMalloc
-// per plan made those threads call into the driver's allocator that often,
+// per plan made those threads call into the CUDA driver's allocator that often,
 // and the calls slowed down as allocations accumulated until they held up
 // the serving thread's own CUDA calls for tens of milliseconds.  Plans now
 // take their tables from chunks of kChunk bytes allocated once per device
@@ -32,21 +32,30 @@ struct Chunk {
   unsigned char* base = nullptr;
   size_t size = 0;
   std::map<size_t, size_t> free;  // offset -> length of each free range, coalesced
+  size_t largest = 0;             // longest free range (chunks that cannot fit are skipped)
 };
 
 struct Arena {
   std::mutex mu;
   std::vector<Chunk> chunks;
+  std::map<uintptr_t, size_t> by_base;  // chunk base address -> index in chunks
 };
+
+void recompute_largest(Chunk& c) {
+  c.largest = 0;
+  for (const auto& f : c.free) c.largest = std::max(c.largest, f.second);
+}
 
 Arena g_arena[kMaxDevices];
 
 bool take(Chunk& c, size_t bytes, void** out) {
+  if (c.largest < bytes) return false;
   for (auto it = c.free.begin(); it != c.free.end(); ++it) {
     if (it->second < bytes) continue;
     const size_t off = it->first, len = it->second;
     c.free.erase(it);
     if (len > bytes) c.free.emplace(off + bytes, len - bytes);
+    if (len == c.largest) recompute_largest(c);
     *out = c.base + off;
     return true;
   }
@@ -63,10 +72,12 @@ void give_back(Chunk& c, size_t off, size_t bytes) {
     auto prev = std::prev(next);
     if (prev->first + prev->second == off) {  // merge with the range before
       prev->second += bytes;
+      c.largest = std::max(c.largest, prev->second);
       return;
     }
   }
   c.free.emplace(off, bytes);
+  c.largest = std::max(c.largest, bytes);
 }
 
 }  // namespace
@@ -88,6 +99,8 @@ cudaError_t table_arena_alloc(int device, size_t bytes, void** out) {
   c.base = static_cast<unsigned char*>(base);
   c.size = kChunk;
   c.free.emplace(0, kChunk);
+  c.largest = kChunk;
+  a.by_base.emplace(reinterpret_cast<uintptr_t>(base), a.chunks.size());
   a.chunks.push_back(std::move(c));
   take(a.chunks.back(), bytes, out);
   return cudaSuccess;
@@ -102,13 +115,12 @@ void table_arena_free(int device, void* p, size_t bytes) {
   }
   Arena& a = g_arena[device];
   std::lock_guard<std::mutex> lock(a.mu);
-  unsigned char* q = static_cast<unsigned char*>(p);
-  for (Chunk& c : a.chunks) {
-    if (q >= c.base && q < c.base + c.size) {
-      give_back(c, (size_t)(q - c.base), bytes);
-      return;
-    }
-  }
+  const uintptr_t q = reinterpret_cast<uintptr_t>(p);
+  auto it = a.by_base.upper_bound(q);  // the chunk with the highest base <= q
+  if (it == a.by_base.begin()) return;
+  --it;
+  Chunk& c = a.chunks[it->second];
+  if (q < it->first + c.size) give_back(c, (size_t)(q - it->first), bytes);
 }
 
 }  // namespace fht

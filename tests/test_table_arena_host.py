@@ -9,7 +9,8 @@ allocations and frees checks that:
   * ranges above a quarter chunk get an allocation of their own, returned on
     free;
   * freed neighbours coalesce: once everything is freed, the chunks hold
-    quarter-chunk ranges back to back without a new chunk.
+    quarter-chunk ranges back to back without a new chunk;
+  * a free range with both neighbours held is handed out again.
 """
 import os
 import shutil
@@ -95,6 +96,13 @@ int main() {
     q.push_back(p);
   }
   if (g_mallocs != before) { printf("FAIL not coalesced: %d new chunks\n", g_mallocs - before); return 1; }
+  // every chunk is full: an isolated free range (both neighbours held) is found again
+  fht::table_arena_free(0, q[1], kChunk / 4);
+  void* again = nullptr;
+  if (fht::table_arena_alloc(0, kChunk / 4, &again) != cudaSuccess || again != q[1] || g_mallocs != before) {
+    printf("FAIL isolated free range not reused\n");
+    return 1;
+  }
   for (void* p : q) fht::table_arena_free(0, p, kChunk / 4);
   printf("OK chunks %d dedicated %d\n", chunks, dedicated);
   return 0;
