@@ -127,6 +127,13 @@ def test_argument_errors_without_a_gpu(F):
     assert lib.fht_forward_noalloc(p._h, 16, 8, 16, None) == _capi.FHT_ERR_INVALID
     assert lib.fht_submit(None, 1, None, None) == _capi.FHT_ERR_INVALID
     assert lib.fht_queue_destroy(None) == _capi.FHT_OK
+    r = ctypes.c_int32(7)
+    assert lib.fht_queue_ready(None, ctypes.byref(r)) == _capi.FHT_ERR_INVALID
+    assert lib.fht_queue_ready(None, None) == _capi.FHT_ERR_INVALID
+    bp = ctypes.c_void_p()
+    assert lib.fht_builder_create(ctypes.byref(bp), 0) == _capi.FHT_ERR_INVALID
+    assert lib.fht_builder_poll(None, None, None, None, 0, None) == _capi.FHT_ERR_INVALID
+    assert lib.fht_builder_destroy(None) == _capi.FHT_OK
     assert lib.fht_adjoint(p._h, 16, 16, 8, 256, p.adjoint_workspace_bytes, None) == _capi.FHT_ERR_INVALID
     assert lib.fht_pattern_errors(0, 5, 0, None, None) == _capi.FHT_ERR_INVALID
     assert lib.fht_plan_check(None) == _capi.FHT_ERR_INVALID
