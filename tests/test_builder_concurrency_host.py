@@ -11,8 +11,6 @@ for byte, the same configuration built serially through fht_plan.
 import ctypes
 import time
 
-import pytest
-
 from paper_2411_07351_gb300 import _capi as C
 
 CONFIGS = [
