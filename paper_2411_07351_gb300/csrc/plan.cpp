@@ -208,8 +208,9 @@ static constexpr size_t kStageSmemMax = 96 << 10;
 static void build_spine_staging(HostPlan& P) {
   const int32_t acc = P.acc_size;
   const int32_t epc = 16 / acc;  // elements per 16-byte chunk
-  auto floor_to = [](int64_t a, int64_t m) { return a >= 0 ? a / m * m : -((-a + m - 1) / m) * m; };
-  auto ceil_to = [](int64_t a, int64_t m) { return (a + m - 1) / m * m; };
+  // m is a power of two (elements per 16 bytes): round by masking
+  auto floor_to = [](int64_t a, int64_t m) { return a & ~(m - 1); };
+  auto ceil_to = [](int64_t a, int64_t m) { return (a + m - 1) & ~(m - 1); };
   struct Seg {
     int64_t row;
     int32_t wpart, lo, hi;
@@ -373,6 +374,7 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
   for (auto& v : spine_levels_rows) v.clear();
   for (auto& v : spine_levels_terms) v.clear();
   size_t nlevels = 0;  // levels in use this plan (the scratch may hold more, empty)
+  std::vector<std::vector<MergeRow>> spine_tabs[2];  // per tree: merge tables of its spine nodes
   std::vector<int64_t> chunk_row0;  // per spine chunk: first row, width, height of each part
   std::vector<int32_t> chunk_w, chunk_m;
   int64_t pre_bytes = 0;
@@ -600,10 +602,14 @@ std::string build_plan(const PlanConfig& cfg_in, HostPlan& P) {
         P.band_bytes += ((int64_t)band.m * (cfg.ext ? Q.L + 63 : Q.W) + (int64_t)band.m * bi_width(cfg, Q, band.m)) * acc;
       }
       if (!spine.empty()) {
-        std::vector<std::vector<MergeRow>> stab(spine.size());
-        for (size_t k = 0; k < spine.size(); k++) {
-          const TreeNode& nd = tr.nodes[spine[k]];
-          merge_table(nd.m, tr.nodes[nd.child[0]].m, tr.nodes[nd.child[1]].m, stab[k]);
+        // the spine nodes' merge tables, once per tree (Q0 / Q1 and Q2 / Q3 share theirs)
+        std::vector<std::vector<MergeRow>>& stab = spine_tabs[ti];
+        if (stab.empty()) {
+          stab.resize(spine.size());
+          for (size_t k = 0; k < spine.size(); k++) {
+            const TreeNode& nd = tr.nodes[spine[k]];
+            merge_table(nd.m, tr.nodes[nd.child[0]].m, tr.nodes[nd.child[1]].m, stab[k]);
+          }
         }
         auto node_row = [&](int32_t pi, int32_t row) -> int64_t {
           if (inner_row0_of[pi] >= 0) return inner_base + (inner_row0_of[pi] + row) * pitch;
