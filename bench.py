@@ -450,16 +450,28 @@ def run_fht(args, wl):
         if world == 1 and not args.no_extras:
             # the rest of the metric (latency, batched vs plain, served vs plain),
             # measured after the headline's timed region on the same GPU
-            c1, c3 = measure_c1(args), measure_c3(args)
-            c5 = _c5_in_fresh_process(args)
-            line["c1_latency"] = dict(c1["latency_us"], unit="us", workload=c1["config"]["workload"],
-                                      launches_per_call=c1["gpu_launches_per_call"])
-            line["c3_batching"] = {k: c3[k] for k in ("batched_ms", "graph_ms", "plain_ms", "plain_value",
-                                                      "graph_value", "speedup_vs_plain", "model_gbs_batched",
-                                                      "gpu_launches")}
-            line["c3_batching"].update(batched_value=c3["value"], unit=UNIT, workload=c3["config"]["workload"])
-            line["c5_serving"] = {"served": c5["served"], "plain": c5["plain"], "unit": UNIT,
-                                  "workload": c5["config"]["workload"]}
+            # (an extra that fails is reported as such; the headline line still prints)
+            def c1_part():
+                c1 = measure_c1(args)
+                return dict(c1["latency_us"], unit="us", workload=c1["config"]["workload"],
+                            launches_per_call=c1["gpu_launches_per_call"])
+
+            def c3_part():
+                c3 = measure_c3(args)
+                out = {k: c3[k] for k in ("batched_ms", "graph_ms", "plain_ms", "plain_value", "graph_value",
+                                          "speedup_vs_plain", "model_gbs_batched", "gpu_launches")}
+                out.update(batched_value=c3["value"], unit=UNIT, workload=c3["config"]["workload"])
+                return out
+
+            def c5_part():
+                c5 = _c5_in_fresh_process(args)
+                return {"served": c5["served"], "plain": c5["plain"], "unit": UNIT, "workload": c5["config"]["workload"]}
+
+            for key, part in (("c1_latency", c1_part), ("c3_batching", c3_part), ("c5_serving", c5_part)):
+                try:
+                    line[key] = part()
+                except Exception as exc:  # noqa: BLE001 - recorded in the line
+                    line[key] = {"error": f"{type(exc).__name__}: {str(exc)[-400:]}"}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
