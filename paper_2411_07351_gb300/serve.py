@@ -164,8 +164,10 @@ class _Batch:
 class Server:
     def __init__(self, device: int = 0, budget_bytes: int = 16 << 30, streams: int = 4, quads: int = C.FHT_QALL,
                  boundary: str = "cyclic", split: str = "T", max_batch: int = 1024, keep_outputs: bool = True,
-                 max_batch_pixels: int = 16 << 20, plain_pixels: int = 1 << 20, max_inflight: int = 4):
+                 max_batch_pixels: int = 16 << 20, plain_pixels: int = 1 << 20, max_inflight: int = 4,
+                 solo_plain: bool = True):
         self.device = device
+        self.solo_plain = solo_plain
         self.max_batch_pixels = max_batch_pixels
         self.plain_pixels = plain_pixels
         self.keep_outputs = keep_outputs
@@ -258,16 +260,25 @@ class Server:
             best = k
         return best
 
+    def _launch_plain(self) -> bool:
+        """Whether the head of the admitted queue runs the per-image kernels:
+        a large request (it fills the GPU by itself), or, with `solo_plain`, a
+        small one admitted alone (three short launches finish it sooner than a
+        one-job persistent launch and its host-side listing; under load the
+        queue holds several and they are batched)."""
+        head = self.admitted[0]
+        return head.image.numel() >= self.plain_pixels or (self.solo_plain and len(self.admitted) == 1)
+
     def _launch(self, now_fn=None):
         while self.admitted:
-            head = self.admitted[0]
-            slot = self._pick_stream(batched=head.image.numel() < self.plain_pixels)
+            plain = self._launch_plain()
+            slot = self._pick_stream(batched=not plain)
             if slot is None:
                 return
             s = self.streams[slot]
-            if head.image.numel() >= self.plain_pixels:
-                # a large request fills the GPU by itself: the per-image kernels,
-                # no persistent batch
+            if plain:
+                # the per-image kernels, no persistent batch (a large request,
+                # or a small one admitted alone)
                 r = self.admitted.popleft()
                 with torch.cuda.stream(s):
                     r.out = r.plan.new_output()

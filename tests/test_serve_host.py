@@ -198,3 +198,23 @@ def test_batched_launch_only_on_a_queue_that_does_not_block():
     assert s._pick_stream(batched=True) is None
     assert s._pick_stream(batched=False) == 0
     assert s.queues[2].asked == 0  # a full stream's queue is not even asked
+
+
+def test_lone_small_request_takes_the_per_image_kernels():
+    # Small requests are batched into one persistent launch when several are
+    # admitted together; one admitted alone runs the per-image kernels (three
+    # short launches beat a one-job persistent launch); large ones always do.
+    s = serve.Server.__new__(serve.Server)
+    s.plain_pixels = 1000
+    s.solo_plain = True
+    small = lambda rid: serve.Request(rid=rid, arrival=0.0, image=SimpleNamespace(numel=lambda: 100))
+    large = serve.Request(rid=9, arrival=0.0, image=SimpleNamespace(numel=lambda: 5000))
+    s.admitted = collections.deque([small(0)])
+    assert s._launch_plain()
+    s.admitted = collections.deque([small(0), small(1)])
+    assert not s._launch_plain()
+    s.admitted = collections.deque([large, small(1)])
+    assert s._launch_plain()
+    s.solo_plain = False
+    s.admitted = collections.deque([small(0)])
+    assert not s._launch_plain()
