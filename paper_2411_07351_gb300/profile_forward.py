@@ -25,6 +25,7 @@ def main():
     ap.add_argument("--dtype", choices=["f32", "u8"], default="f32")
     ap.add_argument("--boundary", choices=["cyclic", "extended"], default="extended")
     ap.add_argument("--adjoint", action="store_true")
+    ap.add_argument("--quads", type=int, default=15, help="quadrant mask (1 = Q0 ... 15 = all four)")
     ap.add_argument("--tile-cols", type=int, default=0, help="column tile (0: the library default)")
     ap.add_argument("--threads", type=int, default=0, help="CTA size of the fused pass (0: default)")
     a = ap.parse_args()
@@ -32,7 +33,7 @@ def main():
         x = torch.from_numpy(inputs.normal_f32(2, a.h, a.w)).cuda()
     else:
         x = torch.from_numpy(inputs.uniform_u8(2, a.h, a.w)).cuda()
-    p = F.Plan(a.h, a.w, x.dtype, F.FHT_QALL, a.boundary, with_adjoint=a.adjoint, tile_cols=a.tile_cols,
+    p = F.Plan(a.h, a.w, x.dtype, a.quads, a.boundary, with_adjoint=a.adjoint, tile_cols=a.tile_cols,
                threads=a.threads)
     out, ws = p.new_output(), p.new_workspace(adjoint=a.adjoint)
     gin = torch.empty((a.h, a.w), dtype=p.out_dtype, device="cuda") if a.adjoint else None
