@@ -55,7 +55,8 @@ def test_served_results_equal_oracle_and_single(F):
     from paper_2411_07351_gb300.serve import Server, run_stream
 
     reqs, host = _requests(300, 4000.0, 64, 700, 6)
-    srv = Server(budget_bytes=1 << 30, streams=3)
+    # solo_plain off: every small request goes through the persistent batch launch
+    srv = Server(budget_bytes=1 << 30, streams=3, solo_plain=False)
     done, wall = run_stream(srv, reqs)
     assert len(done) == len(reqs)
     assert srv.max_used <= 1 << 30
@@ -73,7 +74,7 @@ def test_served_full_size_range(F):
     from paper_2411_07351_gb300.serve import Server, run_stream
 
     reqs, host = _requests(48, 2000.0, 64, 4096, 61)
-    srv = Server(budget_bytes=16 << 30)
+    srv = Server(budget_bytes=16 << 30, solo_plain=False)
     done, _ = run_stream(srv, reqs)
     assert len(done) == len(reqs)
     assert srv.max_used <= 16 << 30
@@ -84,6 +85,20 @@ def test_served_full_size_range(F):
     _check_against_oracle(done, host)
     for r in done:
         assert torch.equal(r.out, r.plan.forward(r.image)), r.rid
+    srv.close()
+
+
+def test_served_default_policy_equals_oracle(F):
+    """The default policy at a low arrival rate: most small requests arrive
+    alone and take the per-image kernels, any that meet in one turn share a
+    persistent launch; every output equals the oracle's."""
+    from paper_2411_07351_gb300.serve import Server, run_stream
+
+    reqs, host = _requests(60, 500.0, 64, 1500, 8)
+    srv = Server(budget_bytes=4 << 30)
+    done, _ = run_stream(srv, reqs)
+    assert len(done) == len(reqs)
+    _check_against_oracle(done, host)
     srv.close()
 
 
