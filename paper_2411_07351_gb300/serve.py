@@ -9,7 +9,9 @@ launch (fht_submit) on the least busy of its streams (each stream holds up to
 ``max_inflight`` launches, and a batched launch goes only to a stream whose
 queue can take it without the host waiting: the loop itself never blocks on
 the device); a large request (at least ``plain_pixels``)
-fills the GPU by itself and runs the per-image kernels instead.  Batches on
+fills the GPU by itself and runs the per-image kernels instead, and so does a
+small request admitted alone (``solo_plain``: three short launches finish it
+sooner than a one-job persistent launch).  Batches on
 different streams overlap on the device; a request that arrives while others
 run joins the next batch as soon as memory and a stream are free.  Plans are
 built on the library's native builder threads; requests are admitted in
